@@ -1,0 +1,249 @@
+"""CPU oracle of the (MC)^2MI hot path: plain FP64 C, loaded with ctypes.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The CUDA product
+path never imports it, and it imports nothing from the product package.
+
+Each function cites the passage of the paper it follows; the arithmetic lives
+in ``mcmi_oracle.c`` (see its header for the readings of the points the paper
+leaves open).  ``chains_from_eps`` is *parity unpinned* (the paper does not
+state the rule).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mcmi_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+TABLE_CUMULATIVE = 0
+TABLE_ALIAS = 1
+
+
+def compile_lib(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE FP64, no FMA contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call([
+            "gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+            "-fno-fast-math", "-Wall", "-Wno-unused-function", _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        compile_lib()
+        lib = C.CDLL(_LIB)
+        P = C.c_void_p
+        i64, u64, f64, i32 = C.c_int64, C.c_uint64, C.c_double, C.c_int
+        lib.orc_philox4x32_10.argtypes = [P, P, P]
+        lib.orc_split.argtypes = [i64, P, P, P, f64, P, P, P]
+        lib.orc_split.restype = i32
+        lib.orc_alias_build.argtypes = [P, i64, u64, P, P]
+        lib.orc_pick_cumulative_many.argtypes = [P, i64, P, i64, P]
+        lib.orc_pick_alias_many.argtypes = [P, P, i64, u64, P, i64, P]
+        lib.orc_tables.argtypes = [i64, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_tables.restype = i32
+        lib.orc_max_walk_len.argtypes = [f64, f64, i64]
+        lib.orc_max_walk_len.restype = i64
+        lib.orc_chains_from_eps.argtypes = [f64, f64]
+        lib.orc_chains_from_eps.restype = i64
+        lib.orc_walk_rows.argtypes = [i64, P, P, P, P, P, i32, P, i64, i64, i64, f64, u64, i64, i32,
+                                      P, P, P, P, P, P]
+        lib.orc_walk_rows.restype = i32
+        lib.orc_build_rows.argtypes = [i64, P, P, P, P, P, i32, P, i64, i64, i64, f64, u64, f64, i64,
+                                       i64, i32, P, P, P, P]
+        lib.orc_build_rows.restype = i32
+        lib.orc_filter_row.argtypes = [i64, P, P, i64, f64, i64, P, P]
+        lib.orc_filter_row.restype = i64
+        lib.orc_spmv.argtypes = [i64, P, P, P, P, P]
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _csr(m):
+    rp = np.ascontiguousarray(m.row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(m.col, dtype=np.int32)
+    val = np.ascontiguousarray(m.val, dtype=np.float64)
+    return rp, col, val
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__(f"oracle status {status} {msg}")
+        self.status = status
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block (Salmon et al., SC'11)."""
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    _L().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def split(m, alpha: float = 0.0):
+    """Eq. 1 split (with the Sec. V-C augmentation when alpha > 0) and the
+    Jacobi scaling: returns (d, s), d_i = bhat_ii, s_i = ||c_i||_1."""
+    rp, col, val = _csr(m)
+    d = np.zeros(m.n)
+    s = np.zeros(m.n)
+    bad = np.zeros(1, dtype=np.int64)
+    st = _L().orc_split(m.n, _p(rp), _p(col), _p(val), alpha, _p(d), _p(s), _p(bad))
+    if st:
+        raise OracleError(st, f"row {int(bad[0])}")
+    return d, s
+
+
+def tables(m, d, s, alias: bool = False):
+    """Integer sampling tables of every row (p of Eq. 2 as integers).
+    Returns dict(off, Q, q[, prob, alias]) over off-diagonals in CSR order."""
+    rp, col, val = _csr(m)
+    noff = int(rp[-1]) - int(np.sum(col == np.repeat(np.arange(m.n), np.diff(rp))))
+    off = np.zeros(m.n + 1, dtype=np.int64)
+    Q = np.zeros(m.n, dtype=np.uint64)
+    q = np.zeros(max(noff, 1), dtype=np.uint32)
+    prob = np.zeros(max(noff, 1), dtype=np.uint32) if alias else None
+    al = np.zeros(max(noff, 1), dtype=np.int32) if alias else None
+    _L().orc_tables(m.n, _p(rp), _p(col), _p(val), _p(np.ascontiguousarray(d)),
+                    _p(np.ascontiguousarray(s)), _p(off), _p(Q), _p(q),
+                    _p(prob) if alias else None, _p(al) if alias else None)
+    out = dict(off=off, Q=Q, q=q[:noff])
+    if alias:
+        out["prob"] = prob[:noff]
+        out["alias"] = al[:noff]
+    return out
+
+
+def alias_build(q, Q=None):
+    q = np.ascontiguousarray(q, dtype=np.uint32)
+    Q = int(q.astype(np.uint64).sum()) if Q is None else int(Q)
+    prob = np.zeros(len(q), dtype=np.uint32)
+    al = np.zeros(len(q), dtype=np.int32)
+    _L().orc_alias_build(_p(q), len(q), Q, _p(prob), _p(al))
+    return prob, al
+
+
+def pick_cumulative(q, r):
+    q = np.ascontiguousarray(q, dtype=np.uint32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    out = np.zeros(len(r), dtype=np.int64)
+    _L().orc_pick_cumulative_many(_p(q), len(q), _p(r), len(r), _p(out))
+    return out
+
+
+def pick_alias(prob, al, Q, r):
+    prob = np.ascontiguousarray(prob, dtype=np.uint32)
+    al = np.ascontiguousarray(al, dtype=np.int32)
+    r = np.ascontiguousarray(r, dtype=np.uint32)
+    out = np.zeros(len(r), dtype=np.int64)
+    _L().orc_pick_alias_many(_p(prob), _p(al), len(prob), int(Q), _p(r), len(r), _p(out))
+    return out
+
+
+def max_walk_len(smax, delta, max_len):
+    return int(_L().orc_max_walk_len(float(smax), float(delta), int(max_len)))
+
+
+def chains_from_eps(eps, smax):
+    """N from epsilon (parity unpinned: rule of the earlier (MC)^2MI papers)."""
+    return int(_L().orc_chains_from_eps(float(eps), float(smax)))
+
+
+def _rows(m, rows):
+    if rows is None:
+        rows = np.arange(m.n, dtype=np.int64)
+    return np.ascontiguousarray(rows, dtype=np.int64)
+
+
+def walk(m, rows=None, chains=100, max_len=64, delta=1e-3, seed=1, table=TABLE_CUMULATIVE,
+         alpha=0.0, threads=0):
+    """Eq. 2 estimator, unfiltered: for each listed row a dict with the visited
+    columns (sorted), X = (1/N) sum W, A = (1/N) sum |W|, V = visit counts,
+    and the number of transitions taken."""
+    rp, col, val = _csr(m)
+    d, s = split(m, alpha)
+    rows = _rows(m, rows)
+    tb = max_walk_len(s.max() if m.n else 0.0, delta, max_len)
+    cap = int(min(m.n, chains * (tb + 1)))
+    nr = len(rows)
+    count = np.zeros(nr, dtype=np.int64)
+    steps = np.zeros(nr, dtype=np.uint64)
+    oc = np.zeros(nr * cap, dtype=np.int32)
+    oX = np.zeros(nr * cap)
+    oA = np.zeros(nr * cap)
+    oV = np.zeros(nr * cap, dtype=np.uint32)
+    st = _L().orc_walk_rows(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), table, _p(rows), nr,
+                            chains, max_len, delta, seed, cap, threads, _p(count), _p(steps),
+                            _p(oc), _p(oX), _p(oA), _p(oV))
+    if st:
+        raise OracleError(st)
+    out = []
+    for p in range(nr):
+        a, b = p * cap, p * cap + int(count[p])
+        out.append(dict(row=int(rows[p]), col=oc[a:b].copy(), X=oX[a:b].copy(), A=oA[a:b].copy(),
+                        V=oV[a:b].copy(), steps=int(steps[p])))
+    return out, d, s
+
+
+def filter_row(i, cols, mvals, tau=0.0, top_k=0):
+    """Sec. IV-B filter of one column-scaled row (cols sorted)."""
+    cols = np.ascontiguousarray(cols, dtype=np.int32)
+    mvals = np.ascontiguousarray(mvals, dtype=np.float64)
+    oc = np.zeros(max(len(cols), 1), dtype=np.int32)
+    ov = np.zeros(max(len(cols), 1))
+    k = _L().orc_filter_row(int(i), _p(cols), _p(mvals), len(cols), float(tau), int(top_k), _p(oc), _p(ov))
+    return oc[:k].copy(), ov[:k].copy()
+
+
+def build(m, rows=None, chains=100, max_len=64, delta=1e-3, seed=1, tau=0.0, top_k=0,
+          table=TABLE_CUMULATIVE, alpha=0.0, threads=0):
+    """Preconditioner rows: Eq. 2 walks, column scaling by 1/d_j (phase 4),
+    Sec. IV-B filter.  Returns (row_ptr, col, val, steps_per_row) for the
+    listed rows (in the given order)."""
+    rp, col, val = _csr(m)
+    d, s = split(m, alpha)
+    rows = _rows(m, rows)
+    tb = max_walk_len(s.max() if m.n else 0.0, delta, max_len)
+    cap = int(min(m.n, chains * (tb + 1)))
+    if top_k > 0:
+        cap = min(cap, top_k + 1)
+    nr = len(rows)
+    count = np.zeros(nr, dtype=np.int64)
+    steps = np.zeros(nr, dtype=np.uint64)
+    oc = np.zeros(nr * cap, dtype=np.int32)
+    ov = np.zeros(nr * cap)
+    st = _L().orc_build_rows(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), table, _p(rows), nr,
+                             chains, max_len, delta, seed, tau, top_k, cap, threads,
+                             _p(count), _p(steps), _p(oc), _p(ov))
+    if st:
+        raise OracleError(st)
+    orp = np.zeros(nr + 1, dtype=np.int64)
+    np.cumsum(count, out=orp[1:])
+    keep = np.concatenate([np.arange(p * cap, p * cap + count[p]) for p in range(nr)]) if nr else np.zeros(0, int)
+    return orp, oc[keep], ov[keep], steps
+
+
+def spmv(rp, col, val, x):
+    rp = np.ascontiguousarray(rp, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(len(rp) - 1)
+    _L().orc_spmv(len(rp) - 1, _p(rp), _p(col), _p(val), _p(x), _p(y))
+    return y

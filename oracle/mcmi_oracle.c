@@ -1,0 +1,544 @@
+/*
+ * mcmi_oracle.c -- plain, slow, FP64 CPU reference of the (MC)^2MI hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this file's library.  It shares no
+ * code, header or constant table with the CUDA path.
+ *
+ * What it computes (paper: Lebedev & Alexandrov, "On Advanced Monte Carlo
+ * Methods for Linear Algebra on Advanced Accelerator Architectures"):
+ *   - the split of Eq. 1 with the sgn(b_ii)-aware augmentation of Sec. V-C
+ *     (alpha = 0 leaves B unchanged) and the Jacobi scaling of Sec. III-A /
+ *     Sec. IV-A phase 2: d_i = bhat_ii, c_ij = -b_ij / d_i (j != i),
+ *     s_i = ||c_i||_1 summed in CSR order;
+ *   - the transition probabilities p_ij = |c_ij| / s_i (the p of Eq. 2), held
+ *     as integer weights q_ij = max(1, floor(p_ij 2^31)) (0 for c_ij == 0)
+ *     so that every sampled transition is an integer decision;
+ *   - the estimator of Eq. 2: N chains per row r, each starting at r with
+ *     weight 1 (the empty product, j = 0 term), moving r -> s1 -> s2 ... with
+ *     probability p, multiplying the weight by a/p = sign(c) s, and adding
+ *     the weight to column s_j of row r at every visit; chains stop at a
+ *     weight cutoff delta or a maximum length L;
+ *   - phase 4 of Sec. IV (column scaling by B_1^-1) and the row filter of
+ *     Sec. IV-B (keep the entries largest in magnitude).
+ *
+ * Readings of points the paper leaves open (each is listed with its reason in
+ * the design notes): the stop rule is tested on a single-precision shadow of
+ * the weight, W32 <- fl32(W32 * fl32(sign s)), before each transition, so
+ * that a single-precision implementation stops at the same step; random
+ * numbers are Philox4x32-10 keyed by the seed, counter (t/4, chain, row lo,
+ * row hi), word t mod 4 for transition t; a row with s_i == 0 is absorbing.
+ *
+ * Parity pins: every exported function here is checked by the CPU test-suite
+ * against something other than itself (cuRAND's host Philox, dense matrix
+ * powers, path enumeration, closed forms, numpy sorting).  The only function
+ * without such a pin is orc_chains_from_eps (parity unpinned: the paper does
+ * not state how N follows from epsilon).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_BAD_CSR = 2, ORC_ERR_ZERO_DIAG = 3,
+       ORC_ERR_NOT_CONTRACTIVE = 4, ORC_ERR_CAPACITY = 5 };
+enum { ORC_TABLE_CUMULATIVE = 0, ORC_TABLE_ALIAS = 1 };
+
+/* ---------------------------------------------------------------------- */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11.  Round: two 32x32->64 products of counter       */
+/* words 0 and 2 with the round multipliers, outputs permuted and xored     */
+/* with the key; the key is bumped by the Weyl constants between rounds.    */
+/* ---------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        x0 = y0; x1 = lo1; x2 = y2; x3 = lo0;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Eq. 1 split + Jacobi scaling (Sec. III-A; Sec. IV-A phases 1-2; the      */
+/* augmentation alpha*||B||_inf*sgn(b_ii) of Sec. V-C).                     */
+/* ---------------------------------------------------------------------- */
+int orc_split(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+              double alpha, double *d, double *s, int64_t *bad_row)
+{
+    double bnorm = 0.0;
+    *bad_row = -1;
+    if (alpha > 0.0) {
+        for (int64_t i = 0; i < n; ++i) {
+            double r = 0.0;
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) r += fabs(val[k]);
+            if (r > bnorm) bnorm = r;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        double bii = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (col[k] == i) bii = val[k];
+        double di = bii;
+        if (alpha > 0.0) di = bii + alpha * bnorm * (bii < 0.0 ? -1.0 : 1.0);
+        if (di == 0.0) { *bad_row = i; return ORC_ERR_ZERO_DIAG; }
+        double si = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            if (col[k] == i) continue;
+            double c = -val[k] / di;
+            si += fabs(c);
+        }
+        d[i] = di;
+        s[i] = si;
+    }
+    return ORC_OK;
+}
+
+/* Integer weight of one off-diagonal entry: q = max(1, floor(|c|/s * 2^31)),  */
+/* 0 for an entry whose c is exactly zero (never sampled).                    */
+static uint32_t weight_of(double b, double di, double si)
+{
+    double c = -b / di;
+    if (c == 0.0) return 0u;
+    double x = floor(fabs(c) / si * 2147483648.0);
+    uint32_t q = (uint32_t)x;
+    return q < 1u ? 1u : q;
+}
+
+/* Row i's off-diagonal weights in CSR order; returns the degree.           */
+static int64_t row_weights(int64_t i, const int64_t *rp, const int32_t *col, const double *val,
+                           const double *d, const double *s, uint32_t *q, int32_t *cols,
+                           uint8_t *neg, uint64_t *Q)
+{
+    int64_t m = 0;
+    uint64_t tot = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        if (col[k] == i) continue;
+        uint32_t w = s[i] > 0.0 ? weight_of(val[k], d[i], s[i]) : 0u;
+        if (q) q[m] = w;
+        if (cols) cols[m] = col[k];
+        if (neg) neg[m] = (-val[k] / d[i]) < 0.0;
+        tot += w;
+        ++m;
+    }
+    *Q = tot;
+    return m;
+}
+
+/* Cumulative sampler: x = floor(r Q / 2^32); the pick is the smallest m with   */
+/* x < T_m, T_m = q_0 + ... + q_m.                                            */
+static int64_t pick_cumulative(uint32_t r, const uint32_t *q, int64_t deg, uint64_t Q)
+{
+    uint64_t x = ((uint64_t)r * Q) >> 32;
+    uint64_t T = 0;
+    for (int64_t m = 0; m < deg; ++m) {
+        T += q[m];
+        if (x < T) return m;
+    }
+    return -1; /* unreachable when Q > 0 */
+}
+
+/* Walker/Vose alias table over the integer weights.  Bucket capacity Q,    */
+/* weight of entry j is q_j * deg (so the deg buckets hold deg*Q in total).  */
+/* Both work lists are stacks (last in, first out), filled in CSR order;    */
+/* after each pairing the large entry is pushed back on the list its        */
+/* remaining weight belongs to.                                             */
+void orc_alias_build(const uint32_t *q, int64_t deg, uint64_t Q, uint32_t *prob, int32_t *alias)
+{
+    uint64_t *w = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(deg > 0 ? deg : 1));
+    int64_t *small = (int64_t *)malloc(sizeof(int64_t) * (size_t)(deg > 0 ? deg : 1));
+    int64_t *large = (int64_t *)malloc(sizeof(int64_t) * (size_t)(deg > 0 ? deg : 1));
+    int64_t ns = 0, nl = 0;
+    for (int64_t j = 0; j < deg; ++j) {
+        w[j] = (uint64_t)q[j] * (uint64_t)deg;
+        if (w[j] < Q) small[ns++] = j; else large[nl++] = j;
+    }
+    while (ns > 0 && nl > 0) {
+        int64_t a = small[--ns];
+        int64_t b = large[--nl];
+        prob[a] = (uint32_t)w[a];
+        alias[a] = (int32_t)b;
+        w[b] -= Q - w[a];
+        if (w[b] < Q) small[ns++] = b; else large[nl++] = b;
+    }
+    while (nl > 0) { int64_t b = large[--nl]; prob[b] = (uint32_t)Q; alias[b] = (int32_t)b; }
+    while (ns > 0) { int64_t a = small[--ns]; prob[a] = (uint32_t)Q; alias[a] = (int32_t)a; }
+    free(w); free(small); free(large);
+}
+
+/* Alias sampler: bucket b = floor(r deg / 2^32); the low 32 bits of r*deg,   */
+/* scaled to [0, Q), decide between the bucket's own entry and its alias.    */
+static int64_t pick_alias(uint32_t r, int64_t deg, uint64_t Q, const uint32_t *prob, const int32_t *alias)
+{
+    uint64_t p = (uint64_t)r * (uint64_t)deg;
+    int64_t b = (int64_t)(p >> 32);
+    uint64_t y = ((p & 0xFFFFFFFFull) * Q) >> 32;
+    return y < prob[b] ? b : alias[b];
+}
+
+/* Exported samplers for the CPU tests (vectorised over r).                */
+void orc_pick_cumulative_many(const uint32_t *q, int64_t deg, const uint32_t *r, int64_t cnt, int64_t *out)
+{
+    uint64_t Q = 0;
+    for (int64_t m = 0; m < deg; ++m) Q += q[m];
+    for (int64_t t = 0; t < cnt; ++t) out[t] = pick_cumulative(r[t], q, deg, Q);
+}
+
+void orc_pick_alias_many(const uint32_t *prob, const int32_t *alias, int64_t deg, uint64_t Q,
+                         const uint32_t *r, int64_t cnt, int64_t *out)
+{
+    for (int64_t t = 0; t < cnt; ++t) out[t] = pick_alias(r[t], deg, Q, prob, alias);
+}
+
+/* Per-row integer tables, for the table-parity tests.  Output per row i:    */
+/* Q[i]; per off-diagonal entry (in CSR order, offsets off[i]):            */
+/* q, and for the alias table prob and alias (row-local index).            */
+int orc_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+               const double *d, const double *s, int64_t *off, uint64_t *Q,
+               uint32_t *q, uint32_t *prob, int32_t *alias)
+{
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        off[i] = o;
+        int64_t deg = row_weights(i, rp, col, val, d, s, q + o, NULL, NULL, &Q[i]);
+        if (prob && alias && deg > 0) orc_alias_build(q + o, deg, Q[i], prob + o, alias + o);
+        o += deg;
+    }
+    off[n] = o;
+    return ORC_OK;
+}
+
+/* Longest possible chain: every factor is at most fl32(max_i s_i) in        */
+/* magnitude and fl32 multiplication is monotone, so no chain outlives the   */
+/* product of that constant.                                               */
+int64_t orc_max_walk_len(double smax, double delta, int64_t L)
+{
+    float f = (float)smax, w = 1.0f;
+    if (!(delta > 0.0) || f >= 1.0f) return L;
+    int64_t t = 0;
+    while (t < L && !((double)fabsf(w) < delta)) {
+        w = w * f;
+        ++t;
+    }
+    return t;
+}
+
+/* Number of chains from the accuracy epsilon when the caller gives none     */
+/* (parity unpinned: the paper does not state the rule; this is the rule of  */
+/* the earlier (MC)^2MI papers it builds on, N = (0.6745 / (eps (1-||C||)))^2). */
+int64_t orc_chains_from_eps(double eps, double smax)
+{
+    double v = 0.6745 / (eps * (1.0 - smax));
+    return (int64_t)ceil(v * v);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Eq. 2 walks.                                                           */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int64_t n;
+    const int64_t *rp;
+    const int32_t *col;
+    const double *val;
+    const double *d, *s;
+    /* derived, per row: offsets into the off-diagonal arrays */
+    int64_t *off;
+    uint64_t *Q;
+    uint32_t *q;
+    int32_t *ocol;
+    uint8_t *neg;
+    uint32_t *prob;
+    int32_t *alias;
+} orc_mat;
+
+static int mat_prepare(orc_mat *M, int table)
+{
+    int64_t n = M->n;
+    int64_t noff = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = M->rp[i]; k < M->rp[i + 1]; ++k)
+            if (M->col[k] != i) ++noff;
+    size_t sz = (size_t)(noff > 0 ? noff : 1);
+    M->off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    M->Q = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(n > 0 ? n : 1));
+    M->q = (uint32_t *)malloc(sizeof(uint32_t) * sz);
+    M->ocol = (int32_t *)malloc(sizeof(int32_t) * sz);
+    M->neg = (uint8_t *)malloc(sz);
+    M->prob = table == ORC_TABLE_ALIAS ? (uint32_t *)malloc(sizeof(uint32_t) * sz) : NULL;
+    M->alias = table == ORC_TABLE_ALIAS ? (int32_t *)malloc(sizeof(int32_t) * sz) : NULL;
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        M->off[i] = o;
+        int64_t deg = row_weights(i, M->rp, M->col, M->val, M->d, M->s, M->q + o, M->ocol + o,
+                                  M->neg + o, &M->Q[i]);
+        if (table == ORC_TABLE_ALIAS && deg > 0)
+            orc_alias_build(M->q + o, deg, M->Q[i], M->prob + o, M->alias + o);
+        o += deg;
+    }
+    M->off[n] = o;
+    return ORC_OK;
+}
+
+static void mat_release(orc_mat *M)
+{
+    free(M->off); free(M->Q); free(M->q); free(M->ocol); free(M->neg);
+    free(M->prob); free(M->alias);
+}
+
+typedef struct {
+    double *X, *A;
+    uint32_t *V;
+    int64_t *touched;
+    int64_t ntouched;
+} orc_acc;
+
+static void acc_add(orc_acc *a, int64_t j, double w)
+{
+    if (a->V[j] == 0) a->touched[a->ntouched++] = j;
+    a->X[j] += w;
+    a->A[j] += fabs(w);
+    a->V[j] += 1;
+}
+
+static int cmp_i64(const void *x, const void *y)
+{
+    int64_t a = *(const int64_t *)x, b = *(const int64_t *)y;
+    return (a > b) - (a < b);
+}
+
+/* All N chains of row i (Eq. 2); fills the accumulator, returns transitions. */
+static uint64_t walk_row(const orc_mat *M, int table, int64_t i, int64_t N, int64_t L,
+                         double delta, uint64_t seed, orc_acc *acc)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint64_t steps = 0;
+    for (int64_t k = 0; k < N; ++k) {
+        int64_t state = i;
+        double w = 1.0;
+        float w32 = 1.0f;
+        uint32_t r4[4] = {0, 0, 0, 0};
+        int64_t t = 0;
+        acc_add(acc, state, w);
+        for (;;) {
+            if (t == L) break;
+            if ((double)fabsf(w32) < delta) break;
+            if (M->Q[state] == 0) break;
+            if (t % 4 == 0) {
+                uint32_t ctr[4] = {(uint32_t)(t / 4), (uint32_t)k, (uint32_t)i, (uint32_t)((uint64_t)i >> 32)};
+                orc_philox4x32_10(ctr, key, r4);
+            }
+            uint32_t r = r4[t % 4];
+            int64_t o = M->off[state], deg = M->off[state + 1] - o;
+            int64_t m = table == ORC_TABLE_ALIAS
+                            ? pick_alias(r, deg, M->Q[state], M->prob + o, M->alias + o)
+                            : pick_cumulative(r, M->q + o, deg, M->Q[state]);
+            double sj = M->s[state];
+            int negative = M->neg[o + m];
+            w = w * (negative ? -sj : sj);
+            float f32 = (float)sj;
+            w32 = w32 * (negative ? -f32 : f32);
+            state = M->ocol[o + m];
+            ++t;
+            acc_add(acc, state, w);
+        }
+        steps += (uint64_t)t;
+    }
+    return steps;
+}
+
+static int acc_alloc(orc_acc *a, int64_t n)
+{
+    a->X = (double *)calloc((size_t)n, sizeof(double));
+    a->A = (double *)calloc((size_t)n, sizeof(double));
+    a->V = (uint32_t *)calloc((size_t)n, sizeof(uint32_t));
+    a->touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    a->ntouched = 0;
+    return a->X && a->A && a->V && a->touched ? 0 : -1;
+}
+
+static void acc_reset(orc_acc *a)
+{
+    for (int64_t t = 0; t < a->ntouched; ++t) {
+        int64_t j = a->touched[t];
+        a->X[j] = 0.0; a->A[j] = 0.0; a->V[j] = 0;
+    }
+    a->ntouched = 0;
+}
+
+static void acc_free(orc_acc *a) { free(a->X); free(a->A); free(a->V); free(a->touched); }
+
+static void set_threads(int threads)
+{
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#else
+    (void)threads;
+#endif
+}
+
+/* Raw accumulators of the listed rows: for row r (position p in rows[]),    */
+/* entries p*cap .. p*cap+count[p]-1 hold (column, X/N, A/N, V) sorted by    */
+/* column, where A is the sum of |W| (the scale used to judge cancellation). */
+int orc_walk_rows(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                  const double *d, const double *s, int table, const int64_t *rows, int64_t nrows,
+                  int64_t N, int64_t L, double delta, uint64_t seed, int64_t cap, int threads,
+                  int64_t *count, uint64_t *steps, int32_t *ocol, double *oX, double *oA, uint32_t *oV)
+{
+    orc_mat M = {n, rp, col, val, d, s};
+    mat_prepare(&M, table);
+    int status = ORC_OK;
+    set_threads(threads);
+#pragma omp parallel
+    {
+        orc_acc acc;
+        acc_alloc(&acc, n);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t p = 0; p < nrows; ++p) {
+            int64_t i = rows[p];
+            steps[p] = walk_row(&M, table, i, N, L, delta, seed, &acc);
+            qsort(acc.touched, (size_t)acc.ntouched, sizeof(int64_t), cmp_i64);
+            if (acc.ntouched > cap) {
+#pragma omp atomic write
+                status = ORC_ERR_CAPACITY;
+                count[p] = -1;
+            } else {
+                count[p] = acc.ntouched;
+                for (int64_t t = 0; t < acc.ntouched; ++t) {
+                    int64_t j = acc.touched[t];
+                    ocol[p * cap + t] = (int32_t)j;
+                    oX[p * cap + t] = acc.X[j] / (double)N;
+                    oA[p * cap + t] = acc.A[j] / (double)N;
+                    oV[p * cap + t] = acc.V[j];
+                }
+            }
+            acc_reset(&acc);
+        }
+        acc_free(&acc);
+    }
+    mat_release(&M);
+    return status;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Phase 4 (column scaling by B_1^-1, Sec. IV-A) and the filter of Sec. IV-B. */
+/* ---------------------------------------------------------------------- */
+typedef struct { double mag; int64_t j; } orc_cand;
+
+static int cmp_cand(const void *x, const void *y)
+{
+    const orc_cand *a = (const orc_cand *)x, *b = (const orc_cand *)y;
+    if (a->mag > b->mag) return -1;
+    if (a->mag < b->mag) return 1;
+    return (a->j > b->j) - (a->j < b->j);
+}
+
+/* Filter one row given its column-scaled entries M_j (sorted by column).   */
+/* Keeps the diagonal; off-diagonals with |M_j| >= tau * max|M| (tau > 0);  */
+/* of those, the top_k largest in magnitude, ties to the smaller column.    */
+int64_t orc_filter_row(int64_t i, const int32_t *cols, const double *m, int64_t cnt,
+                       double tau, int64_t top_k, int32_t *out_col, double *out_val)
+{
+    double rowmax = 0.0;
+    for (int64_t t = 0; t < cnt; ++t) if (fabs(m[t]) > rowmax) rowmax = fabs(m[t]);
+    orc_cand *c = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)(cnt > 0 ? cnt : 1));
+    int64_t nc = 0;
+    for (int64_t t = 0; t < cnt; ++t) {
+        if (cols[t] == i) continue;
+        if (tau > 0.0 && !(fabs(m[t]) >= tau * rowmax)) continue;
+        c[nc].mag = fabs(m[t]);
+        c[nc].j = cols[t];
+        ++nc;
+    }
+    if (top_k > 0 && nc > top_k) {
+        /* rank by magnitude (descending), then column (ascending) */
+        qsort(c, (size_t)nc, sizeof(orc_cand), cmp_cand);
+        nc = top_k;
+    }
+    /* kept columns plus the diagonal, emitted in column order */
+    int64_t *keep = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nc + 1));
+    int64_t nk = 0;
+    for (int64_t u = 0; u < nc; ++u) keep[nk++] = c[u].j;
+    for (int64_t t = 0; t < cnt; ++t) if (cols[t] == i) { keep[nk++] = i; break; }
+    qsort(keep, (size_t)nk, sizeof(int64_t), cmp_i64);
+    int64_t t = 0;
+    for (int64_t u = 0; u < nk; ++u) {
+        while (cols[t] != keep[u]) ++t;
+        out_col[u] = cols[t];
+        out_val[u] = m[t];
+    }
+    free(c); free(keep);
+    return nk;
+}
+
+/* Whole preconditioner rows: walk (Eq. 2), scale column j by 1/d_j, filter. */
+int orc_build_rows(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                   const double *d, const double *s, int table, const int64_t *rows, int64_t nrows,
+                   int64_t N, int64_t L, double delta, uint64_t seed, double tau, int64_t top_k,
+                   int64_t cap, int threads, int64_t *count, uint64_t *steps,
+                   int32_t *out_col, double *out_val)
+{
+    orc_mat M = {n, rp, col, val, d, s};
+    mat_prepare(&M, table);
+    int status = ORC_OK;
+    set_threads(threads);
+#pragma omp parallel
+    {
+        orc_acc acc;
+        acc_alloc(&acc, n);
+        int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        double *m = (double *)malloc(sizeof(double) * (size_t)n);
+        int32_t *kc = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+        double *kv = (double *)malloc(sizeof(double) * (size_t)n);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t p = 0; p < nrows; ++p) {
+            int64_t i = rows[p];
+            steps[p] = walk_row(&M, table, i, N, L, delta, seed, &acc);
+            qsort(acc.touched, (size_t)acc.ntouched, sizeof(int64_t), cmp_i64);
+            for (int64_t t = 0; t < acc.ntouched; ++t) {
+                int64_t j = acc.touched[t];
+                cols[t] = (int32_t)j;
+                m[t] = (acc.X[j] / (double)N) / d[j];
+            }
+            int64_t nk = orc_filter_row(i, cols, m, acc.ntouched, tau, top_k, kc, kv);
+            if (nk > cap) {
+#pragma omp atomic write
+                status = ORC_ERR_CAPACITY;
+                count[p] = -1;
+            } else {
+                count[p] = nk;
+                memcpy(out_col + p * cap, kc, sizeof(int32_t) * (size_t)nk);
+                memcpy(out_val + p * cap, kv, sizeof(double) * (size_t)nk);
+            }
+            acc_reset(&acc);
+        }
+        acc_free(&acc);
+        free(cols); free(m); free(kc); free(kv);
+    }
+    mat_release(&M);
+    return status;
+}
+
+/* y = M x for a CSR M (the preconditioner applied as in Sec. III-A's use).  */
+void orc_spmv(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+              const double *x, double *y)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) acc += val[k] * x[col[k]];
+        y[i] = acc;
+    }
+}
