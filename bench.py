@@ -1,0 +1,349 @@
+#!/usr/bin/env python3
+"""Throughput of the (MC)^2MI preconditioner build on B300: MC walk steps/s.
+
+A step is one pass of the whole hot path over the workload: mcmi_build_ex
+(validation, Eq. 1 split + Jacobi scaling, integer tables, Eq. 2 walks with
+the fused column scaling and filter, CSR assembly) followed by one
+mcmi_apply (y = M x).  Inputs are resident in HBM; L2 is flushed (256 MiB
+write) between timed steps; every step is timed with CUDA events on the
+build stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank builds the preconditioner of its own copy of the
+workload (independent problems, no collective on the data path: weak
+scaling); rank 0 prints one JSON line.  ``--impl reference`` times the CPU
+oracle (plain FP64 C) on the host cores on a bounded row sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "stencil3d_64": "3D 7-point variable-coefficient diffusion, 64^3 grid (n=262144), lognormal(0,1) face "
+                    "coefficients, ||C||_inf=0.9; 256 chains/row, cutoff 1e-2, max length 128, top-16 per row",
+    "stencil3d_32": "3D 7-point as stencil3d_64 on a 32^3 grid (n=32768): profiling-size case",
+    "stencil2d_32x32": "2D 5-point, 32x32 (n=1024), diag 4+U(0,0.5), off-diag -U(0.8,1.0); 1000 chains/row, "
+                       "cutoff 1e-3, max length 64, tau 1e-2",
+    "powerlaw_1m": "random sparse nonsymmetric n=1048576, power-law rows (alpha 2.5, 4..256), N(0,1) values, "
+                   "dominance 0.85; 128 chains/row, cutoff 1e-3, max length 256, tau 5e-3",
+}
+SLOT_BYTES = 64   # one row record (two 32-B sectors) read per visited state
+METRIC = "MC walk steps/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stencil3d_64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def _traffic(kernel_src):
+    """DRAM bytes per walk launch from the committed ncu summary, if it was
+    taken on the current kernel source (else null)."""
+    path = os.path.join(ROOT, "profiles", "walk_stencil3d_64_traffic.txt")
+    try:
+        kv = dict(l.split(":", 1) for l in open(path).read().splitlines() if ":" in l)
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    if kv.get("walk_cu_sha256_16", "").strip() != src_hash:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.count(",") >= 8]
+        os.unlink(self.f.name)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _params_for(mc, name, seed):
+    m, w = synth.workload(name)
+    p = mc.params(chains=w["chains"], max_len=w["max_len"], delta=w["delta"], filter_tau=w["tau"],
+                  top_k=w["top_k"], seed=seed)
+    return m, w, p
+
+
+def _cpu_baseline(m, w, seconds, table):
+    """The oracle, as it stands, on all host cores, on a strided row sample
+    sized to about `seconds` of CPU work."""
+    import oracle
+    cores = os.cpu_count() or 1
+    probe = np.arange(0, m.n, max(1, m.n // 256))[:256]
+    t0 = time.perf_counter()
+    oracle.build(m, rows=probe, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
+                 tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    nrows = int(min(m.n, max(256, len(probe) * seconds / dt)))
+    rows = np.linspace(0, m.n - 1, nrows).astype(np.int64)
+    t0 = time.perf_counter()
+    _, _, _, steps = oracle.build(m, rows=rows, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
+                                  tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": float(steps.sum()) / dt, "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nrows} of {m.n} rows (evenly spaced), {int(steps.sum())} transitions in {dt:.1f} s",
+            "rows_per_s": nrows / dt}
+
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    m, w = synth.workload(a.workload)
+    table = 0 if (m.nnz - m.n) <= 6 * m.n else 1
+    cores = os.cpu_count() or 1
+    budget = 150.0 / max(1, a.steps + a.warmup)
+    probe = np.arange(0, m.n, max(1, m.n // 128))[:128]
+    t0 = time.perf_counter()
+    oracle.build(m, rows=probe, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
+                 tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    nrows = int(min(m.n, max(128, len(probe) * budget / dt)))
+    rows = np.linspace(0, m.n - 1, nrows).astype(np.int64)
+    times, tot = [], 0
+    for it in range(a.warmup + a.steps):
+        t0 = time.perf_counter()
+        _, _, _, steps = oracle.build(m, rows=rows, chains=w["chains"], max_len=w["max_len"], delta=w["delta"],
+                                      seed=1 + it, tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+        dt = time.perf_counter() - t0
+        if it >= a.warmup:
+            times.append(dt)
+            tot += int(steps.sum())
+    value = tot / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1000 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "rows_per_step": nrows,
+                       "rows_per_s": nrows * len(times) / sum(times)},
+            "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{nrows} of {m.n} rows per step (evenly spaced)"},
+            "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import paper_2409_03095_b300 as mc
+    mc.load()
+    m, w, p = _params_for(mc, a.workload, seed=1000 + rank)
+    B = mc.DeviceCsr.from_host(m)
+    x = torch.ones(m.n, device="cuda", dtype=torch.float32)
+    y = torch.empty(m.n, device="cuda", dtype=torch.float32)
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)   # 256 MiB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        M = mc.mcmi_build_ex(B, p, stream)
+        mc.mcmi_apply(M, x, y, stream)
+        st = M.stats
+        M.close()
+        return st
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    times, walk_ms, steps, visits, launches = [], [], 0, 0, 0
+    for it in range(a.steps):
+        flush.fill_(float(it))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        walk_ms.append(st.ms_walk_kernel)
+        steps += st.steps
+        visits += st.steps + st.chains * st.rows
+        launches += st.launches + 1
+        last = st
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ck = clocks.stop() if clocks else None
+    tot_ms = sum(times)
+    tot_steps = steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        s = torch.tensor([float(steps)], device="cuda", dtype=torch.float64)
+        dist.all_reduce(s, op=dist.ReduceOp.SUM)
+        tot_steps = s.item()
+    value = tot_steps / (tot_ms / 1e3)
+
+    # e2e through the public API with host buffers: H2D of B, build, apply,
+    # D2H of M and y, all inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        h_rp = torch.from_numpy(m.row_ptr.astype(np.int64)).pin_memory()
+        h_col = torch.from_numpy(m.col.astype(np.int32)).pin_memory()
+        h_val = torch.from_numpy(m.val.astype(np.float64)).pin_memory()
+        h_x = torch.ones(m.n, dtype=torch.float32).pin_memory()
+        d_rp, d_col, d_val = torch.empty_like(h_rp, device="cuda"), torch.empty_like(h_col, device="cuda"), \
+            torch.empty_like(h_val, device="cuda")
+        Bd = mc.DeviceCsr(m.n, d_rp, d_col, d_val)
+        d_x = torch.empty(m.n, device="cuda", dtype=torch.float32)
+        h_y = torch.empty(m.n, dtype=torch.float32).pin_memory()
+        et, esteps, h2d, d2h = [], 0, 0, 0
+        for it in range(max(1, min(a.steps, 5))):
+            flush.fill_(float(it))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            d_rp.copy_(h_rp, non_blocking=True)
+            d_col.copy_(h_col, non_blocking=True)
+            d_val.copy_(h_val, non_blocking=True)
+            d_x.copy_(h_x, non_blocking=True)
+            M = mc.mcmi_build_ex(Bd, p, stream)
+            mc.mcmi_apply(M, d_x, y, stream)
+            rp_, col_, val_ = M.to_torch(stream)
+            h_mrp, h_mcol, h_mval = rp_.to("cpu", non_blocking=True), col_.to("cpu", non_blocking=True), \
+                val_.to("cpu", non_blocking=True)
+            h_y.copy_(y, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            et.append(e0.elapsed_time(e1))
+            esteps += M.stats.steps
+            h2d = (h_rp.numel() * 8 + h_col.numel() * 4 + h_val.numel() * 8 + h_x.numel() * 4)
+            d2h = (rp_.numel() * 8 + col_.numel() * 4 + val_.numel() * 4 + h_y.numel() * 4)
+            M.close()
+        e2e = {"value": esteps / (sum(et) / 1e3), "unit": "steps/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": sum(et) / len(et)}
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    peaks, peak_src = _peaks()
+    walk_total_ms = sum(walk_ms)
+    alg_bytes = SLOT_BYTES * visits
+    achieved = alg_bytes / (walk_total_ms / 1e3) / 1e9
+    traffic = _traffic(os.path.join(ROOT, "paper_2409_03095_b300", "csrc", "walk.cu"))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+            "kernel": "k_walk (walk + accumulate + filter)",
+            "peak_source": f"{peak_src} HBM copy bandwidth",
+            "algorithmic_bytes_per_launch": alg_bytes / max(1, len(walk_ms)),
+            "bytes_per_unit": "64 B (one 64-B row record, two 32-B sectors) per visited state",
+            "walk_kernel_ms": walk_total_ms / max(1, len(walk_ms)),
+            "walk_share_of_step": walk_total_ms / tot_ms if world == 1 else None}
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        cpu = _cpu_baseline(m, w, a.cpu_seconds, last.table)
+    rows_per_s = (last.rows * a.steps * world) / (tot_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "rows": last.rows,
+                       "rows_per_s": rows_per_s, "chains": last.chains, "table": ["cumulative", "alias"][last.table],
+                       "nnz_M": last.nnz, "steps_per_build": last.steps, "max_len_bound": last.max_len_bound,
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"rows on one GPU; {world} independent builds (one per GPU)",
+                       "stage_ms": {"prepare": last.ms_prepare, "walk": last.ms_walk, "assemble": last.ms_assemble}},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,188 @@
+/*
+ * mcmi.h -- C ABI of the B300 (sm_103a) Markov Chain Monte Carlo Matrix
+ * Inversion ((MC)^2MI) sparse-approximate-inverse preconditioner.
+ *
+ * Method (Lebedev & Alexandrov, "On Advanced Monte Carlo Methods for Linear
+ * Algebra on Advanced Accelerator Architectures"): split B = Bhat - C
+ * (Eq. 1), scale by D = diag(Bhat) so that C = I - D^-1 Bhat has
+ * ||C||_inf < 1 (Sec. III-A, Sec. IV-A phases 1-2), estimate the rows of
+ * (I - C)^-1 by random walks over the Neumann series (Eq. 2, phase 3),
+ * scale column j by 1/d_j (phase 4), and keep per row the entries largest in
+ * magnitude (Sec. IV-B).  The recovery of Eq. 3 (phase 5) is not done: the
+ * paper notes it costs O(n^3) and is usually skipped (Sec. IV).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named "device" must point to device memory of the current CUDA
+ *    device; "host" pointers to host memory.  Input arrays are owned by the
+ *    caller and only read during the call.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    ordered on it.  Entry points that must learn a size on the host
+ *    (mcmi_build*, mcmi_walk_dump) synchronise `stream` before returning;
+ *    mcmi_apply and mcmi_debug_tables do not.
+ *  - Return value: MCMI_OK or an error code.  On error no output handle is
+ *    produced (*M_out == NULL) and mcmi_last_error() describes the cause.
+ *  - Matrices: CSR, int64 row_ptr[n+1] (row_ptr[0] == 0, non-decreasing,
+ *    row_ptr[n] == nnz), int32 col[nnz] strictly increasing inside a row and
+ *    in [0, n), float64 val[nnz] finite.  nnz must be below 2^32.
+ *  - Determinism: a walk is a function of (seed, row, chain, step) only, so
+ *    the same inputs and seed give the same paths and visit counts on any
+ *    launch configuration, row subset or table layout of the same table
+ *    type.  FP32 sums are accumulated with compensated (Kahan) additions in
+ *    an order that depends on thread timing: results can differ in the last
+ *    bits between runs; FP64 sums likewise.
+ */
+#ifndef MCMI_H
+#define MCMI_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCMI_OK = 0,
+    MCMI_ERR_ARG = 1,             /* null pointer, bad size or unsupported parameter */
+    MCMI_ERR_BAD_CSR = 2,         /* malformed CSR: row_ptr, column order/range, non-finite value */
+    MCMI_ERR_ZERO_DIAG = 3,       /* d_i = bhat_ii == 0 for some row (Eq. 1 needs d_i != 0) */
+    MCMI_ERR_NOT_CONTRACTIVE = 4, /* some s_i = ||c_i||_1 >= 1: raise alpha (Eq. 1) */
+    MCMI_ERR_OOM = 5,             /* device allocation failed */
+    MCMI_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+    MCMI_ERR_TIMEOUT = 7,         /* a bounded device-side wait gave up */
+    MCMI_ERR_CAPACITY = 8         /* an internal device capacity was exceeded */
+} mcmi_status;
+
+/* Sampling table of the transition probabilities p_ij = |c_ij| / s_i.    */
+enum {
+    MCMI_TABLE_AUTO = -1,       /* pick from the degree distribution */
+    MCMI_TABLE_CUMULATIVE = 0,  /* integer cumulative thresholds */
+    MCMI_TABLE_ALIAS = 1        /* integer Walker/Vose alias buckets */
+};
+
+typedef struct {
+    int64_t n;              /* rows (= columns) */
+    int64_t nnz;            /* stored entries */
+    const int64_t *row_ptr; /* device, n+1 */
+    const int32_t *col;     /* device, nnz */
+    const double *val;      /* device, nnz */
+} mcmi_csr;
+
+/* Parameters of one preconditioner build.  Fill with mcmi_params_default.  */
+typedef struct {
+    double eps;          /* accuracy epsilon; used only to derive chains when chains == 0 */
+    double delta;        /* weight cutoff: a chain stops once |W| < delta (tested on the FP32 weight) */
+    double filter_tau;   /* keep |M_ij| >= tau * max_j |M_ij|; 0 disables */
+    double alpha;        /* Eq. 1 augmentation bhat_ii = b_ii + alpha ||B||_inf sgn(b_ii); 0 = none */
+    uint64_t seed;       /* Philox key */
+    int32_t chains;      /* chains N per row (0: from eps and max_i s_i) */
+    int32_t max_len;     /* maximum transitions L per chain (>= 0) */
+    int32_t top_k;       /* keep at most top_k off-diagonals per row; 0 disables */
+    int32_t precision;   /* 32: FP32 weights, Kahan FP32 sums; 64: FP64 weights and sums */
+    int32_t table;       /* MCMI_TABLE_* */
+    int32_t threads;     /* threads per block of the walk kernel (0 = auto; 128 or 256) */
+    int32_t hash_log2;   /* log2 of the on-chip accumulator slots per block (0 = auto) */
+    int32_t reserved;
+    int64_t row_begin;   /* build rows [row_begin, row_end) only; both 0 = all rows */
+    int64_t row_end;
+} mcmi_params;
+
+/* Counters of the last build (all optional outputs).                      */
+typedef struct {
+    uint64_t steps;         /* transitions taken, summed over rows and chains */
+    int64_t rows;           /* rows built */
+    int64_t nnz;            /* entries of M */
+    double max_s;           /* max_i ||c_i||_1 */
+    int32_t chains;         /* N used */
+    int32_t max_len_bound;  /* no chain can take more transitions than this */
+    int32_t table;          /* table type used */
+    int32_t hash_log2;      /* accumulator slots used (log2) */
+    int64_t spilled;        /* accumulator entries that went to the global overflow table */
+    int64_t deferred_rows;  /* rows re-run because the first output buffer was full */
+    float ms_prepare;       /* split + tables (CUDA events on the build stream) */
+    float ms_walk;          /* walk stage incl. overflow-table set-up and deferred rows */
+    float ms_assemble;      /* CSR assembly */
+    float ms_walk_kernel;   /* the first walk kernel launch alone */
+    int32_t launches;       /* kernels this build launched */
+    int32_t reserved;
+} mcmi_stats;
+
+typedef struct mcmi_matrix_s *mcmi_matrix;
+
+/* Defaults: eps 0.01, delta 1e-3, tau 0, alpha 0, seed 1, chains 128,
+ * max_len 256, top_k 0, precision 32, table AUTO, all rows.              */
+void mcmi_params_default(mcmi_params *p);
+
+/* Build M ~ Bhat^-1 restricted to the sparsity the filter keeps (Eq. 2 walks,
+ * phase 4 column scaling, Sec. IV-B filter).  Uses mcmi_params_default for
+ * every parameter not in the argument list.  Synchronises `stream`.
+ * B: device CSR (see conventions).  M_out: receives a library-owned handle
+ * (free with mcmi_free).                                                  */
+mcmi_status mcmi_build(const mcmi_csr *B, double eps, double delta, int32_t chains,
+                       double filter_tau, uint64_t seed, void *stream, mcmi_matrix *M_out);
+
+/* As mcmi_build with every parameter given; `stats` may be NULL.           */
+mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
+                          mcmi_matrix *M_out, mcmi_stats *stats);
+
+/* Device CSR of M (library-owned, valid until mcmi_free): rows
+ * [row_begin, row_end) of the build, columns global, entries sorted by
+ * column, FP32 values.  Any output pointer may be NULL.  Does not sync.    */
+mcmi_status mcmi_matrix_csr(mcmi_matrix M, int64_t *rows, int64_t *row_begin, int64_t *nnz,
+                            const int64_t **row_ptr, const int32_t **col, const float **val);
+
+/* Copy M into caller-owned device buffers: row_ptr int64[rows+1], col
+ * int32[nnz], val float[nnz] (sizes from mcmi_matrix_csr).  Asynchronous
+ * on `stream`.                                                           */
+mcmi_status mcmi_matrix_copy(mcmi_matrix M, int64_t *row_ptr, int32_t *col, float *val, void *stream);
+
+/* y = M x (Sec. III-A: M is applied directly as a preconditioner).
+ * x: device float[n] (global columns); y: device float[rows of M].
+ * Asynchronous on `stream`.                                               */
+mcmi_status mcmi_apply(mcmi_matrix M, const float *x, float *y, void *stream);
+
+/* Release a handle (stream-ordered on the stream it was built on).  NULL ok. */
+void mcmi_free(mcmi_matrix M);
+
+/* Description of the last error on the calling host thread.               */
+const char *mcmi_last_error(void);
+
+/* ---------------------------------------------------------------------
+ * Parity entry points (the same kernels, exposing intermediate results).
+ * --------------------------------------------------------------------- */
+
+/* Unfiltered Eq. 2 estimate of listed rows: for rows[p] (device int64,
+ * nrows of them) writes out_count[p] entries at p*cap .. into out_col
+ * (int32), out_val (float64: (1/N) sum_visits W / d_col, i.e. the row of
+ * D-scaled estimate before filtering) and out_visits (uint32 visit counts),
+ * unsorted, and out_steps[p] = transitions of the row's N chains.
+ * All outputs device.  A row with more than cap entries sets out_count[p]
+ * to -1 and the call returns MCMI_ERR_CAPACITY.  Synchronises `stream`.   */
+mcmi_status mcmi_walk_dump(const mcmi_csr *B, const mcmi_params *p, const int64_t *rows,
+                           int64_t nrows, int64_t cap, int32_t *out_count, uint64_t *out_steps,
+                           int32_t *out_col, double *out_val, uint32_t *out_visits, void *stream);
+
+/* The split and the sampling tables as built for the walk kernel.
+ * out_d, out_s: device float64[n] (d_i, s_i = ||c_i||_1).
+ * out_slot: device uint32[16 n]: the 64-byte row record of each row:
+ *   [0] Q (sum of the row's integer weights; 0 = no transition),
+ *   [1] fl32(s_i) bits, [2] fl32(1/d_i) bits, [3] deg | 0x80000000 if the
+ *   row's table is out of line, [4..15] inline table or [4] = first index of
+ *   the out-of-line table.
+ *   Cumulative inline: up to 6 pairs (T_m, col_m | neg_m << 31), unused
+ *   pairs (0xFFFFFFFF, 0).  Alias inline: up to 4 triples (prob_b,
+ *   col_b | neg_b << 31, alias col | neg << 31).
+ * out_a, out_b, out_c: device uint32[nnz] out-of-line tables (cumulative: a
+ *   = T_m, b = col|neg; alias: a = prob, b = own col|neg, c = alias col|neg),
+ *   row i's table starting at slot[4].  Asynchronous on `stream`.         */
+mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *out_d,
+                              double *out_s, uint32_t *out_slot, uint32_t *out_a,
+                              uint32_t *out_b, uint32_t *out_c, void *stream);
+
+/* Library version string. */
+const char *mcmi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCMI_H */

@@ -1,0 +1,223 @@
+"""Python binding of libmcmi, the B300 (sm_103a) (MC)^2MI preconditioner.
+
+Argument marshalling only: every stage runs in the CUDA kernels of
+``libmcmi.so`` behind the C ABI declared in ``include/mcmi.h``.  PyTorch
+provides device memory and streams.  The names mirror the C entry points.
+There is no CPU fallback: importing this package on a machine without the
+built library raises, and every call needs a CUDA device.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmcmi.so")
+
+MCMI_OK = 0
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_BAD_CSR", 3: "ERR_ZERO_DIAG", 4: "ERR_NOT_CONTRACTIVE",
+          5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_CAPACITY"}
+TABLE_AUTO, TABLE_CUMULATIVE, TABLE_ALIAS = -1, 0, 1
+
+
+class McmiError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mcmi_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p)]
+
+
+class mcmi_params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("delta", C.c_double), ("filter_tau", C.c_double), ("alpha", C.c_double),
+                ("seed", C.c_uint64), ("chains", C.c_int32), ("max_len", C.c_int32), ("top_k", C.c_int32),
+                ("precision", C.c_int32), ("table", C.c_int32), ("threads", C.c_int32), ("hash_log2", C.c_int32),
+                ("reserved", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64)]
+
+
+class mcmi_stats(C.Structure):
+    _fields_ = [("steps", C.c_uint64), ("rows", C.c_int64), ("nnz", C.c_int64), ("max_s", C.c_double),
+                ("chains", C.c_int32), ("max_len_bound", C.c_int32), ("table", C.c_int32), ("hash_log2", C.c_int32),
+                ("spilled", C.c_int64), ("deferred_rows", C.c_int64), ("ms_prepare", C.c_float),
+                ("ms_walk", C.c_float), ("ms_assemble", C.c_float), ("ms_walk_kernel", C.c_float),
+                ("launches", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+_lib = None
+
+
+def load():
+    """Load libmcmi.so from the package directory (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libmcmi.so not built ({LIB_PATH}); run python -m paper_2409_03095_b300.build")
+    lib = C.CDLL(LIB_PATH)
+    P, i32, i64, u64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    lib.mcmi_params_default.argtypes = [C.POINTER(mcmi_params)]
+    lib.mcmi_params_default.restype = None
+    lib.mcmi_build.argtypes = [C.POINTER(mcmi_csr), f64, f64, i32, f64, u64, P, C.POINTER(P)]
+    lib.mcmi_build_ex.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, C.POINTER(P), C.POINTER(mcmi_stats)]
+    lib.mcmi_matrix_csr.argtypes = [P, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64), C.POINTER(P), C.POINTER(P),
+                                    C.POINTER(P)]
+    lib.mcmi_matrix_copy.argtypes = [P, P, P, P, P]
+    lib.mcmi_apply.argtypes = [P, P, P, P]
+    lib.mcmi_free.argtypes = [P]
+    lib.mcmi_free.restype = None
+    lib.mcmi_last_error.restype = C.c_char_p
+    lib.mcmi_version.restype = C.c_char_p
+    lib.mcmi_walk_dump.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, i64, i64, P, P, P, P, P, P]
+    lib.mcmi_debug_tables.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, P, P, P, P, P, P]
+    for f in ("mcmi_build", "mcmi_build_ex", "mcmi_matrix_csr", "mcmi_matrix_copy", "mcmi_apply",
+              "mcmi_walk_dump", "mcmi_debug_tables"):
+        getattr(lib, f).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != MCMI_OK:
+        raise McmiError(st, load().mcmi_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def params(**kw) -> mcmi_params:
+    """mcmi_params with the library defaults, overridden by keyword."""
+    p = mcmi_params()
+    load().mcmi_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class DeviceCsr:
+    """A CSR matrix in device memory (torch tensors) and its mcmi_csr view."""
+
+    def __init__(self, n, row_ptr, col, val):
+        self.n = int(n)
+        self.row_ptr, self.col, self.val = row_ptr, col, val
+        self.c = mcmi_csr(self.n, int(col.numel()), row_ptr.data_ptr(), col.data_ptr(), val.data_ptr())
+
+    @classmethod
+    def from_host(cls, m, device="cuda"):
+        import torch
+        rp = torch.from_numpy(np.ascontiguousarray(m.row_ptr, dtype=np.int64)).to(device)
+        col = torch.from_numpy(np.ascontiguousarray(m.col, dtype=np.int32)).to(device)
+        val = torch.from_numpy(np.ascontiguousarray(m.val, dtype=np.float64)).to(device)
+        return cls(m.n, rp, col, val)
+
+
+class Matrix:
+    """Library-owned preconditioner M (freed with the object or close())."""
+
+    def __init__(self, handle, stats=None):
+        self.h = handle
+        self.stats = stats
+
+    def close(self):
+        if self.h:
+            load().mcmi_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self):
+        rows, rb, nnz = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().mcmi_matrix_csr(self.h, C.byref(rows), C.byref(rb), C.byref(nnz), None, None, None))
+        return rows.value, rb.value, nnz.value
+
+    def to_torch(self, stream=None):
+        """Copy of M as (row_ptr int64, col int32, val float32) CUDA tensors."""
+        import torch
+        rows, rb, nnz = self.shape()
+        rp = torch.empty(rows + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(nnz, 1), dtype=torch.float32, device="cuda")
+        _check(load().mcmi_matrix_copy(self.h, _ptr(rp), _ptr(col), _ptr(val), _stream(stream)))
+        return rp, col[:nnz], val[:nnz]
+
+
+def mcmi_build(B: DeviceCsr, eps, delta, chains, filter_tau, seed, stream=None) -> Matrix:
+    h = C.c_void_p()
+    _check(load().mcmi_build(C.byref(B.c), eps, delta, chains, filter_tau, seed, _stream(stream), C.byref(h)))
+    return Matrix(h)
+
+
+def mcmi_build_ex(B: DeviceCsr, p: mcmi_params, stream=None) -> Matrix:
+    h = C.c_void_p()
+    st = mcmi_stats()
+    _check(load().mcmi_build_ex(C.byref(B.c), C.byref(p), _stream(stream), C.byref(h), C.byref(st)))
+    return Matrix(h, st)
+
+
+def mcmi_apply(M: Matrix, x, y, stream=None):
+    _check(load().mcmi_apply(M.h, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def mcmi_walk_dump(B: DeviceCsr, p: mcmi_params, rows, cap, stream=None):
+    """Unfiltered estimate of the listed rows (parity entry point); returns a
+    list of dicts with col, val (D-scaled), visits, steps (host numpy)."""
+    import torch
+    rows_t = torch.as_tensor(np.asarray(rows, dtype=np.int64)).cuda()
+    nr = rows_t.numel()
+    cnt = torch.zeros(nr, dtype=torch.int32, device="cuda")
+    steps = torch.zeros(nr, dtype=torch.int64, device="cuda")
+    col = torch.zeros(nr * cap, dtype=torch.int32, device="cuda")
+    val = torch.zeros(nr * cap, dtype=torch.float64, device="cuda")
+    vis = torch.zeros(nr * cap, dtype=torch.int32, device="cuda")
+    _check(load().mcmi_walk_dump(C.byref(B.c), C.byref(p), _ptr(rows_t), nr, cap, _ptr(cnt), _ptr(steps),
+                                 _ptr(col), _ptr(val), _ptr(vis), _stream(stream)))
+    cnt, steps = cnt.cpu().numpy(), steps.cpu().numpy().view(np.uint64)
+    col, val, vis = col.cpu().numpy(), val.cpu().numpy(), vis.cpu().numpy().view(np.uint32)
+    out = []
+    for i in range(nr):
+        a, b = i * cap, i * cap + int(cnt[i])
+        o = np.argsort(col[a:b], kind="stable")
+        out.append(dict(col=col[a:b][o], val=val[a:b][o], visits=vis[a:b][o], steps=int(steps[i])))
+    return out
+
+
+def mcmi_debug_tables(B: DeviceCsr, p: mcmi_params, stream=None):
+    import torch
+    n, nnz = B.n, int(B.col.numel())
+    d = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s = torch.zeros(n, dtype=torch.float64, device="cuda")
+    slot = torch.zeros(16 * n, dtype=torch.int32, device="cuda")
+    a = torch.zeros(max(nnz, 1), dtype=torch.int32, device="cuda")
+    b = torch.zeros(max(nnz, 1), dtype=torch.int32, device="cuda")
+    c = torch.zeros(max(nnz, 1), dtype=torch.int32, device="cuda")
+    _check(load().mcmi_debug_tables(C.byref(B.c), C.byref(p), _ptr(d), _ptr(s), _ptr(slot), _ptr(a), _ptr(b),
+                                    _ptr(c), _stream(stream)))
+    torch.cuda.synchronize()
+    u = lambda t: t.cpu().numpy().view(np.uint32)
+    return dict(d=d.cpu().numpy(), s=s.cpu().numpy(), slot=u(slot).reshape(n, 16), a=u(a), b=u(b), c=u(c))
+
+
+def version() -> str:
+    return load().mcmi_version().decode()

@@ -1,0 +1,656 @@
+// C ABI of libmcmi: argument checks, device memory, stage ordering on the
+// caller's stream, and the sizes the host must learn (max_i s_i, nnz of M).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "mcmi.h"
+#include "mcmi_internal.cuh"
+
+using namespace mcmi;
+
+struct mcmi_matrix_s {
+    int64_t rows = 0, row_begin = 0, n_cols = 0, nnz = 0;
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr;
+    float *val = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+mcmi_status fail(mcmi_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+mcmi_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? MCMI_ERR_OOM : MCMI_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// One memory pool per device with a high release threshold, so that repeated
+// builds reuse device memory instead of returning it to the driver.
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[128] = {};
+
+cudaError_t device_pool(int dev, cudaMemPool_t *out)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        cudaError_t e = cudaMemPoolCreate(&p, &props);
+        if (e != cudaSuccess) return e;
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+// Stream-ordered device allocations released together when the owner ends.
+struct Scratch {
+    cudaStream_t s;
+    cudaMemPool_t pool = nullptr;
+    std::vector<void *> ptrs;
+    cudaError_t err = cudaSuccess;
+    explicit Scratch(cudaStream_t st) : s(st)
+    {
+        int dev = 0;
+        err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = device_pool(dev, &pool);
+    }
+    template <class T>
+    T *get(size_t count)
+    {
+        if (err != cudaSuccess) return nullptr;
+        void *p = nullptr;
+        const size_t bytes = count > 0 ? count * sizeof(T) : 16;
+        err = cudaMallocFromPoolAsync(&p, bytes, pool, s);
+        if (err != cudaSuccess) return nullptr;
+        ptrs.push_back(p);
+        return static_cast<T *>(p);
+    }
+    void release(void *p)
+    {
+        for (auto &q : ptrs)
+            if (q == p) {
+                cudaFreeAsync(q, s);
+                q = nullptr;
+            }
+    }
+    // hand ownership of p to the caller
+    void keep(void *p)
+    {
+        for (auto &q : ptrs)
+            if (q == p) q = nullptr;
+    }
+    ~Scratch()
+    {
+        for (void *p : ptrs)
+            if (p) cudaFreeAsync(p, s);
+    }
+};
+
+const char *status_name(int c)
+{
+    switch (c) {
+    case MCMI_ERR_ARG: return "invalid argument";
+    case MCMI_ERR_BAD_CSR: return "malformed CSR (row_ptr, column order/range, or non-finite value)";
+    case MCMI_ERR_ZERO_DIAG: return "zero diagonal after the split (d_i == 0)";
+    case MCMI_ERR_NOT_CONTRACTIVE: return "||c_i||_1 >= 1: the Neumann series need not converge (raise alpha)";
+    case MCMI_ERR_CAPACITY: return "internal capacity exceeded";
+    case MCMI_ERR_TIMEOUT: return "device wait timed out";
+    default: return "error";
+    }
+}
+
+// smallest float >= delta: |w| < delta (in FP64) <=> |w| < delta_f for float w
+float delta_float(double delta)
+{
+    float f = (float)delta;
+    if ((double)f < delta) f = nextafterf(f, INFINITY);
+    return f;
+}
+
+// No chain outlives the FP32 product of fl32(max_i s_i): rounding is monotone.
+int32_t walk_len_bound(double smax, double delta, int32_t L)
+{
+    const float f = (float)smax;
+    if (!(delta > 0.0) || f >= 1.0f) return L;
+    const float df = delta_float(delta);
+    float w = 1.0f;
+    int32_t t = 0;
+    while (t < L && w >= df) {
+        w = w * f;
+        ++t;
+    }
+    return t;
+}
+
+int ceil_log2(uint64_t v)
+{
+    int l = 0;
+    while ((1ull << l) < v) ++l;
+    return l;
+}
+
+struct Prepared {
+    int64_t n = 0, nnz = 0;
+    double *d = nullptr, *s = nullptr;
+    uint4 *slots = nullptr;
+    uint32_t *a = nullptr, *b = nullptr, *c = nullptr;
+    uint4 *bkt = nullptr;
+    double2 *rowd = nullptr;
+    double smax = 0.0;
+    int table = MCMI_TABLE_CUMULATIVE;
+    int32_t N = 0, Lb = 0;
+    DevState *st = nullptr;
+};
+
+mcmi_status check_csr(const mcmi_csr *B)
+{
+    if (!B) return fail(MCMI_ERR_ARG, "B is NULL");
+    if (B->n < 0 || B->nnz < 0) return fail(MCMI_ERR_ARG, "negative size");
+    if (B->n >= (1ll << 31) - 1) return fail(MCMI_ERR_ARG, "n must be below 2^31-1");
+    if (B->nnz >= (1ll << 32)) return fail(MCMI_ERR_ARG, "nnz must be below 2^32");
+    if (B->n > 0 && (!B->row_ptr || (B->nnz > 0 && (!B->col || !B->val))))
+        return fail(MCMI_ERR_ARG, "NULL CSR array");
+    return MCMI_OK;
+}
+
+mcmi_status check_params(const mcmi_params *p)
+{
+    if (!p) return fail(MCMI_ERR_ARG, "params is NULL");
+    if (!(p->delta >= 0.0) || !(p->filter_tau >= 0.0) || !(p->alpha >= 0.0))
+        return fail(MCMI_ERR_ARG, "delta, filter_tau and alpha must be >= 0");
+    if (p->chains < 0 || p->max_len < 0 || p->top_k < 0) return fail(MCMI_ERR_ARG, "negative count");
+    if (p->chains == 0 && !(p->eps > 0.0)) return fail(MCMI_ERR_ARG, "chains == 0 needs eps > 0");
+    if (p->precision != 32 && p->precision != 64) return fail(MCMI_ERR_ARG, "precision must be 32 or 64");
+    if (p->table < -1 || p->table > 1) return fail(MCMI_ERR_ARG, "unknown table type");
+    if (p->threads != 0 && p->threads != 128 && p->threads != 256) return fail(MCMI_ERR_ARG, "threads must be 0, 128 or 256");
+    if (p->hash_log2 != 0 && (p->hash_log2 < 6 || p->hash_log2 > 13)) return fail(MCMI_ERR_ARG, "hash_log2 out of [6, 13]");
+    return MCMI_OK;
+}
+
+mcmi_status read_state(DevState *st, DevState *h, cudaStream_t s)
+{
+    cudaError_t e = cudaMemcpyAsync(h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "device state read");
+    if (h->err != ~0ull) {
+        const int code = (int)(h->err & 0xFF);
+        const long long row = (long long)(h->err >> 8);
+        return fail((mcmi_status)code, "%s (row %lld)", status_name(code), row);
+    }
+    return MCMI_OK;
+}
+
+// Stages a1 + a2: validation, split (FP64), integer tables.
+mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scratch &S, Prepared &P,
+                    bool keep_debug)
+{
+    P.n = B->n;
+    P.nnz = B->nnz;
+    const int64_t n = B->n, nnz = B->nnz;
+    P.st = S.get<DevState>(1);
+    P.d = S.get<double>(n);
+    P.s = S.get<double>(n);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
+    cudaMemsetAsync(P.st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(&P.st->err, 0xFF, sizeof(unsigned long long), s);
+    launch_validate(n, nnz, B->row_ptr, B->col, B->val, P.st, s);
+    DevState h;
+    mcmi_status r = read_state(P.st, &h, s);
+    if (r != MCMI_OK) return r;
+    if (p->alpha > 0.0) launch_rownorm(n, B->row_ptr, B->val, P.st, s);
+    launch_split(n, B->row_ptr, B->col, B->val, p->alpha, P.d, P.s, P.st, s);
+    r = read_state(P.st, &h, s);
+    if (r != MCMI_OK) return r;
+    double smax;
+    memcpy(&smax, &h.smax_bits, sizeof(double));
+    P.smax = smax;
+    // table type: short rows favour the inline cumulative table (one 64-byte
+    // load per step); long rows the alias table (two loads, no search)
+    int table = p->table;
+    if (table == MCMI_TABLE_AUTO) table = (nnz - (int64_t)h.ndiag) <= 6 * n ? MCMI_TABLE_CUMULATIVE : MCMI_TABLE_ALIAS;
+    P.table = table;
+    if (p->chains > 0) {
+        P.N = p->chains;
+    } else {
+        const double v = 0.6745 / (p->eps * (1.0 - smax));
+        const double N = std::ceil(v * v);
+        P.N = N > (double)(1 << 24) ? (1 << 24) : (int32_t)N;
+    }
+    P.Lb = walk_len_bound(smax, p->delta, p->max_len);
+    P.slots = S.get<uint4>((size_t)n * 4);
+    P.a = S.get<uint32_t>(nnz);
+    P.b = S.get<uint32_t>(nnz);
+    unsigned long long *wscr = nullptr;
+    uint32_t *sstk = nullptr, *lstk = nullptr;
+    if (table == MCMI_TABLE_ALIAS || keep_debug) P.c = S.get<uint32_t>(nnz);
+    if (table == MCMI_TABLE_ALIAS) {
+        P.bkt = S.get<uint4>(nnz);
+        wscr = S.get<unsigned long long>(nnz);
+        sstk = S.get<uint32_t>(nnz);
+        lstk = S.get<uint32_t>(nnz);
+    }
+    if (p->precision == 64) P.rowd = S.get<double2>(n);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
+    if (keep_debug) {
+        cudaMemsetAsync(P.a, 0, nnz * 4, s);
+        cudaMemsetAsync(P.b, 0, nnz * 4, s);
+        cudaMemsetAsync(P.c, 0, nnz * 4, s);
+    }
+    launch_tables(n, B->row_ptr, B->col, B->val, P.d, P.s, table, P.slots, P.a, P.b, P.c, P.bkt, wscr, sstk,
+                  lstk, P.rowd, s);
+    if (wscr) S.release(wscr);
+    if (sstk) S.release(sstk);
+    if (lstk) S.release(lstk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "table kernels");
+    return MCMI_OK;
+}
+
+struct WalkPlan {
+    int threads = 256, log2H = 12, log2G = 8, grid = 1;
+};
+
+mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, bool dump, WalkPlan &W)
+{
+    W.threads = p->threads ? p->threads : (P.N >= 256 ? 256 : 128);
+    // distinct columns a row can reach: at most N (Lb + 1) visits, at most n columns
+    const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
+    const uint64_t distinct = reach < (uint64_t)P.n ? reach : (uint64_t)P.n;
+    if (p->hash_log2) {
+        W.log2H = p->hash_log2;
+    } else {
+        int l = ceil_log2((distinct * 5) / 3 + 1);   // on-chip table at most ~60% full
+        W.log2H = l < 8 ? 8 : (l > 12 ? 12 : l);
+    }
+    int l2 = ceil_log2(2 * distinct + 2);
+    W.log2G = l2 < 8 ? 8 : l2;
+    int bps = 0;
+    cudaError_t e = walk_occupancy(p->precision, P.table, dump, W.threads, W.log2H, &bps);
+    if (e != cudaSuccess) return cuda_fail(e, "walk occupancy");
+    if (bps < 1) return fail(MCMI_ERR_ARG, "walk kernel does not fit (threads %d, hash 2^%d)", W.threads, W.log2H);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t grid = (int64_t)sms * bps;
+    if (grid > rows) grid = rows;
+    W.grid = (int)(grid < 1 ? 1 : grid);
+    return MCMI_OK;
+}
+
+void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const WalkPlan &W)
+{
+    memset(&a, 0, sizeof(a));
+    a.slots = P.slots;
+    a.ool_a = P.a;
+    a.ool_b = P.b;
+    a.ool_bkt = P.bkt;
+    a.rowd = P.rowd;
+    a.N = P.N;
+    a.L = p->max_len;
+    a.delta_f = delta_float(p->delta);
+    a.key0 = (uint32_t)p->seed;
+    a.key1 = (uint32_t)(p->seed >> 32);
+    a.log2H = W.log2H;
+    a.log2G = W.log2G;
+    a.tau = p->filter_tau;
+    a.top_k = p->top_k;
+    a.st = P.st;
+}
+
+mcmi_status alloc_overflow(Scratch &S, const WalkPlan &W, WalkArgs &a, cudaStream_t s)
+{
+    const size_t G = (size_t)W.grid << W.log2G;
+    a.g_keys = S.get<uint32_t>(G);
+    a.g_vals = S.get<unsigned long long>(G);
+    a.g_cnt = S.get<uint32_t>(G);
+    a.g_list = S.get<uint32_t>(G);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (overflow table)");
+    cudaMemsetAsync(a.g_keys, 0xFF, G * 4, s);
+    cudaMemsetAsync(a.g_vals, 0, G * 8, s);
+    cudaMemsetAsync(a.g_cnt, 0, G * 4, s);
+    return MCMI_OK;
+}
+
+void reset_queue(DevState *st, cudaStream_t s)
+{
+    cudaMemsetAsync(&st->work, 0, sizeof(unsigned long long), s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mcmi_last_error(void) { return g_err.c_str(); }
+
+const char *mcmi_version(void) { return "mcmi-b300 0.1 (sm_103a)"; }
+
+void mcmi_params_default(mcmi_params *p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->eps = 0.01;
+    p->delta = 1e-3;
+    p->filter_tau = 0.0;
+    p->alpha = 0.0;
+    p->seed = 1;
+    p->chains = 128;
+    p->max_len = 256;
+    p->top_k = 0;
+    p->precision = 32;
+    p->table = MCMI_TABLE_AUTO;
+}
+
+mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream, mcmi_matrix *M_out,
+                          mcmi_stats *stats)
+{
+    if (!M_out) return fail(MCMI_ERR_ARG, "M_out is NULL");
+    *M_out = nullptr;
+    mcmi_status r = check_csr(B);
+    if (r == MCMI_OK) r = check_params(p);
+    if (r != MCMI_OK) return r;
+    const int64_t n = B->n;
+    const int64_t rb = (p->row_begin == 0 && p->row_end == 0) ? 0 : p->row_begin;
+    const int64_t re = (p->row_begin == 0 && p->row_end == 0) ? n : p->row_end;
+    if (rb < 0 || re < rb || re > n) return fail(MCMI_ERR_ARG, "row range [%lld, %lld) outside [0, %lld)",
+                                                 (long long)rb, (long long)re, (long long)n);
+    const int64_t rows = re - rb;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    mcmi_matrix M = new mcmi_matrix_s();
+    M->rows = rows;
+    M->row_begin = rb;
+    M->n_cols = n;
+    M->stream = s;
+    cudaGetDevice(&M->device);
+    auto give_up = [&](mcmi_status st) {
+        if (M->rp) cudaFreeAsync(M->rp, s);
+        if (M->col) cudaFreeAsync(M->col, s);
+        if (M->val) cudaFreeAsync(M->val, s);
+        delete M;
+        return st;
+    };
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (n == 0 || rows == 0) {
+        M->rp = S.get<int64_t>(rows + 1);
+        if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation"));
+        S.keep(M->rp);
+        cudaMemsetAsync(M->rp, 0, (rows + 1) * sizeof(int64_t), s);
+        cudaStreamSynchronize(s);
+        *M_out = M;
+        return MCMI_OK;
+    }
+    cudaEvent_t ev[6];
+    for (auto &e : ev) cudaEventCreate(&e);
+    struct EvGuard { cudaEvent_t *e; ~EvGuard() { for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]); } } evg{ev};
+    int launches = 3 + (p->alpha > 0.0 ? 1 : 0);   // validate, split, tables (+ row norms)
+    cudaEventRecord(ev[0], s);
+
+    Prepared P;
+    r = prepare(B, p, s, S, P, false);
+    if (r != MCMI_OK) return give_up(r);
+    cudaEventRecord(ev[1], s);
+
+    WalkPlan W;
+    r = plan_walk(p, P, rows, false, W);
+    if (r != MCMI_OK) return give_up(r);
+    WalkArgs a;
+    fill_walk_args(a, p, P, W);
+    a.row_begin = rb;
+    a.row_end = re;
+    r = alloc_overflow(S, W, a, s);
+    if (r != MCMI_OK) return give_up(r);
+    const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
+    const uint64_t distinct = reach < (uint64_t)n ? reach : (uint64_t)n;
+    uint64_t cap = p->top_k > 0 ? (uint64_t)rows * (uint64_t)(p->top_k + 1) : (uint64_t)rows * 24 + 1024;
+    if (p->top_k > 0 && (uint64_t)(p->top_k + 1) > distinct) cap = (uint64_t)rows * distinct;
+    a.st_col = S.get<uint32_t>(cap);
+    a.st_val = S.get<float>(cap);
+    a.st_cap = cap;
+    a.row_off = S.get<int64_t>(rows);
+    a.row_cnt = S.get<int32_t>(rows);
+    a.deferred_list = S.get<int64_t>(rows);
+    if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (staging)"));
+    reset_queue(P.st, s);
+    cudaEventRecord(ev[4], s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, false, W.grid, W.threads, s);
+    if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch"));
+    cudaEventRecord(ev[5], s);
+    ++launches;
+    DevState h;
+    r = read_state(P.st, &h, s);
+    if (r != MCMI_OK) return give_up(r);
+    int64_t deferred = (int64_t)h.deferred;
+    if (deferred > 0) {
+        // rows that found the staging buffer full run again (same seed, so the
+        // same walks) into a buffer large enough for any row
+        const uint64_t need = h.cursor + (uint64_t)deferred * (distinct + 1);
+        uint32_t *col2 = S.get<uint32_t>(need);
+        float *val2 = S.get<float>(need);
+        int64_t *list2 = S.get<int64_t>(deferred);
+        if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (staging regrowth)"));
+        cudaMemcpyAsync(col2, a.st_col, cap * 4, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(val2, a.st_val, cap * 4, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(list2, a.deferred_list, deferred * 8, cudaMemcpyDeviceToDevice, s);
+        S.release(a.st_col);
+        S.release(a.st_val);
+        a.st_col = col2;
+        a.st_val = val2;
+        a.st_cap = need;
+        a.row_list = list2;
+        a.n_list = deferred;
+        a.out_by_row = 1;
+        cudaMemsetAsync(&P.st->deferred, 0, 8, s);
+        reset_queue(P.st, s);
+        WalkPlan W2 = W;
+        W2.grid = (int)(deferred < W.grid ? deferred : W.grid);
+        e = launch_walk(a, p->precision, P.table, false, W2.grid, W2.threads, s);
+        if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch (deferred rows)"));
+        ++launches;
+        r = read_state(P.st, &h, s);
+        if (r != MCMI_OK) return give_up(r);
+        if (h.deferred) return give_up(fail(MCMI_ERR_CAPACITY, "staging buffer still full"));
+    }
+    cudaEventRecord(ev[2], s);
+
+    M->rp = S.get<int64_t>(rows + 1);
+    int64_t *tmp = S.get<int64_t>(scan_tmp_elems(rows));
+    if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (row_ptr)"));
+    S.keep(M->rp);
+    e = scan_counts(a.row_cnt, rows, M->rp, tmp, s);
+    if (e != cudaSuccess) return give_up(cuda_fail(e, "scan"));
+    int64_t nnzM = 0;
+    e = cudaMemcpyAsync(&nnzM, M->rp + rows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return give_up(cuda_fail(e, "nnz read"));
+    M->nnz = nnzM;
+    M->col = S.get<int32_t>(nnzM);
+    M->val = S.get<float>(nnzM);
+    if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (M)"));
+    S.keep(M->col);
+    S.keep(M->val);
+    e = launch_assemble(rows, M->rp, a.row_off, a.row_cnt, a.st_col, a.st_val, M->col, M->val, s);
+    if (e != cudaSuccess) return give_up(cuda_fail(e, "assembly"));
+    launches += 4;   // three scan kernels + assembly
+    cudaEventRecord(ev[3], s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return give_up(cuda_fail(e, "build"));
+    if (stats) {
+        stats->steps = h.steps;
+        stats->rows = rows;
+        stats->nnz = nnzM;
+        stats->max_s = P.smax;
+        stats->chains = P.N;
+        stats->max_len_bound = P.Lb;
+        stats->table = P.table;
+        stats->hash_log2 = W.log2H;
+        stats->spilled = (int64_t)h.spilled;
+        stats->deferred_rows = deferred;
+        cudaEventElapsedTime(&stats->ms_prepare, ev[0], ev[1]);
+        cudaEventElapsedTime(&stats->ms_walk, ev[1], ev[2]);
+        cudaEventElapsedTime(&stats->ms_assemble, ev[2], ev[3]);
+        cudaEventElapsedTime(&stats->ms_walk_kernel, ev[4], ev[5]);
+        stats->launches = launches;
+    }
+    *M_out = M;
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_build(const mcmi_csr *B, double eps, double delta, int32_t chains, double filter_tau,
+                       uint64_t seed, void *stream, mcmi_matrix *M_out)
+{
+    mcmi_params p;
+    mcmi_params_default(&p);
+    p.eps = eps;
+    p.delta = delta;
+    p.chains = chains;
+    p.filter_tau = filter_tau;
+    p.seed = seed;
+    return mcmi_build_ex(B, &p, stream, M_out, nullptr);
+}
+
+mcmi_status mcmi_matrix_csr(mcmi_matrix M, int64_t *rows, int64_t *row_begin, int64_t *nnz,
+                            const int64_t **row_ptr, const int32_t **col, const float **val)
+{
+    if (!M) return fail(MCMI_ERR_ARG, "M is NULL");
+    if (rows) *rows = M->rows;
+    if (row_begin) *row_begin = M->row_begin;
+    if (nnz) *nnz = M->nnz;
+    if (row_ptr) *row_ptr = M->rp;
+    if (col) *col = M->col;
+    if (val) *val = M->val;
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_matrix_copy(mcmi_matrix M, int64_t *row_ptr, int32_t *col, float *val, void *stream)
+{
+    if (!M) return fail(MCMI_ERR_ARG, "M is NULL");
+    if (!row_ptr || (M->nnz > 0 && (!col || !val))) return fail(MCMI_ERR_ARG, "NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(row_ptr, M->rp, (M->rows + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && M->nnz > 0)
+        e = cudaMemcpyAsync(col, M->col, M->nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess && M->nnz > 0)
+        e = cudaMemcpyAsync(val, M->val, M->nnz * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "matrix copy");
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_apply(mcmi_matrix M, const float *x, float *y, void *stream)
+{
+    if (!M) return fail(MCMI_ERR_ARG, "M is NULL");
+    if (M->rows > 0 && (!x || !y)) return fail(MCMI_ERR_ARG, "NULL vector");
+    if (M->rows == 0) return MCMI_OK;
+    cudaError_t e = launch_spmv(M->rows, M->rp, M->col, M->val, x, y, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "apply");
+    return MCMI_OK;
+}
+
+void mcmi_free(mcmi_matrix M)
+{
+    if (!M) return;
+    if (M->rp) cudaFreeAsync(M->rp, M->stream);
+    if (M->col) cudaFreeAsync(M->col, M->stream);
+    if (M->val) cudaFreeAsync(M->val, M->stream);
+    delete M;
+}
+
+mcmi_status mcmi_walk_dump(const mcmi_csr *B, const mcmi_params *p, const int64_t *rows, int64_t nrows,
+                           int64_t cap, int32_t *out_count, uint64_t *out_steps, int32_t *out_col,
+                           double *out_val, uint32_t *out_visits, void *stream)
+{
+    mcmi_status r = check_csr(B);
+    if (r == MCMI_OK) r = check_params(p);
+    if (r != MCMI_OK) return r;
+    if (nrows < 0 || cap < 1) return fail(MCMI_ERR_ARG, "nrows < 0 or cap < 1");
+    if (nrows == 0) return MCMI_OK;
+    if (!rows || !out_count || !out_steps || !out_col || !out_val || !out_visits)
+        return fail(MCMI_ERR_ARG, "NULL output");
+    if (B->n == 0) return fail(MCMI_ERR_ARG, "rows listed for an empty matrix");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    Prepared P;
+    r = prepare(B, p, s, S, P, false);
+    if (r != MCMI_OK) return r;
+    WalkPlan W;
+    r = plan_walk(p, P, nrows, true, W);
+    if (r != MCMI_OK) return r;
+    WalkArgs a;
+    fill_walk_args(a, p, P, W);
+    a.row_list = rows;
+    a.n_list = nrows;
+    a.row_begin = 0;
+    a.row_end = B->n;
+    a.out_by_row = 0;
+    r = alloc_overflow(S, W, a, s);
+    if (r != MCMI_OK) return r;
+    a.d_count = out_count;
+    a.d_col = out_col;
+    a.d_val = out_val;
+    a.d_vis = out_visits;
+    a.d_cap = cap;
+    a.row_steps = out_steps;
+    reset_queue(P.st, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, true, W.grid, W.threads, s);
+    if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
+    DevState h;
+    return read_state(P.st, &h, s);
+}
+
+mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *out_d, double *out_s,
+                              uint32_t *out_slot, uint32_t *out_a, uint32_t *out_b, uint32_t *out_c,
+                              void *stream)
+{
+    mcmi_status r = check_csr(B);
+    if (r == MCMI_OK) r = check_params(p);
+    if (r != MCMI_OK) return r;
+    if (B->n == 0) return MCMI_OK;
+    if (!out_d || !out_s || !out_slot || !out_a || !out_b || !out_c) return fail(MCMI_ERR_ARG, "NULL output");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    Prepared P;
+    r = prepare(B, p, s, S, P, true);
+    if (r != MCMI_OK) return r;
+    const int64_t n = B->n, nnz = B->nnz;
+    cudaMemcpyAsync(out_d, P.d, n * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(out_s, P.s, n * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(out_slot, P.slots, n * 64, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(out_a, P.a, nnz * 4, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(out_b, P.b, nnz * 4, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(out_c, P.c, nnz * 4, cudaMemcpyDeviceToDevice, s);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "table export");
+    return MCMI_OK;
+}
+
+}  // extern "C"

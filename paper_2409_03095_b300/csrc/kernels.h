@@ -1,0 +1,36 @@
+// Host-side launchers of libmcmi's kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mcmi_internal.cuh"
+
+namespace mcmi {
+
+void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col, const double *val,
+                     DevState *st, cudaStream_t s);
+void launch_rownorm(int64_t n, const int64_t *rp, const double *val, DevState *st, cudaStream_t s);
+void launch_split(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double alpha,
+                  double *d, double *sv, DevState *st, cudaStream_t s);
+void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
+                   const double *sv, int table, uint4 *slots, uint32_t *a, uint32_t *b, uint32_t *c,
+                   uint4 *bkt, unsigned long long *wscr, uint32_t *sstk, uint32_t *lstk, double2 *rowd,
+                   cudaStream_t s);
+
+size_t walk_smem_bytes(int log2H, bool dump);
+cudaError_t walk_occupancy(int precision, int table, bool dump, int threads, int log2H, int *blocks_per_sm);
+cudaError_t launch_walk(const WalkArgs &a, int precision, int table, bool dump, int grid, int threads,
+                        cudaStream_t s);
+
+// exclusive scan of int32 counts into int64 offsets (out has n+1 entries)
+cudaError_t scan_counts(const int32_t *counts, int64_t n, int64_t *out, int64_t *block_tmp, cudaStream_t s);
+size_t scan_tmp_elems(int64_t n);
+
+cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t *st_off, const int32_t *st_cnt,
+                            const uint32_t *st_col, const float *st_val, int32_t *out_col, float *out_val,
+                            cudaStream_t s);
+cudaError_t launch_spmv(int64_t rows, const int64_t *rp, const int32_t *col, const float *val, const float *x,
+                        float *y, cudaStream_t s);
+
+}  // namespace mcmi

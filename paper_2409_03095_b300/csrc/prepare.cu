@@ -1,0 +1,244 @@
+// Stage a1 + a2 of the hot path: CSR validation, the Eq. 1 split with
+// Jacobi scaling (FP64), and the per-row integer sampling tables.
+#include "mcmi_internal.cuh"
+#include "kernels.h"
+
+namespace mcmi {
+
+// One thread per row: row_ptr bounds, strictly increasing in-range columns,
+// finite values.
+__global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, const double *__restrict__ val,
+                           DevState *st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = rp[i], b = rp[i + 1];
+        if (i == 0 && a != 0) report(st, 0, MCMI_ERR_BAD_CSR);
+        if (i == n - 1 && b != nnz) report(st, i, MCMI_ERR_BAD_CSR);
+        if (a < 0 || b < a || b > nnz) {
+            report(st, i, MCMI_ERR_BAD_CSR);
+            continue;
+        }
+        int64_t prev = -1;
+        bool diag = false;
+        for (int64_t k = a; k < b; ++k) {
+            const int64_t c = col[k];
+            if (c < 0 || c >= n || c <= prev) report(st, i, MCMI_ERR_BAD_CSR);
+            if (!isfinite(val[k])) report(st, i, MCMI_ERR_BAD_CSR);
+            diag |= (c == i);
+            prev = c;
+        }
+        if (diag) atomicAdd(&st->ndiag, 1ull);
+    }
+}
+
+// ||B||_inf for the Eq. 1 augmentation.
+__global__ void k_rownorm(int64_t n, const int64_t *__restrict__ rp, const double *__restrict__ val,
+                          DevState *st)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double r = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) r = __dadd_rn(r, fabs(val[k]));
+        atomicMax(&st->bnorm_bits, (unsigned long long)__double_as_longlong(r));
+    }
+}
+
+// Eq. 1 + Jacobi scaling: d_i = b_ii + alpha ||B|| sgn(b_ii), c_ij = -b_ij/d_i,
+// s_i = sum_j |c_ij| in CSR order (explicitly rounded operations, no FMA).
+__global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                        const double *__restrict__ val, double alpha, double *__restrict__ d,
+                        double *__restrict__ s, DevState *st)
+{
+    const double bnorm = __longlong_as_double((long long)st->bnorm_bits);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = rp[i], b = rp[i + 1];
+        double bii = 0.0;
+        for (int64_t k = a; k < b; ++k)
+            if (col[k] == i) bii = val[k];
+        double di = bii;
+        if (alpha > 0.0) di = __dadd_rn(bii, __dmul_rn(__dmul_rn(alpha, bnorm), bii < 0.0 ? -1.0 : 1.0));
+        if (di == 0.0) {
+            report(st, i, MCMI_ERR_ZERO_DIAG);
+            d[i] = 0.0;
+            s[i] = 0.0;
+            continue;
+        }
+        double si = 0.0;
+        for (int64_t k = a; k < b; ++k) {
+            if (col[k] == i) continue;
+            si = __dadd_rn(si, fabs(__ddiv_rn(-val[k], di)));
+        }
+        d[i] = di;
+        s[i] = si;
+        if (!(si < 1.0)) report(st, i, MCMI_ERR_NOT_CONTRACTIVE);
+        atomicMax(&st->smax_bits, (unsigned long long)__double_as_longlong(si));
+    }
+}
+
+// Integer weight of one entry: max(1, floor(|c|/s 2^31)); 0 if c == 0.
+__device__ __forceinline__ uint32_t entry_weight(double b, double di, double si, bool *neg)
+{
+    const double c = __ddiv_rn(-b, di);
+    *neg = c < 0.0;
+    if (c == 0.0 || !(si > 0.0)) return 0u;
+    const double x = floor(__dmul_rn(__ddiv_rn(fabs(c), si), 2147483648.0));
+    const uint32_t q = (uint32_t)x;
+    return q < 1u ? 1u : q;
+}
+
+// One thread per row: the 64-byte slot (header + inline table) or the
+// out-of-line table at [row_ptr[i], row_ptr[i] + deg).
+//   cumulative: T_m = q_0 + ... + q_m; a draw x = floor(r Q / 2^32) picks
+//               the smallest m with x < T_m.
+//   alias:      Walker/Vose over weights q_j * deg with bucket capacity Q;
+//               LIFO work lists filled in CSR order.
+__global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                         const double *__restrict__ val, const double *__restrict__ d,
+                         const double *__restrict__ s, int table, uint4 *__restrict__ slots,
+                         uint32_t *__restrict__ ool_a, uint32_t *__restrict__ ool_b,
+                         uint32_t *__restrict__ ool_c, uint4 *__restrict__ ool_bkt,
+                         unsigned long long *__restrict__ wscratch,
+                         uint32_t *__restrict__ small_stk, uint32_t *__restrict__ large_stk,
+                         double2 *__restrict__ rowd)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = rp[i], b = rp[i + 1];
+        const double di = d[i], si = s[i];
+        uint32_t w[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) w[k] = 0u;
+        // pass 1: degree and total mass
+        uint32_t deg = 0;
+        unsigned long long Q = 0;
+        for (int64_t k = a; k < b; ++k) {
+            if (col[k] == i) continue;
+            bool ng;
+            Q += entry_weight(val[k], di, si, &ng);
+            ++deg;
+        }
+        w[0] = (uint32_t)Q;
+        w[1] = __float_as_uint(__double2float_rn(si));
+        w[2] = __float_as_uint(__double2float_rn(__ddiv_rn(1.0, di)));
+        if (rowd) rowd[i] = make_double2(si, __ddiv_rn(1.0, di));
+        const uint32_t begin = (uint32_t)a;
+        if (table == MCMI_TABLE_CUMULATIVE) {
+            const bool inl = deg <= (uint32_t)kInlineCum;
+            w[3] = deg | (inl ? 0u : kOolFlag);
+            if (inl) {
+#pragma unroll
+                for (int m = 0; m < kInlineCum; ++m) { w[4 + 2 * m] = 0xFFFFFFFFu; w[5 + 2 * m] = 0u; }
+            } else {
+                w[4] = begin;
+            }
+            uint32_t T = 0, m = 0;
+            for (int64_t k = a; k < b; ++k) {
+                if (col[k] == i) continue;
+                bool ng;
+                T += entry_weight(val[k], di, si, &ng);
+                const uint32_t cs = (uint32_t)col[k] | (ng ? kNegBit : 0u);
+                if (inl) {
+                    // unrolled store into the register array (m < 6)
+#pragma unroll
+                    for (int u = 0; u < kInlineCum; ++u)
+                        if (u == (int)m) { w[4 + 2 * u] = T; w[5 + 2 * u] = cs; }
+                } else {
+                    ool_a[begin + m] = T;
+                    ool_b[begin + m] = cs;
+                }
+                ++m;
+            }
+        } else {
+            const bool inl = deg <= (uint32_t)kInlineAlias;
+            w[3] = deg | (inl ? 0u : kOolFlag);
+            if (!inl) w[4] = begin;
+            // weights q_j * deg and the two LIFO lists (scratch at [begin, begin+deg))
+            uint32_t ns = 0, nl = 0, m = 0;
+            for (int64_t k = a; k < b; ++k) {
+                if (col[k] == i) continue;
+                bool ng;
+                const unsigned long long wj = (unsigned long long)entry_weight(val[k], di, si, &ng) * deg;
+                wscratch[begin + m] = wj;
+                ool_b[begin + m] = (uint32_t)col[k] | (ng ? kNegBit : 0u);  // own col|sign (CSR order)
+                if (wj < Q) small_stk[begin + ns++] = m; else large_stk[begin + nl++] = m;
+                ++m;
+            }
+            while (ns > 0 && nl > 0) {
+                const uint32_t sm = small_stk[begin + --ns];
+                const uint32_t lg = large_stk[begin + --nl];
+                const unsigned long long ws = wscratch[begin + sm];
+                ool_a[begin + sm] = (uint32_t)ws;
+                ool_c[begin + sm] = lg;                       // alias as a row-local index for now
+                const unsigned long long wl = wscratch[begin + lg] - (Q - ws);
+                wscratch[begin + lg] = wl;
+                if (wl < Q) small_stk[begin + ns++] = lg; else large_stk[begin + nl++] = lg;
+            }
+            while (nl > 0) { const uint32_t lg = large_stk[begin + --nl]; ool_a[begin + lg] = (uint32_t)Q; ool_c[begin + lg] = lg; }
+            while (ns > 0) { const uint32_t sm = small_stk[begin + --ns]; ool_a[begin + sm] = (uint32_t)Q; ool_c[begin + sm] = sm; }
+            // alias index -> alias col|sign; inline copy for short rows
+            for (uint32_t bkt = 0; bkt < deg; ++bkt) {
+                const uint32_t al = ool_b[begin + ool_c[begin + bkt]];
+                if (inl) {
+#pragma unroll
+                    for (int u = 0; u < kInlineAlias; ++u)
+                        if (u == (int)bkt) {
+                            w[4 + 3 * u] = ool_a[begin + bkt];
+                            w[5 + 3 * u] = ool_b[begin + bkt];
+                            w[6 + 3 * u] = al;
+                        }
+                } else {
+                    wscratch[begin + bkt] = al;   // stash: ool_c is still read as an index below
+                }
+            }
+            if (!inl)
+                for (uint32_t bkt = 0; bkt < deg; ++bkt) {
+                    ool_c[begin + bkt] = (uint32_t)wscratch[begin + bkt];
+                    ool_bkt[begin + bkt] = make_uint4(ool_a[begin + bkt], ool_b[begin + bkt], ool_c[begin + bkt], 0u);
+                }
+        }
+        uint4 *o = slots + 4 * i;
+        o[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        o[1] = make_uint4(w[4], w[5], w[6], w[7]);
+        o[2] = make_uint4(w[8], w[9], w[10], w[11]);
+        o[3] = make_uint4(w[12], w[13], w[14], w[15]);
+    }
+}
+
+void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col, const double *val,
+                     DevState *st, cudaStream_t s)
+{
+    const int bs = 256;
+    const int64_t g = (n + bs - 1) / bs;
+    k_validate<<<(unsigned)(g < 148 * 32 ? g : 148 * 32), bs, 0, s>>>(n, nnz, rp, col, val, st);
+}
+
+void launch_rownorm(int64_t n, const int64_t *rp, const double *val, DevState *st, cudaStream_t s)
+{
+    const int bs = 256;
+    const int64_t g = (n + bs - 1) / bs;
+    k_rownorm<<<(unsigned)(g < 148 * 32 ? g : 148 * 32), bs, 0, s>>>(n, rp, val, st);
+}
+
+void launch_split(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double alpha,
+                  double *d, double *sv, DevState *st, cudaStream_t s)
+{
+    const int bs = 256;
+    const int64_t g = (n + bs - 1) / bs;
+    k_split<<<(unsigned)(g < 148 * 32 ? g : 148 * 32), bs, 0, s>>>(n, rp, col, val, alpha, d, sv, st);
+}
+
+void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
+                   const double *sv, int table, uint4 *slots, uint32_t *a, uint32_t *b, uint32_t *c,
+                   uint4 *bkt, unsigned long long *wscr, uint32_t *sstk, uint32_t *lstk, double2 *rowd,
+                   cudaStream_t s)
+{
+    const int bs = 128;
+    const int64_t g = (n + bs - 1) / bs;
+    k_tables<<<(unsigned)(g < 148 * 64 ? g : 148 * 64), bs, 0, s>>>(n, rp, col, val, d, sv, table, slots, a,
+                                                                     b, c, bkt, wscr, sstk, lstk, rowd);
+}
+
+}  // namespace mcmi

@@ -302,6 +302,8 @@ WORKLOADS = {
                             delta=1e-3, max_len=64, tau=1e-2, top_k=0),
     "stencil3d_64": dict(gen=lambda: stencil3d_7pt(64, seed=1002), chains=256,
                          delta=1e-2, max_len=128, tau=0.0, top_k=16),
+    "stencil3d_32": dict(gen=lambda: stencil3d_7pt(32, seed=1002), chains=256,
+                         delta=1e-2, max_len=128, tau=0.0, top_k=16),
     "powerlaw_1m": dict(gen=lambda: powerlaw_random(1 << 20, seed=1003), chains=128,
                         delta=1e-3, max_len=256, tau=5e-3, top_k=0),
 }

@@ -1,0 +1,293 @@
+"""CUDA path vs the CPU oracle, through the C ABI.
+
+Bit-exact: the split (d, s), the integer tables, every walk's visited
+columns, visit counts and transition counts.  Floating point: entries within
+1e-5 relative (bounded by (1/N) sum |W| / |d_j| where signed weights cancel).
+Filtered patterns equal except entries inside the rounding band of a cut.
+"""
+import numpy as np
+import pytest
+
+import synth
+from tests import _parity as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2409_03095_b300 as mc  # noqa: E402
+
+
+def _orc():
+    import oracle
+    return oracle
+
+
+def _cases_small():
+    return {
+        "rand_mixed": synth.random_dd(300, 5, seed=1, diag_sign="mixed", zero_frac=0.1, dominance=0.85),
+        "rand_long": synth.random_dd(500, 23, seed=2, dominance=0.8, dominance_jitter=0.3),
+        "stencil2d": synth.stencil2d_5pt(32, 32, seed=1001),
+        "stencil3d_12": synth.stencil3d_7pt(12, seed=7),
+        "powerlaw_4k": synth.powerlaw_random(4096, seed=3),
+    }
+
+
+# ------------------------------------------------------------------ tables
+
+
+@pytest.mark.parametrize("name", list(_cases_small()))
+@pytest.mark.parametrize("table", [0, 1])
+def test_tables_bit_exact(name, table):
+    orc = _orc()
+    m = _cases_small()[name]
+    B = mc.DeviceCsr.from_host(m)
+    g = mc.mcmi_debug_tables(B, mc.params(table=table))
+    d, s = orc.split(m)
+    assert np.array_equal(g["d"], d) and np.array_equal(g["s"], s)
+    tb = orc.tables(m, d, s, alias=table == 1)
+    slot = g["slot"]
+    assert np.array_equal(slot[:, 0], tb["Q"].astype(np.uint32))
+    assert np.array_equal(slot[:, 1], s.astype(np.float32).view(np.uint32))
+    assert np.array_equal(slot[:, 2], (1.0 / d).astype(np.float32).view(np.uint32))
+    for i in range(m.n):
+        a, b = tb["off"][i], tb["off"][i + 1]
+        deg = b - a
+        cols = np.array([c for c in m.col[m.row_ptr[i]:m.row_ptr[i + 1]] if c != i], dtype=np.int64)
+        vals = np.array([v for c, v in zip(m.col[m.row_ptr[i]:m.row_ptr[i + 1]], m.val[m.row_ptr[i]:m.row_ptr[i + 1]]) if c != i])
+        cs = (cols | np.where(-vals / d[i] < 0, 1 << 31, 0)).astype(np.uint32)
+        inline = deg <= (6 if table == 0 else 4)
+        assert slot[i, 3] == (deg | (0 if inline else 1 << 31))
+        if table == 0:
+            T = np.cumsum(tb["q"][a:b].astype(np.uint64)).astype(np.uint32)
+            if inline:
+                assert np.array_equal(slot[i, 4:4 + 2 * deg:2], T) and np.array_equal(slot[i, 5:5 + 2 * deg:2], cs)
+                assert np.all(slot[i, 4 + 2 * deg:16:2] == 0xFFFFFFFF)
+            else:
+                o = slot[i, 4]
+                assert np.array_equal(g["a"][o:o + deg], T) and np.array_equal(g["b"][o:o + deg], cs)
+        else:
+            prob, al = tb["prob"][a:b], tb["alias"][a:b]
+            if inline:
+                got = slot[i, 4:4 + 3 * deg].reshape(deg, 3) if deg else np.zeros((0, 3), np.uint32)
+            else:
+                o = slot[i, 4]
+                got = np.stack([g["a"][o:o + deg], g["b"][o:o + deg], g["c"][o:o + deg]], axis=1)
+            assert np.array_equal(got[:, 0], prob) and np.array_equal(got[:, 1], cs) and np.array_equal(got[:, 2], cs[al])
+
+
+# ------------------------------------------------------------------ walks
+
+
+WALK_CASES = [
+    # name, precision, table, N, L, delta, extra params
+    ("stencil2d", 64, 0, 1000, 64, 1e-3, {}),
+    ("stencil2d", 32, 0, 1000, 64, 1e-3, {}),
+    ("stencil3d_12", 32, 0, 256, 128, 1e-2, {}),
+    ("stencil3d_12", 32, 1, 256, 128, 1e-2, {}),
+    ("rand_mixed", 32, 0, 300, 80, 1e-4, {}),
+    ("rand_mixed", 64, 1, 100, 80, 1e-4, {}),
+    ("rand_long", 32, 1, 128, 256, 1e-3, {}),
+    ("rand_long", 32, 0, 128, 256, 1e-3, {"threads": 256}),
+    ("powerlaw_4k", 32, 1, 128, 256, 1e-3, {}),
+    ("powerlaw_4k", 32, 0, 128, 256, 1e-3, {"hash_log2": 6}),      # forces the global overflow table
+    ("stencil2d", 32, 0, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 128}),
+]
+
+
+@pytest.mark.parametrize("case", WALK_CASES, ids=lambda c: f"{c[0]}-fp{c[1]}-t{c[2]}-{c[6]}")
+def test_walk_paths_and_visits_bit_exact(case):
+    orc = _orc()
+    name, prec, table, N, L, delta, extra = case
+    m = _cases_small()[name]
+    rng = np.random.default_rng(5)
+    rows = np.unique(np.concatenate([[0, m.n - 1], rng.choice(m.n, min(m.n, 48), replace=False)]))
+    seed = 0x5EED0000 + N
+    B = mc.DeviceCsr.from_host(m)
+    p = mc.params(chains=N, max_len=L, delta=delta, seed=seed, precision=prec, table=table, **extra)
+    orows, d, s = orc.walk(m, rows=rows, chains=N, max_len=L, delta=delta, seed=seed, table=table)
+    cap = max(len(r["col"]) for r in orows) + 16
+    grows = mc.mcmi_walk_dump(B, p, rows, cap)
+    mx, med, bounded = P.compare_dump(grows, orows, d)
+    print(f"{name} fp{prec} table{table}: max rel {mx:.2e} median {med:.2e} bounded {bounded:.3f}")
+    assert bounded <= 1.0
+
+
+def test_sharded_rows_equal_one_launch():
+    """Counter-keyed RNG: a row's walks do not depend on which launch, block
+    or row subset it runs in."""
+    m = _cases_small()["rand_long"]
+    B = mc.DeviceCsr.from_host(m)
+    p = mc.params(chains=200, max_len=100, delta=1e-3, seed=9, table=1)
+    a = mc.mcmi_walk_dump(B, p, np.arange(m.n), 4000)
+    b = mc.mcmi_walk_dump(B, p, np.arange(m.n)[::-1].copy(), 4000)[::-1]
+    c = mc.mcmi_walk_dump(B, p, np.arange(7, 19), 4000)
+    for x, y in zip(a, b):
+        assert np.array_equal(x["col"], y["col"]) and np.array_equal(x["visits"], y["visits"])
+        # FP32 compensated sums in a timing-dependent order: equal up to a few
+        # ulps of the row's largest partial sums (entries may cancel)
+        assert np.allclose(x["val"], y["val"], rtol=1e-6, atol=1e-6 * np.abs(x["val"]).max())
+    for k, r in enumerate(c):
+        assert np.array_equal(r["col"], a[7 + k]["col"]) and np.array_equal(r["visits"], a[7 + k]["visits"])
+
+
+# ------------------------------------------------------------------ build (filter + CSR)
+
+
+def _gpu_rows(M):
+    rp, col, val = (t.cpu().numpy() for t in M.to_torch())
+    torch.cuda.synchronize()
+    return rp, col, val
+
+
+def _check_build(m, rows, N, L, delta, tau, top_k, prec=32, table=-1, seed=11, extra=None):
+    orc = _orc()
+    extra = extra or {}
+    B = mc.DeviceCsr.from_host(m)
+    p = mc.params(chains=N, max_len=L, delta=delta, seed=seed, precision=prec, table=table,
+                  filter_tau=tau, top_k=top_k, **extra)
+    M = mc.mcmi_build_ex(B, p)
+    used_table = M.stats.table
+    rp, col, val = _gpu_rows(M)
+    rb = p.row_begin
+    orows, d, s = orc.walk(m, rows=rows, chains=N, max_len=L, delta=delta, seed=seed, table=used_table)
+    worst_rel = worst_b = 0.0
+    for r in orows:
+        i = r["row"]
+        mvals = r["X"] / d[r["col"]]
+        oc, ov = orc.filter_row(i, r["col"], mvals, tau=tau, top_k=top_k)
+        gi = i - rb
+        gc, gv = col[rp[gi]:rp[gi + 1]], val[rp[gi]:rp[gi + 1]]
+        assert np.all(np.diff(gc) > 0), "row not sorted by column"
+        rel, b = P.compare_rows(gc, gv.astype(np.float64), oc, ov, r["col"], mvals, r["A"] / np.abs(d[r["col"]]),
+                                i, tau, top_k)
+        worst_rel, worst_b = max(worst_rel, rel), max(worst_b, b)
+    print(f"build n={m.n} fp{prec} table{used_table}: max rel {worst_rel:.2e} bounded {worst_b:.3f} "
+          f"steps {M.stats.steps} spilled {M.stats.spilled}")
+    assert worst_b <= 1.0
+    return M, rp, col, val
+
+
+def test_build_stencil2d_full_fp64_and_fp32():
+    m = synth.stencil2d_5pt(32, 32, seed=1001)
+    for prec in (64, 32):
+        _check_build(m, np.arange(m.n), 1000, 64, 1e-3, 1e-2, 0, prec=prec)
+
+
+def test_build_topk_and_tau_combinations():
+    m = synth.random_dd(400, 9, seed=4, diag_sign="mixed", dominance=0.85)
+    rows = np.arange(m.n)
+    for tau, k in [(0.0, 0), (0.0, 3), (5e-2, 0), (1e-2, 4), (0.3, 16)]:
+        _check_build(m, rows, 150, 60, 1e-3, tau, k, table=1)
+
+
+def test_build_staging_regrowth_reruns_rows():
+    # tau = 0 keeps every visited column: far more than the first staging buffer
+    m = synth.powerlaw_random(2048, seed=8)
+    M, rp, col, val = _check_build(m, np.arange(0, m.n, 37), 64, 40, 1e-3, 0.0, 0)
+    assert M.stats.deferred_rows > 0
+
+
+def test_build_row_range():
+    m = synth.stencil3d_7pt(10, seed=3)
+    a = _check_build(m, np.arange(200, 420), 256, 128, 1e-2, 0.0, 16, extra=dict(row_begin=200, row_end=420))
+    assert a[0].shape()[0] == 220
+
+
+def test_apply_matches_oracle_spmv():
+    orc = _orc()
+    m = synth.stencil3d_7pt(16, seed=5)
+    B = mc.DeviceCsr.from_host(m)
+    M = mc.mcmi_build_ex(B, mc.params(chains=256, max_len=128, delta=1e-2, top_k=16))
+    rp, col, val = _gpu_rows(M)
+    x = torch.randn(m.n, device="cuda", dtype=torch.float32)
+    y = torch.empty(m.n, device="cuda", dtype=torch.float32)
+    mc.mcmi_apply(M, x, y)
+    ref = orc.spmv(rp, col, val.astype(np.float64), x.cpu().numpy().astype(np.float64))
+    assert np.allclose(y.cpu().numpy(), ref, rtol=1e-5, atol=1e-6)
+
+
+# ------------------------------------------------------------------ edge cases
+
+
+def _csr(n, rows, cols, vals):
+    return synth._from_coo(n, np.array(rows), np.array(cols), np.array(vals, dtype=np.float64))
+
+
+def test_edge_diagonal_only_and_single_row():
+    for m in (_csr(1, [0], [0], [2.0]), _csr(5, range(5), range(5), [1.0, -2.0, 3.0, 4.0, -0.5])):
+        B = mc.DeviceCsr.from_host(m)
+        M = mc.mcmi_build_ex(B, mc.params(chains=33, max_len=10, delta=1e-3, top_k=2))
+        rp, col, val = _gpu_rows(M)
+        d = m.to_scipy().diagonal()
+        assert np.array_equal(col, np.arange(m.n)) and np.allclose(val, (1.0 / d).astype(np.float32), rtol=1e-7)
+        assert M.stats.steps == 0
+
+
+def test_edge_zero_length_and_huge_cutoff():
+    m = synth.random_dd(50, 4, seed=2)
+    B = mc.DeviceCsr.from_host(m)
+    d = m.to_scipy().diagonal()
+    for kw in (dict(max_len=0, delta=1e-3), dict(max_len=50, delta=2.0)):
+        M = mc.mcmi_build_ex(B, mc.params(chains=64, **kw))
+        rp, col, val = _gpu_rows(M)
+        assert M.stats.steps == 0 and np.array_equal(col, np.arange(m.n))
+        assert np.allclose(val, 1.0 / d, rtol=1e-6)
+
+
+def test_edge_empty_matrix_and_empty_range():
+    m = _csr(0, [], [], [])
+    B = mc.DeviceCsr(0, torch.zeros(1, dtype=torch.int64, device="cuda"), torch.zeros(0, dtype=torch.int32, device="cuda"),
+                     torch.zeros(0, dtype=torch.float64, device="cuda"))
+    M = mc.mcmi_build_ex(B, mc.params())
+    assert M.shape() == (0, 0, 0)
+    m = synth.random_dd(20, 3, seed=1)
+    M = mc.mcmi_build_ex(mc.DeviceCsr.from_host(m), mc.params(row_begin=5, row_end=5))
+    assert M.shape() == (0, 5, 0)
+
+
+@pytest.mark.parametrize("defect,status", [("zero_diag", 3), ("unsorted", 2), ("nan", 2), ("col_range", 2),
+                                           ("not_dd", 4), ("row_ptr", 2)])
+def test_edge_invalid_inputs_report_status(defect, status):
+    m = synth.random_dd(30, 4, seed=3)
+    rp, col, val = m.row_ptr.copy(), m.col.copy(), m.val.copy()
+    dpos = [int(rp[i] + np.flatnonzero(col[rp[i]:rp[i + 1]] == i)[0]) for i in range(m.n)]
+    if defect == "zero_diag":
+        val[dpos[7]] = 0.0
+    elif defect == "unsorted":
+        a = int(rp[4])
+        col[a], col[a + 1] = col[a + 1], col[a]
+    elif defect == "nan":
+        val[int(rp[9]) + 1] = np.nan
+    elif defect == "col_range":
+        col[int(rp[3]) + 1] = m.n + 5
+    elif defect == "not_dd":
+        val[dpos[11]] *= 0.5
+    elif defect == "row_ptr":
+        rp[6] = rp[7] + 1
+    bad = synth.Csr(m.n, rp, col, val)
+    B = mc.DeviceCsr.from_host(bad)
+    with pytest.raises(mc.McmiError) as e:
+        mc.mcmi_build_ex(B, mc.params(chains=16, max_len=20))
+    assert e.value.status == status, str(e.value)
+
+
+def test_edge_bad_parameters():
+    m = synth.random_dd(10, 3, seed=1)
+    B = mc.DeviceCsr.from_host(m)
+    for kw in (dict(precision=16), dict(chains=-1), dict(delta=-1.0), dict(table=5), dict(row_begin=3, row_end=2),
+               dict(threads=96), dict(chains=0, eps=0.0)):
+        with pytest.raises(mc.McmiError) as e:
+            mc.mcmi_build_ex(B, mc.params(**kw))
+        assert e.value.status == 1, kw
+
+
+def test_north_star_signature_and_eps_rule():
+    m = synth.random_dd(64, 4, seed=6, dominance=0.5)
+    B = mc.DeviceCsr.from_host(m)
+    M = mc.mcmi_build(B, 0.05, 1e-3, 64, 1e-2, 5)
+    assert M.shape()[0] == m.n
+    M2 = mc.mcmi_build_ex(B, mc.params(chains=0, eps=0.05, delta=1e-3))
+    assert M2.stats.chains == _orc().chains_from_eps(0.05, float(M2.stats.max_s))
