@@ -95,21 +95,31 @@ def _traffic(kernel_src):
 
 
 class Clocks:
-    """nvidia-smi samples during the timed region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """nvidia-smi samples (every 200 ms), started before the warm-up so that
+    the sampler is running when the timed region begins; only samples taken
+    inside [t0, t1] (host clock) are reported."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.t0 = self.t1 = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
 
+    def start(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
+
     def stop(self):
+        import datetime
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.p.terminate()
@@ -118,21 +128,24 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.count(",") >= 8]
+        rows = [l.split(",") for l in open(self.f.name).read().splitlines() if l.count(",") >= 9]
         os.unlink(self.f.name)
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        sm, mx, reasons = [], [], set()
+        samples = []
         for r in rows:
             try:
-                sm.append(float(r[1]))
-                mx.append(float(r[2]))
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                samples.append((ts, float(r[2]), float(r[3]), [n for k, n in enumerate(names)
+                                                               if r[6 + k].strip().lower().startswith("active")]))
             except ValueError:
                 continue
-            for k, name in enumerate(names):
-                if r[5 + k].strip().lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [s for s in samples if self.t0 is not None and self.t0 <= s[0] <= (self.t1 or s[0])]
+        if not inside and samples and self.t0 is not None:   # region shorter than the sampling period
+            inside = [min(samples, key=lambda s: abs(s[0] - 0.5 * (self.t0 + (self.t1 or self.t0))))]
+        reasons = sorted({n for s in inside for n in s[3]})
+        return {"sm_mhz": statistics.median([s[1] for s in inside]) if inside else None,
+                "sm_max_mhz": max(s[2] for s in inside) if inside else None,
+                "reasons": reasons, "samples": len(inside)}
 
 
 def _params_for(mc, name, seed):
@@ -225,12 +238,14 @@ def run_ours(a):
         M.close()
         return st
 
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
     times, walk_ms, steps, visits, launches = [], [], 0, 0, 0
     for it in range(a.steps):
         flush.fill_(float(it))
@@ -247,6 +262,8 @@ def run_ours(a):
         launches += st.launches + 1
         last = st
     torch.cuda.synchronize()
+    if clocks:
+        clocks.end()
     if world > 1:
         torch.distributed.barrier()
     ck = clocks.stop() if clocks else None

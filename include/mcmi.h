@@ -60,6 +60,12 @@ enum {
     MCMI_TABLE_ALIAS = 1        /* integer Walker/Vose alias buckets */
 };
 
+/* Row accumulator of the walk kernel.                                    */
+enum {
+    MCMI_ACC_FIXED64 = 0,  /* exact 64-bit fixed-point sum of the weights (deterministic) */
+    MCMI_ACC_KAHAN32 = 1   /* FP32 sums of W/d_j with a compensation word (precision 32 only) */
+};
+
 typedef struct {
     int64_t n;              /* rows (= columns) */
     int64_t nnz;            /* stored entries */
@@ -82,7 +88,7 @@ typedef struct {
     int32_t table;       /* MCMI_TABLE_* */
     int32_t threads;     /* threads per block of the walk kernel (0 = auto; 128 or 256) */
     int32_t hash_log2;   /* log2 of the on-chip accumulator slots per block (0 = auto) */
-    int32_t reserved;
+    int32_t accumulator; /* MCMI_ACC_*: row sums exact in 64-bit fixed point (default) or FP32 Kahan */
     int64_t row_begin;   /* build rows [row_begin, row_end) only; both 0 = all rows */
     int64_t row_end;
 } mcmi_params;
@@ -110,7 +116,8 @@ typedef struct {
 typedef struct mcmi_matrix_s *mcmi_matrix;
 
 /* Defaults: eps 0.01, delta 1e-3, tau 0, alpha 0, seed 1, chains 128,
- * max_len 256, top_k 0, precision 32, table AUTO, all rows.              */
+ * max_len 256, top_k 0, precision 32, table AUTO, accumulator FIXED64,
+ * all rows.                                                              */
 void mcmi_params_default(mcmi_params *p);
 
 /* Build M ~ Bhat^-1 restricted to the sparsity the filter keeps (Eq. 2 walks,

@@ -20,6 +20,7 @@ MCMI_OK = 0
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_BAD_CSR", 3: "ERR_ZERO_DIAG", 4: "ERR_NOT_CONTRACTIVE",
           5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_CAPACITY"}
 TABLE_AUTO, TABLE_CUMULATIVE, TABLE_ALIAS = -1, 0, 1
+ACC_FIXED64, ACC_KAHAN32 = 0, 1
 
 
 class McmiError(RuntimeError):
@@ -37,7 +38,7 @@ class mcmi_params(C.Structure):
     _fields_ = [("eps", C.c_double), ("delta", C.c_double), ("filter_tau", C.c_double), ("alpha", C.c_double),
                 ("seed", C.c_uint64), ("chains", C.c_int32), ("max_len", C.c_int32), ("top_k", C.c_int32),
                 ("precision", C.c_int32), ("table", C.c_int32), ("threads", C.c_int32), ("hash_log2", C.c_int32),
-                ("reserved", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64)]
+                ("accumulator", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64)]
 
 
 class mcmi_stats(C.Structure):

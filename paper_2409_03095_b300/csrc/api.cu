@@ -164,7 +164,7 @@ struct Prepared {
     uint32_t *a = nullptr, *b = nullptr, *c = nullptr;
     uint4 *bkt = nullptr;
     double2 *rowd = nullptr;
-    double smax = 0.0;
+    double smax = 0.0, smin = 0.0;
     int table = MCMI_TABLE_CUMULATIVE;
     int32_t N = 0, Lb = 0;
     DevState *st = nullptr;
@@ -190,8 +190,12 @@ mcmi_status check_params(const mcmi_params *p)
     if (p->chains == 0 && !(p->eps > 0.0)) return fail(MCMI_ERR_ARG, "chains == 0 needs eps > 0");
     if (p->precision != 32 && p->precision != 64) return fail(MCMI_ERR_ARG, "precision must be 32 or 64");
     if (p->table < -1 || p->table > 1) return fail(MCMI_ERR_ARG, "unknown table type");
-    if (p->threads != 0 && p->threads != 128 && p->threads != 256) return fail(MCMI_ERR_ARG, "threads must be 0, 128 or 256");
+    if (p->threads != 0 && p->threads != 64 && p->threads != 128) return fail(MCMI_ERR_ARG, "threads must be 0, 64 or 128");
     if (p->hash_log2 != 0 && (p->hash_log2 < 6 || p->hash_log2 > 13)) return fail(MCMI_ERR_ARG, "hash_log2 out of [6, 13]");
+    if (p->accumulator != MCMI_ACC_FIXED64 && p->accumulator != MCMI_ACC_KAHAN32)
+        return fail(MCMI_ERR_ARG, "unknown accumulator");
+    if (p->accumulator == MCMI_ACC_KAHAN32 && p->precision != 32)
+        return fail(MCMI_ERR_ARG, "the Kahan FP32 accumulator needs precision 32");
     return MCMI_OK;
 }
 
@@ -221,6 +225,7 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
     cudaMemsetAsync(P.st, 0, sizeof(DevState), s);
     cudaMemsetAsync(&P.st->err, 0xFF, sizeof(unsigned long long), s);
+    cudaMemsetAsync(&P.st->smin_bits, 0xFF, sizeof(unsigned long long), s);
     launch_validate(n, nnz, B->row_ptr, B->col, B->val, P.st, s);
     DevState h;
     mcmi_status r = read_state(P.st, &h, s);
@@ -232,6 +237,7 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     double smax;
     memcpy(&smax, &h.smax_bits, sizeof(double));
     P.smax = smax;
+    if (h.smin_bits != ~0ull) memcpy(&P.smin, &h.smin_bits, sizeof(double));
     // table type: short rows favour the inline cumulative table (one 64-byte
     // load per step); long rows the alias table (two loads, no search)
     int table = p->table;
@@ -280,20 +286,24 @@ struct WalkPlan {
 
 mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, bool dump, WalkPlan &W)
 {
-    W.threads = p->threads ? p->threads : (P.N >= 256 ? 256 : 128);
+    // two chains per thread: 128 threads keep 256 chains of a row in flight
+    W.threads = p->threads ? p->threads : (P.N > 128 ? 128 : 64);
     // distinct columns a row can reach: at most N (Lb + 1) visits, at most n columns
     const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
     const uint64_t distinct = reach < (uint64_t)P.n ? reach : (uint64_t)P.n;
     if (p->hash_log2) {
         W.log2H = p->hash_log2;
     } else {
-        int l = ceil_log2((distinct * 5) / 3 + 1);   // on-chip table at most ~60% full
-        W.log2H = l < 8 ? 8 : (l > 12 ? 12 : l);
+        // on-chip table at most ~75% full for the reachable columns, capped at
+        // 2^11 slots (24 KB) so that six blocks share an SM; rows that reach
+        // more columns put the excess in the global overflow table
+        int l = ceil_log2((distinct * 4) / 3 + 1);
+        W.log2H = l < 8 ? 8 : (l > 11 ? 11 : l);
     }
     int l2 = ceil_log2(2 * distinct + 2);
     W.log2G = l2 < 8 ? 8 : l2;
     int bps = 0;
-    cudaError_t e = walk_occupancy(p->precision, P.table, dump, W.threads, W.log2H, &bps);
+    cudaError_t e = walk_occupancy(p->precision, P.table, p->accumulator, dump, W.threads, W.log2H, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "walk occupancy");
     if (bps < 1) return fail(MCMI_ERR_ARG, "walk kernel does not fit (threads %d, hash 2^%d)", W.threads, W.log2H);
     int dev = 0, sms = 0;
@@ -321,8 +331,26 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     a.log2H = W.log2H;
     a.log2G = W.log2G;
     a.tau = p->filter_tau;
+    // fixed-point scale: N (L_bound + 1) weights of magnitude <= 1 stay below 2^62
+    // Fixed-point scale 2^F: the largest F for which N (L_bound + 1) weights
+    // of magnitude <= 1 stay below 2^62, lowered to what keeps the rounding
+    // of every accumulated weight below 2^-25 relative: weights are >= delta
+    // until the last step of a chain, which is >= delta * min_i s_i.  A small
+    // F keeps most weights below 2^32, so the high-word atomic is rare.
+    const double visits = (double)P.N * (double)(P.Lb + 1) + 1.0;
+    const int Fmax = 62 - (int)std::ceil(std::log2(visits));
+    int F = Fmax;
+    const double wmin = p->delta * (double)(float)P.smin;
+    if (wmin > 0.0) {
+        const int Fneed = 25 + (int)std::ceil(-std::log2(wmin));
+        F = Fneed < 31 ? 31 : Fneed;
+        if (F > Fmax) F = Fmax;
+    }
+    a.fix_shift = F < 8 ? 8 : (F > 62 ? 62 : F);
+    a.fix_inv = std::ldexp(1.0, -a.fix_shift);
     a.top_k = p->top_k;
     a.st = P.st;
+    a.count_steps = 1;
 }
 
 mcmi_status alloc_overflow(Scratch &S, const WalkPlan &W, WalkArgs &a, cudaStream_t s)
@@ -430,8 +458,16 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
     if (r != MCMI_OK) return give_up(r);
     const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
     const uint64_t distinct = reach < (uint64_t)n ? reach : (uint64_t)n;
-    uint64_t cap = p->top_k > 0 ? (uint64_t)rows * (uint64_t)(p->top_k + 1) : (uint64_t)rows * 24 + 1024;
-    if (p->top_k > 0 && (uint64_t)(p->top_k + 1) > distinct) cap = (uint64_t)rows * distinct;
+    // staging entries: exact for top-k; for the tau rule an estimate of up to
+    // 512 kept entries per row (rows that do not fit are re-run), bounded by
+    // a quarter of the free device memory
+    uint64_t per_row = p->top_k > 0 ? (uint64_t)(p->top_k + 1) : 512;
+    if (per_row > distinct + 1) per_row = distinct + 1;
+    uint64_t cap = (uint64_t)rows * per_row + 1024;
+    if (p->top_k == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && cap * 8 > fr / 4) cap = fr / 32 + 1024;
+    }
     a.st_col = S.get<uint32_t>(cap);
     a.st_val = S.get<float>(cap);
     a.st_cap = cap;
@@ -441,7 +477,7 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
     if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (staging)"));
     reset_queue(P.st, s);
     cudaEventRecord(ev[4], s);
-    cudaError_t e = launch_walk(a, p->precision, P.table, false, W.grid, W.threads, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.grid, W.threads, s);
     if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch"));
     cudaEventRecord(ev[5], s);
     ++launches;
@@ -468,11 +504,12 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
         a.row_list = list2;
         a.n_list = deferred;
         a.out_by_row = 1;
+        a.count_steps = 0;   // their transitions were counted in the first launch
         cudaMemsetAsync(&P.st->deferred, 0, 8, s);
         reset_queue(P.st, s);
         WalkPlan W2 = W;
         W2.grid = (int)(deferred < W.grid ? deferred : W.grid);
-        e = launch_walk(a, p->precision, P.table, false, W2.grid, W2.threads, s);
+        e = launch_walk(a, p->precision, P.table, p->accumulator, false, W2.grid, W2.threads, s);
         if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch (deferred rows)"));
         ++launches;
         r = read_state(P.st, &h, s);
@@ -620,7 +657,7 @@ mcmi_status mcmi_walk_dump(const mcmi_csr *B, const mcmi_params *p, const int64_
     a.d_cap = cap;
     a.row_steps = out_steps;
     reset_queue(P.st, s);
-    cudaError_t e = launch_walk(a, p->precision, P.table, true, W.grid, W.threads, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, true, W.grid, W.threads, s);
     if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     DevState h;
     return read_state(P.st, &h, s);

@@ -18,9 +18,9 @@ void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const doubl
                    uint4 *bkt, unsigned long long *wscr, uint32_t *sstk, uint32_t *lstk, double2 *rowd,
                    cudaStream_t s);
 
-size_t walk_smem_bytes(int log2H, bool dump);
-cudaError_t walk_occupancy(int precision, int table, bool dump, int threads, int log2H, int *blocks_per_sm);
-cudaError_t launch_walk(const WalkArgs &a, int precision, int table, bool dump, int grid, int threads,
+size_t walk_smem_bytes(int precision, int log2H, bool dump);
+cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int threads, int log2H, int *blocks_per_sm);
+cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int grid, int threads,
                         cudaStream_t s);
 
 // exclusive scan of int32 counts into int64 offsets (out has n+1 entries)

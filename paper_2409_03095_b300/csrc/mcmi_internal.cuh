@@ -13,11 +13,14 @@ constexpr uint32_t kOolFlag = 0x80000000u;    // slot word 3: table stored out o
 constexpr uint32_t kNegBit = 0x80000000u;     // record: sign of c_ij
 constexpr int kInlineCum = 6;                 // cumulative pairs that fit a 64-byte slot
 constexpr int kInlineAlias = 4;               // alias triples that fit a 64-byte slot
+constexpr int kWalkThreadsMax = 128;          // walk kernel: threads per block (two chains each)
+constexpr int kWalkMinBlocks = 6;             // resident blocks per SM the register budget targets
 
 // Device-side counters and the first error of a launch sequence.
 struct DevState {
     unsigned long long err;        // min over (row << 8 | code); ~0 = no error
     unsigned long long smax_bits;  // bits of max_i s_i (s_i >= 0, so integer order = float order)
+    unsigned long long smin_bits;  // bits of min over s_i > 0 (~0 if none)
     unsigned long long bnorm_bits; // bits of ||B||_inf
     unsigned long long steps;      // transitions taken
     unsigned long long spilled;    // entries placed in the global overflow table
@@ -60,8 +63,11 @@ struct WalkArgs {
     const int64_t *row_list;      // explicit rows (global indices)
     int64_t n_list;
     int out_by_row;               // list mode: outputs indexed by row - row_begin
+    int count_steps;              // add the rows' transitions to the device counter
     int32_t N, L;
     float delta_f;                // smallest float >= delta
+    int fix_shift;                // fixed-point accumulator scale: weight w is added as round(w 2^F)
+    double fix_inv;               // 2^-F
     uint32_t key0, key1;
     int log2H;                    // on-chip slots per block
     // global overflow accumulator, one region per block

@@ -75,6 +75,7 @@ __global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t
         s[i] = si;
         if (!(si < 1.0)) report(st, i, MCMI_ERR_NOT_CONTRACTIVE);
         atomicMax(&st->smax_bits, (unsigned long long)__double_as_longlong(si));
+        if (si > 0.0) atomicMin(&st->smin_bits, (unsigned long long)__double_as_longlong(si));
     }
 }
 

@@ -1,11 +1,22 @@
 // Stages a3-a5 of the hot path in one kernel: the random walks of Eq. 2,
 // the row accumulator (on-chip hash + global overflow table), the phase-4
-// column scaling (fused: each visit adds W / d_col) and the Sec. IV-B
-// filter, writing each row's kept entries to a staging buffer.
+// column scaling by 1/d_j and the Sec. IV-B filter, writing each row's kept
+// entries to a staging buffer.
 //
 // One block per row at a time (rows taken from a device queue), threads as
 // chains: a thread that finishes a chain takes the next chain index of the
 // row, so live chains stay packed into the block's warps.
+//
+// Accumulators (per visited column of the row being built):
+//  ACC_FIXED64 (default): the exact sum of the walk weights as a 64-bit
+//    fixed-point integer (scale 2^F chosen on the host so that N (L+1)
+//    weights of magnitude < 1 cannot overflow), added with two native 32-bit
+//    integer atomics (low word with return, carry into the high word).  The
+//    sum is independent of the order of the additions, so it is
+//    deterministic; 1/d_j is applied once per entry at the end.
+//  ACC_KAHAN32: FP32 sums of W/d_j with a compensation word; the rounding
+//    error of each addition is computed exactly from the returned previous
+//    sum (Knuth's TwoSum) and added to the compensation.
 #include "mcmi_internal.cuh"
 #include "kernels.h"
 
@@ -21,51 +32,55 @@ __device__ __forceinline__ uint32_t hash_home(uint32_t key, int log2)
     return (key * 0x9E3779B1u) >> (32 - log2);
 }
 
-// Compensated (Kahan) FP32 add of v into a packed {sum, compensation} word.
-__device__ __forceinline__ void kahan_add(unsigned long long *p, float v)
+// w * 2^F rounded to the nearest integer, from the bits of an FP32 w (|w| < 1).
+__device__ __forceinline__ long long fix_f32(float w, int F)
 {
-    unsigned long long old = *(volatile unsigned long long *)p, assumed;
-    do {
-        assumed = old;
-        const float sum = __uint_as_float((uint32_t)assumed);
-        const float c = __uint_as_float((uint32_t)(assumed >> 32));
-        const float y = __fsub_rn(v, c);
-        const float t = __fadd_rn(sum, y);
-        const float cn = __fsub_rn(__fsub_rn(t, sum), y);
-        const unsigned long long nv =
-            (unsigned long long)__float_as_uint(t) | ((unsigned long long)__float_as_uint(cn) << 32);
-        old = atomicCAS(p, assumed, nv);
-    } while (old != assumed);
+    const uint32_t b = __float_as_uint(w);
+    const int e = (int)((b >> 23) & 0xFFu);
+    if (e == 0) return 0;
+    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+    const int s = e - 150 + F;
+    long long v;
+    if (s >= 0) v = m << s;
+    else if (s > -40) v = (m + (1ll << (-s - 1))) >> (-s);
+    else v = 0;
+    return (b >> 31) ? -v : v;
 }
 
-template <int PREC>
-__device__ __forceinline__ void acc_add(unsigned long long *p, double v)
+// Same for an FP64 w (|w| < 1).
+__device__ __forceinline__ long long fix_f64(double w, int F)
 {
-    if (PREC == 64)
-        atomicAdd(reinterpret_cast<double *>(p), v);
-    else
-        kahan_add(p, (float)v);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(w);
+    const int e = (int)((b >> 52) & 0x7FFull);
+    if (e == 0) return 0;
+    const long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+    const int s = e - 1075 + F;
+    long long v;
+    if (s >= 0) v = m << s;
+    else if (s > -63) v = (m + (1ll << (-s - 1))) >> (-s);
+    else v = 0;
+    return (b >> 63) ? -v : v;
 }
 
-template <int PREC>
-__device__ __forceinline__ double acc_value(unsigned long long raw, int N)
+// Exact 64-bit add into a shared word from two native 32-bit atomics.
+__device__ __forceinline__ void fix_add_shared(unsigned long long *p, long long v)
 {
-    if (PREC == 64) return __ddiv_rn(__longlong_as_double((long long)raw), (double)N);
-    const float sum = __uint_as_float((uint32_t)raw);
-    const float c = __uint_as_float((uint32_t)(raw >> 32));
-    return (double)__fdiv_rn(__fsub_rn(sum, c), (float)N);
+    uint32_t *w = reinterpret_cast<uint32_t *>(p);
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)((unsigned long long)v >> 32);
+    const uint32_t old = atomicAdd(w, lo);
+    const uint32_t carry = (uint32_t)(old + lo < old);
+    if (hi + carry) atomicAdd(w + 1, hi + carry);
 }
 
-template <int PREC>
-__device__ __forceinline__ void acc_merge(unsigned long long *dst, unsigned long long src)
+// Compensated FP32 add of v into the {sum, comp} pair at p.
+__device__ __forceinline__ void comp_add(unsigned long long *p, float v)
 {
-    if (PREC == 64) {
-        atomicAdd(reinterpret_cast<double *>(dst), __longlong_as_double((long long)src));
-    } else {
-        const float sum = __uint_as_float((uint32_t)src);
-        const float c = __uint_as_float((uint32_t)(src >> 32));
-        kahan_add(dst, __fsub_rn(sum, c));
-    }
+    float *sum = reinterpret_cast<float *>(p);
+    const float a = atomicAdd(sum, v);
+    const float s = __fadd_rn(a, v);
+    const float bp = __fsub_rn(s, a);
+    const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(v, bp));
+    if (err != 0.0f) atomicAdd(sum + 1, err);
 }
 
 __device__ __forceinline__ float block_max(float v, float *red)
@@ -92,68 +107,126 @@ __device__ __forceinline__ unsigned long long block_sum(unsigned long long v, un
     return v;
 }
 
-// Ranking key of the filter: magnitude first, then the smaller column.
-__device__ __forceinline__ unsigned long long rank_key(double v, uint32_t col)
+// Warp 0 picks, from a 256-bin histogram scanned from the top bin down, the
+// bin holding the kk-th largest key; writes the digit and the rank inside it.
+__device__ __forceinline__ void pick_bin(const uint32_t *hist, uint32_t kk, uint32_t *digit, uint32_t *rank)
 {
-    return ((unsigned long long)__float_as_uint(fabsf((float)v)) << 32) | (unsigned long long)(~col);
+    const int l = threadIdx.x;
+    uint32_t c8[8], tot = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        c8[u] = hist[255 - 8 * l - u];
+        tot += c8[u];
+    }
+    uint32_t incl = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (l >= o) incl += nb;
+    }
+    const uint32_t excl = incl - tot;
+    if (excl < kk && incl >= kk) {
+        uint32_t cum = excl;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (cum + c8[u] >= kk) {
+                *digit = 255 - 8 * l - u;
+                *rank = kk - cum;
+                break;
+            }
+            cum += c8[u];
+        }
+    }
+}
+
+// 64-byte row record as two 256-bit loads (one 32-B sector each).
+__device__ __forceinline__ void load_slot(const uint4 *sp, uint32_t (&w)[16])
+{
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                 : "l"(sp));
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+                 : "l"(sp + 2));
 }
 
 }  // namespace
 
-template <int PREC, int TABLE, bool DUMP>
-__global__ void __launch_bounds__(256) k_walk(WalkArgs a)
+template <int PREC, int TABLE, int ACC, bool DUMP>
+__global__ void __launch_bounds__(kWalkThreadsMax, kWalkMinBlocks) k_walk(WalkArgs a)
 {
+    constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
     extern __shared__ __align__(16) unsigned char smem[];
     const int H = 1 << a.log2H;
-    unsigned long long *s_vals = reinterpret_cast<unsigned long long *>(smem);
-    uint32_t *s_keys = reinterpret_cast<uint32_t *>(s_vals + H);
-    uint32_t *s_cnt = s_keys + H;   // DUMP only
+    // per slot: an 8-byte value word (fixed-point sum, or FP32 {sum, comp};
+    // after the walks the finished value of M_ij), the key, and an auxiliary
+    // word (visit counts in the parity build, candidate list for FP64 values)
+    unsigned long long *s_val = reinterpret_cast<unsigned long long *>(smem);
+    uint32_t *s_keys = reinterpret_cast<uint32_t *>(smem + (size_t)8 * H);
+    uint32_t *s_aux = s_keys + H;
+    // FP32 values leave the high half of each value word free for the list
+    auto list_at = [&](uint32_t p) -> uint32_t & {
+        return PREC == 64 ? s_aux[p] : reinterpret_cast<uint32_t *>(s_val + p)[1];
+    };
 
     __shared__ long long s_row, s_pos;
     __shared__ int s_next_chain;
-    __shared__ uint32_t s_nspill, s_fill, s_wpos;
+    __shared__ uint32_t s_nspill, s_fill, s_wpos, s_ncand;
     __shared__ long long s_off;
     __shared__ float s_redf[32];
     __shared__ unsigned long long s_redu[32];
     __shared__ uint32_t s_hist[256];
-    __shared__ unsigned long long s_prefix;
-    __shared__ uint32_t s_kk;
+    __shared__ uint32_t s_digit, s_rank;
 
     const int tid = threadIdx.x, B = blockDim.x;
     const uint32_t fill_cap = (uint32_t)(H - (H >> 2));      // on-chip table kept <= 75% full
     const int G = 1 << a.log2G;
-    uint32_t *gk = a.g_keys + ((size_t)blockIdx.x << a.log2G);
-    unsigned long long *gv = a.g_vals + ((size_t)blockIdx.x << a.log2G);
-    uint32_t *gc = a.g_cnt + ((size_t)blockIdx.x << a.log2G);
-    uint32_t *gl = a.g_list + ((size_t)blockIdx.x << a.log2G);
+    const size_t gbase = (size_t)blockIdx.x << a.log2G;
+    uint32_t *gk = a.g_keys + gbase;
+    uint32_t *gc = a.g_cnt + gbase;
+    uint32_t *gl = a.g_list + gbase;
+    unsigned long long *gv = a.g_vals + gbase;
     const long long total = a.row_list ? a.n_list : a.row_end - a.row_begin;
+    const int F = a.fix_shift;
 
     for (int h = tid; h < H; h += B) {
         s_keys[h] = kEmpty;
-        s_vals[h] = 0ull;
-        if (DUMP) s_cnt[h] = 0u;
+        s_val[h] = 0ull;
+        if (DUMP) s_aux[h] = 0u;
     }
     if (tid == 0) { s_nspill = 0; s_fill = 0; }
 
-    // Adds value v at column col of the current row.
-    auto accumulate = [&](uint32_t col, double v) {
-        uint32_t h = hash_home(col, a.log2H);
+    // Adds the visit of column col with weight w (FP32) / w64 (FP64); the
+    // Kahan accumulator takes the column-scaled value v = w / d_col.
+    auto accumulate = [&](uint32_t col, long long fx, float v) {
+        // linear probing over 4-slot buckets, one 16-byte read per bucket; a
+        // key always takes the first empty slot in probe order, so a search
+        // that meets an empty slot before the key knows the key is absent
+        uint32_t bkt = hash_home(col, a.log2H - 2);
+        const uint32_t nb = (uint32_t)(H >> 2);
 #pragma unroll 1
-        for (int p = 0; p < kProbeOnChip; ++p) {
-            const uint32_t k = ((volatile uint32_t *)s_keys)[h];
-            bool hit = k == col;
-            if (!hit && k == kEmpty) {
-                if (*(volatile uint32_t *)&s_fill >= fill_cap) break;
-                const uint32_t old = atomicCAS(&s_keys[h], kEmpty, col);
-                if (old == kEmpty) atomicAdd(&s_fill, 1u);
-                hit = old == kEmpty || old == col;
+        for (int p = 0; p < kProbeOnChip / 4; ++p) {
+            uint4 kv;
+            asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(kv.x), "=r"(kv.y), "=r"(kv.z), "=r"(kv.w)
+                         : "r"((uint32_t)__cvta_generic_to_shared(s_keys + 4 * bkt)));
+            int slot = kv.x == col ? 0 : kv.y == col ? 1 : kv.z == col ? 2 : kv.w == col ? 3 : -1;
+            if (slot < 0) {
+                const int e = kv.x == kEmpty ? 0 : kv.y == kEmpty ? 1 : kv.z == kEmpty ? 2 : kv.w == kEmpty ? 3 : -1;
+                if (e >= 0) {
+                    if (*(volatile uint32_t *)&s_fill >= fill_cap) break;
+                    const uint32_t old = atomicCAS(&s_keys[4 * bkt + e], kEmpty, col);
+                    if (old == kEmpty) atomicAdd(&s_fill, 1u);
+                    if (old == kEmpty || old == col) slot = e;
+                    else { --p; continue; }   // another key took it: read the bucket again
+                }
             }
-            if (hit) {
-                acc_add<PREC>(&s_vals[h], v);
-                if (DUMP) atomicAdd(&s_cnt[h], 1u);
+            if (slot >= 0) {
+                const uint32_t h = 4 * bkt + (uint32_t)slot;
+                if (FIX) fix_add_shared(&s_val[h], fx); else comp_add(&s_val[h], v);
+                if (DUMP) atomicAdd(&s_aux[h], 1u);
                 return;
             }
-            h = (h + 1) & (uint32_t)(H - 1);
+            bkt = (bkt + 1) & (nb - 1);
         }
         // global overflow table (never more than half full by its sizing)
         uint32_t g = hash_home(col, a.log2G);
@@ -163,14 +236,11 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
             bool hit = k == col;
             if (!hit && k == kEmpty) {
                 const uint32_t old = atomicCAS(&gk[g], kEmpty, col);
-                if (old == kEmpty) {
-                    const uint32_t slot = atomicAdd(&s_nspill, 1u);
-                    gl[slot] = g;
-                }
+                if (old == kEmpty) gl[atomicAdd(&s_nspill, 1u)] = g;
                 hit = old == kEmpty || old == col;
             }
             if (hit) {
-                acc_add<PREC>(&gv[g], v);
+                if (FIX) atomicAdd(&gv[g], (unsigned long long)fx); else comp_add(&gv[g], v);
                 if (DUMP) atomicAdd(&gc[g], 1u);
                 return;
             }
@@ -185,21 +255,25 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
             const long long pos = (long long)atomicAdd(&a.st->work, 1ull);
             s_pos = pos < total ? pos : -1;
             s_row = pos < total ? (a.row_list ? a.row_list[pos] : a.row_begin + pos) : -1;
-            s_next_chain = B;
+            s_next_chain = 2 * B;   // chains tid and tid + B start at once
             if (s_row >= 0) {
-                // t = 0 visits of all N chains: weight 1 at the row itself.
+                // t = 0 visits of all N chains: weight 1 at the row itself
                 const uint32_t r = (uint32_t)s_row;
-                const uint32_t h = hash_home(r, a.log2H);
+                const uint32_t h = 4 * hash_home(r, a.log2H - 2);   // first slot of its bucket
                 s_keys[h] = r;
                 s_fill = 1;
-                if (PREC == 64) {
-                    const double invd = a.rowd[r].y;
-                    s_vals[h] = (unsigned long long)__double_as_longlong(__dmul_rn((double)a.N, invd));
+                if (FIX) {
+                    s_val[h] = (unsigned long long)((long long)a.N << F);
                 } else {
                     const float invd = __uint_as_float(__ldg(&a.slots[4 * (size_t)r].z));
-                    s_vals[h] = (unsigned long long)__float_as_uint(__fmul_rn((float)a.N, invd));
+                    const float s0 = __fmul_rn((float)a.N, invd);
+                    const float c0 = __fmaf_rn((float)a.N, invd, -s0);   // exact residual of the product
+                    // the pair holds sum + comp == value; the compensation is
+                    // stored as an addend, the TwoSum errors are added to it
+                    s_val[h] = (unsigned long long)__float_as_uint(s0) |
+                               ((unsigned long long)__float_as_uint(c0) << 32);
                 }
-                if (DUMP) s_cnt[h] = (uint32_t)a.N;
+                if (DUMP) s_aux[h] = (uint32_t)a.N;
             }
         }
         __syncthreads();
@@ -208,98 +282,127 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
         const long long idx = (a.row_list && !a.out_by_row) ? pos : row - a.row_begin;
         const uint32_t rlo = (uint32_t)row, rhi = (uint32_t)((unsigned long long)row >> 32);
 
-        // ---- walks (Eq. 2) ----
+        // ---- walks (Eq. 2): each thread advances two chains in turn, so that
+        // two dependent gathers are in flight per thread; a chain that stops
+        // is replaced by the row's next chain index ----
         unsigned long long my_steps = 0;
-        for (int k = tid; k < a.N; k = atomicAdd(&s_next_chain, 1)) {
-            uint32_t st = (uint32_t)row;
-            float w = 1.0f;            // FP32 weight (the FP64 path keeps it as the stop shadow)
-            double w64 = 1.0;
-            uint4 r4 = make_uint4(0, 0, 0, 0);
-            int t = 0;
+        uint32_t st[2];
+        float w[2];            // FP32 weight (the FP64 path keeps it as the stop shadow)
+        double w64[2];
+        uint4 r4[2];
+        int t[2], k[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            k[j] = tid + j * B;
+            st[j] = (uint32_t)row;
+            w[j] = 1.0f;
+            w64[j] = 1.0;
+            t[j] = 0;
+            r4[j] = make_uint4(0, 0, 0, 0);
+        }
 #pragma unroll 1
-            for (;;) {
-                const uint4 *sp = a.slots + 4 * (size_t)st;
-                const uint4 h0 = __ldg(sp);
-                const uint4 h1 = __ldg(sp + 1);
-                const uint4 h2 = __ldg(sp + 2);
-                const uint4 h3 = __ldg(sp + 3);
-                double2 rd = make_double2(0.0, 0.0);
-                if (PREC == 64) rd = __ldg(a.rowd + st);
-                if (t > 0) {
-                    if (PREC == 64)
-                        accumulate(st, __dmul_rn(w64, rd.y));
-                    else
-                        accumulate(st, (double)__fmul_rn(w, __uint_as_float(h0.z)));
+        while (k[0] < a.N || k[1] < a.N) {
+            uint32_t s[2][16];
+            double2 rd[2];
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                if (k[j] < a.N) {
+                    load_slot(a.slots + 4 * (size_t)st[j], s[j]);
+                    if (PREC == 64) rd[j] = __ldg(a.rowd + st[j]);
                 }
-                const uint32_t Q = h0.x;
-                if (t == a.L || !(fabsf(w) >= a.delta_f) || Q == 0u) break;
-                if ((t & 3) == 0) r4 = philox4x32_10(make_uint4((uint32_t)(t >> 2), (uint32_t)k, rlo, rhi), a.key0, a.key1);
-                const int ph = t & 3;
-                const uint32_t r = ph == 0 ? r4.x : ph == 1 ? r4.y : ph == 2 ? r4.z : r4.w;
-                const uint32_t deg = h0.w & ~kOolFlag;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                if (k[j] >= a.N) continue;
+                if (t[j] > 0) {
+                    if (FIX)
+                        accumulate(st[j], PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F), 0.0f);
+                    else
+                        accumulate(st[j], 0, __fmul_rn(w[j], __uint_as_float(s[j][2])));
+                }
+                const uint32_t Q = s[j][0];
+                if (t[j] == a.L || !(fabsf(w[j]) >= a.delta_f) || Q == 0u) {
+                    my_steps += (unsigned long long)t[j];
+                    k[j] = atomicAdd(&s_next_chain, 1);
+                    st[j] = (uint32_t)row;
+                    w[j] = 1.0f;
+                    w64[j] = 1.0;
+                    t[j] = 0;
+                    continue;
+                }
+                if ((t[j] & 3) == 0)
+                    r4[j] = philox4x32_10(make_uint4((uint32_t)(t[j] >> 2), (uint32_t)k[j], rlo, rhi), a.key0, a.key1);
+                const int ph = t[j] & 3;
+                const uint32_t r = ph == 0 ? r4[j].x : ph == 1 ? r4[j].y : ph == 2 ? r4[j].z : r4[j].w;
+                const uint32_t *sj = s[j];
+                const uint32_t deg = sj[3] & ~kOolFlag;
                 uint32_t cs;
                 if (TABLE == MCMI_TABLE_CUMULATIVE) {
                     const uint32_t x = __umulhi(r, Q);
-                    if (!(h0.w & kOolFlag)) {
-                        const uint32_t m = (h1.x <= x) + (h1.z <= x) + (h2.x <= x) + (h2.z <= x) +
-                                           (h3.x <= x) + (h3.z <= x);
-                        cs = m == 0 ? h1.y : m == 1 ? h1.w : m == 2 ? h2.y : m == 3 ? h2.w : m == 4 ? h3.y : h3.w;
+                    if (!(sj[3] & kOolFlag)) {
+                        const uint32_t m = (sj[4] <= x) + (sj[6] <= x) + (sj[8] <= x) + (sj[10] <= x) +
+                                           (sj[12] <= x) + (sj[14] <= x);
+                        cs = m == 0 ? sj[5] : m == 1 ? sj[7] : m == 2 ? sj[9] : m == 3 ? sj[11] : m == 4 ? sj[13] : sj[15];
                     } else {
-                        const uint32_t *T = a.ool_a + h1.x;
+                        const uint32_t *T = a.ool_a + sj[4];
                         uint32_t lo = 0, hi = deg - 1;
 #pragma unroll 1
                         while (lo < hi) {
                             const uint32_t mid = (lo + hi) >> 1;
                             if (x < __ldg(T + mid)) hi = mid; else lo = mid + 1;
                         }
-                        cs = __ldg(a.ool_b + h1.x + lo);
+                        cs = __ldg(a.ool_b + sj[4] + lo);
                     }
                 } else {
                     const unsigned long long pr = (unsigned long long)r * deg;
                     const uint32_t b = (uint32_t)(pr >> 32);
                     const uint32_t y = __umulhi((uint32_t)pr, Q);
                     uint32_t prob, own, al;
-                    if (!(h0.w & kOolFlag)) {
-                        prob = b == 0 ? h1.x : b == 1 ? h1.w : b == 2 ? h2.z : h3.y;
-                        own = b == 0 ? h1.y : b == 1 ? h2.x : b == 2 ? h2.w : h3.z;
-                        al = b == 0 ? h1.z : b == 1 ? h2.y : b == 2 ? h3.x : h3.w;
+                    if (!(sj[3] & kOolFlag)) {
+                        prob = b == 0 ? sj[4] : b == 1 ? sj[7] : b == 2 ? sj[10] : sj[13];
+                        own = b == 0 ? sj[5] : b == 1 ? sj[8] : b == 2 ? sj[11] : sj[14];
+                        al = b == 0 ? sj[6] : b == 1 ? sj[9] : b == 2 ? sj[12] : sj[15];
                     } else {
-                        const uint4 bk = __ldg(a.ool_bkt + h1.x + b);
+                        const uint4 bk = __ldg(a.ool_bkt + sj[4] + b);
                         prob = bk.x; own = bk.y; al = bk.z;
                     }
                     cs = y < prob ? own : al;
                 }
-                const float f = __uint_as_float(h0.y);
+                const float f = __uint_as_float(sj[1]);
                 const bool neg = (cs & kNegBit) != 0u;
-                w = __fmul_rn(w, neg ? -f : f);
-                if (PREC == 64) w64 = __dmul_rn(w64, neg ? -rd.x : rd.x);
-                st = cs & ~kNegBit;
-                ++t;
+                w[j] = __fmul_rn(w[j], neg ? -f : f);
+                if (PREC == 64) w64[j] = __dmul_rn(w64[j], neg ? -rd[j].x : rd[j].x);
+                st[j] = cs & ~kNegBit;
+                ++t[j];
             }
-            my_steps += (unsigned long long)t;
         }
         __syncthreads();
 
         // ---- row statistics ----
         const unsigned long long row_steps = block_sum(my_steps, s_redu);
         if (tid == 0) {
-            atomicAdd(&a.st->steps, row_steps);
+            if (a.count_steps) atomicAdd(&a.st->steps, row_steps);
             if (a.row_steps) a.row_steps[idx] = row_steps;
             if (s_nspill) atomicAdd(&a.st->spilled, (unsigned long long)s_nspill);
             s_wpos = 0;
+            s_ncand = 0;
         }
         const uint32_t nsp = s_nspill;
         // overflow entries whose key also sits on chip are merged into it
         for (uint32_t e = tid; e < nsp; e += B) {
             const uint32_t g = gl[e];
             const uint32_t key = gk[g];
-            uint32_t h = hash_home(key, a.log2H);
+            uint32_t h = 4 * hash_home(key, a.log2H - 2);
             for (int p = 0; p < kProbeOnChip; ++p) {
                 const uint32_t k = s_keys[h];
                 if (k == kEmpty) break;
                 if (k == key) {
-                    acc_merge<PREC>(&s_vals[h], gv[g]);
-                    if (DUMP) atomicAdd(&s_cnt[h], gc[g]);
+                    if (FIX) {
+                        fix_add_shared(&s_val[h], (long long)gv[g]);
+                    } else {
+                        comp_add(&s_val[h], __uint_as_float((uint32_t)gv[g]));
+                        comp_add(&s_val[h], __uint_as_float((uint32_t)(gv[g] >> 32)));
+                    }
+                    if (DUMP) atomicAdd(&s_aux[h], gc[g]);
                     gl[e] = g | kDead;
                     break;
                 }
@@ -308,16 +411,44 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
         }
         __syncthreads();
 
+        // finished values M_ij = (1/N) X_ij / d_j, written over the value words
+        auto finish = [&](unsigned long long raw, uint32_t col) -> double {
+            if (FIX) {
+                const double X = __dmul_rn(__ll2double_rn((long long)raw), a.fix_inv);   // exact scaling
+                const double invd = PREC == 64 ? __ldg(&a.rowd[col].y)
+                                               : (double)__uint_as_float(__ldg(&a.slots[4 * (size_t)col].z));
+                return __dmul_rn(__ddiv_rn(X, (double)a.N), invd);
+            }
+            const float sum = __uint_as_float((uint32_t)raw), c = __uint_as_float((uint32_t)(raw >> 32));
+            return (double)__fdiv_rn(__fadd_rn(sum, c), (float)a.N);
+        };
+        auto store = [&](unsigned long long *p, double v) {
+            if (PREC == 64) *p = (unsigned long long)__double_as_longlong(v);
+            else *reinterpret_cast<float *>(p) = (float)v;
+        };
+        for (int h = tid; h < H; h += B)
+            if (s_keys[h] != kEmpty) store(&s_val[h], finish(s_val[h], s_keys[h]));
+        for (uint32_t e = tid; e < nsp; e += B) {
+            const uint32_t g = gl[e];
+            if (!(g & kDead)) store(&gv[g], finish(gv[g], gk[g]));
+        }
+        __syncthreads();
+        auto sval = [&](uint32_t h) -> double {
+            return PREC == 64 ? __longlong_as_double((long long)s_val[h]) : (double)*reinterpret_cast<const float *>(&s_val[h]);
+        };
+        auto gval = [&](uint32_t g) -> double {
+            return PREC == 64 ? __longlong_as_double((long long)gv[g]) : (double)*reinterpret_cast<const float *>(&gv[g]);
+        };
+
         if (DUMP) {
-            // every accumulator entry, unfiltered
             for (int h = tid; h < H; h += B) {
                 const uint32_t k = s_keys[h];
                 if (k == kEmpty) continue;
                 const uint32_t p = atomicAdd(&s_wpos, 1u);
                 if (p < (uint32_t)a.d_cap) {
                     a.d_col[idx * a.d_cap + p] = (int32_t)k;
-                    a.d_val[idx * a.d_cap + p] = acc_value<PREC>(s_vals[h], a.N);
-                    a.d_vis[idx * a.d_cap + p] = s_cnt[h];
+                    a.d_val[idx * a.d_cap + p] = sval(h);
+                    a.d_vis[idx * a.d_cap + p] = s_aux[h];
                 }
             }
             for (uint32_t e = tid; e < nsp; e += B) {
@@ -326,7 +457,7 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
                 const uint32_t p = atomicAdd(&s_wpos, 1u);
                 if (p < (uint32_t)a.d_cap) {
                     a.d_col[idx * a.d_cap + p] = (int32_t)gk[g];
-                    a.d_val[idx * a.d_cap + p] = acc_value<PREC>(gv[g], a.N);
+                    a.d_val[idx * a.d_cap + p] = gval(g);
                     a.d_vis[idx * a.d_cap + p] = gc[g];
                 }
             }
@@ -338,26 +469,13 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
             }
         } else {
             // ---- Sec. IV-B filter: diagonal kept; tau rule; top-k ----
-            float lmax = 0.0f;
-            for (int h = tid; h < H; h += B)
-                if (s_keys[h] != kEmpty) lmax = fmaxf(lmax, fabsf((float)acc_value<PREC>(s_vals[h], a.N)));
-            for (uint32_t e = tid; e < nsp; e += B)
-                if (!(gl[e] & kDead)) lmax = fmaxf(lmax, fabsf((float)acc_value<PREC>(gv[gl[e]], a.N)));
-            // the row maximum in the accumulator's precision, then the FP64 threshold
-            double rowmax = (double)block_max(lmax, s_redf);
+            double rowmax;
             if (PREC == 64) {
-                // exact FP64 maximum for the FP64 path
                 unsigned long long lm = 0;
                 for (int h = tid; h < H; h += B)
-                    if (s_keys[h] != kEmpty) {
-                        const double v = fabs(acc_value<PREC>(s_vals[h], a.N));
-                        lm = max(lm, (unsigned long long)__double_as_longlong(v));
-                    }
+                    if (s_keys[h] != kEmpty) lm = max(lm, (unsigned long long)__double_as_longlong(fabs(sval(h))));
                 for (uint32_t e = tid; e < nsp; e += B)
-                    if (!(gl[e] & kDead)) {
-                        const double v = fabs(acc_value<PREC>(gv[gl[e]], a.N));
-                        lm = max(lm, (unsigned long long)__double_as_longlong(v));
-                    }
+                    if (!(gl[e] & kDead)) lm = max(lm, (unsigned long long)__double_as_longlong(fabs(gval(gl[e]))));
                 for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
                 __syncthreads();
                 if ((tid & 31) == 0) s_redu[tid >> 5] = lm;
@@ -365,79 +483,111 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
                 lm = 0;
                 for (int w = 0; w < (B >> 5); ++w) lm = max(lm, s_redu[w]);
                 rowmax = __longlong_as_double((long long)lm);
+            } else {
+                float lmax = 0.0f;
+                for (int h = tid; h < H; h += B)
+                    if (s_keys[h] != kEmpty) lmax = fmaxf(lmax, fabsf((float)sval(h)));
+                for (uint32_t e = tid; e < nsp; e += B)
+                    if (!(gl[e] & kDead)) lmax = fmaxf(lmax, fabsf((float)gval(gl[e])));
+                rowmax = (double)block_max(lmax, s_redf);
             }
             const double thr = a.tau > 0.0 ? __dmul_rn(a.tau, rowmax) : 0.0;
             const uint32_t rowc = (uint32_t)row;
             auto is_cand = [&](uint32_t k, double v) -> bool {
                 return k != rowc && (a.tau <= 0.0 || fabs(v) >= thr);
             };
-            unsigned long long nc_l = 0;
+            // candidates: on-chip slot h as h, overflow list entry e as H + e
+            const uint32_t list_cap = (uint32_t)H;
             for (int h = tid; h < H; h += B) {
                 const uint32_t k = s_keys[h];
-                if (k != kEmpty && is_cand(k, acc_value<PREC>(s_vals[h], a.N))) ++nc_l;
+                if (k != kEmpty && is_cand(k, sval(h))) {
+                    const uint32_t p = atomicAdd(&s_ncand, 1u);
+                    if (p < list_cap) list_at(p) = (uint32_t)h;
+                }
             }
             for (uint32_t e = tid; e < nsp; e += B) {
                 const uint32_t g = gl[e];
-                if (!(g & kDead) && is_cand(gk[g], acc_value<PREC>(gv[g], a.N))) ++nc_l;
+                if (!(g & kDead) && is_cand(gk[g], gval(g))) {
+                    const uint32_t p = atomicAdd(&s_ncand, 1u);
+                    if (p < list_cap) list_at(p) = (uint32_t)H + e;
+                }
             }
-            const unsigned long long nc = block_sum(nc_l, s_redu);
-            const bool select = a.top_k > 0 && nc > (unsigned long long)a.top_k;
-            unsigned long long kstar = 0;
-            if (select) {
-                // radix select of the top_k-th largest ranking key, 8 bits per pass
-                if (tid == 0) { s_prefix = 0; s_kk = (uint32_t)a.top_k; }
-                unsigned long long mask = 0;
-                for (int shift = 56; shift >= 0; shift -= 8) {
-                    for (int b = tid; b < 256; b += B) s_hist[b] = 0;
-                    __syncthreads();
-                    const unsigned long long pre = s_prefix;
+            __syncthreads();
+            const uint32_t nc = s_ncand;
+            const bool compact = nc <= list_cap;
+            const bool select = a.top_k > 0 && nc > (uint32_t)a.top_k;
+            // visit every candidate: fn(magnitude bits, column, value)
+            auto for_cands = [&](auto fn) {
+                if (compact) {
+                    for (uint32_t i = tid; i < nc; i += B) {
+                        const uint32_t c = list_at(i);
+                        if (c < (uint32_t)H) {
+                            const double v = sval(c);
+                            fn(__float_as_uint(fabsf((float)v)), s_keys[c], v);
+                        } else {
+                            const uint32_t g = gl[c - H] & ~kDead;
+                            const double v = gval(g);
+                            fn(__float_as_uint(fabsf((float)v)), gk[g], v);
+                        }
+                    }
+                } else {
                     for (int h = tid; h < H; h += B) {
                         const uint32_t k = s_keys[h];
                         if (k == kEmpty) continue;
-                        const double v = acc_value<PREC>(s_vals[h], a.N);
-                        if (!is_cand(k, v)) continue;
-                        const unsigned long long rk = rank_key(v, k);
-                        if ((rk & mask) == pre) atomicAdd(&s_hist[(rk >> shift) & 255u], 1u);
+                        const double v = sval(h);
+                        if (is_cand(k, v)) fn(__float_as_uint(fabsf((float)v)), k, v);
                     }
                     for (uint32_t e = tid; e < nsp; e += B) {
                         const uint32_t g = gl[e];
                         if (g & kDead) continue;
-                        const double v = acc_value<PREC>(gv[g], a.N);
-                        if (!is_cand(gk[g], v)) continue;
-                        const unsigned long long rk = rank_key(v, gk[g]);
-                        if ((rk & mask) == pre) atomicAdd(&s_hist[(rk >> shift) & 255u], 1u);
+                        const double v = gval(g);
+                        if (is_cand(gk[g], v)) fn(__float_as_uint(fabsf((float)v)), gk[g], v);
                     }
+                }
+            };
+            uint32_t vstar = 0, cstar_inv = 0;
+            if (select) {
+                // radix select of the top_k-th largest magnitude (FP32 bits), 8 bits per pass
+                uint32_t pre = 0, mask = 0, kk = (uint32_t)a.top_k;
+                for (int shift = 24; shift >= 0; shift -= 8) {
+                    for (int b = tid; b < 256; b += B) s_hist[b] = 0;
                     __syncthreads();
-                    if (tid < 32) {
-                        // warp scan from the top bin down: lane l owns bins 255-8l .. 248-8l
-                        uint32_t c8[8], tot = 0;
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) { c8[u] = s_hist[255 - 8 * tid - u]; tot += c8[u]; }
-                        uint32_t incl = tot;
-                        for (int o = 1; o < 32; o <<= 1) {
-                            const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                            if (tid >= o) incl += nb;
-                        }
-                        const uint32_t kk = s_kk;
-                        const uint32_t excl = incl - tot;
-                        const bool mine = excl < kk && incl >= kk;
-                        if (mine) {
-                            uint32_t cum = excl;
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                if (cum + c8[u] >= kk) {
-                                    s_prefix = pre | ((unsigned long long)(255 - 8 * tid - u) << shift);
-                                    s_kk = kk - cum;
-                                    break;
-                                }
-                                cum += c8[u];
-                            }
-                        }
-                    }
-                    mask |= 255ull << shift;
+                    for_cands([&](uint32_t mag, uint32_t, double) {
+                        if ((mag & mask) == pre) atomicAdd(&s_hist[(mag >> shift) & 255u], 1u);
+                    });
+                    __syncthreads();
+                    if (tid < 32) pick_bin(s_hist, kk, &s_digit, &s_rank);
+                    __syncthreads();
+                    pre |= s_digit << shift;
+                    kk = s_rank;
+                    mask |= 255u << shift;
                     __syncthreads();
                 }
-                kstar = s_prefix;
+                vstar = pre;               // magnitude bits of the top_k-th largest
+                const uint32_t keep_ties = kk;
+                unsigned long long eq_l = 0;
+                for_cands([&](uint32_t mag, uint32_t, double) { eq_l += (mag == vstar); });
+                const unsigned long long neq = block_sum(eq_l, s_redu);
+                if (neq > keep_ties) {
+                    // equal magnitudes: keep the keep_ties smallest columns (radix select on ~col)
+                    uint32_t cpre = 0, cmask = 0, ck = keep_ties;
+                    for (int shift = 24; shift >= 0; shift -= 8) {
+                        for (int b = tid; b < 256; b += B) s_hist[b] = 0;
+                        __syncthreads();
+                        for_cands([&](uint32_t mag, uint32_t col, double) {
+                            const uint32_t inv = ~col;
+                            if (mag == vstar && (inv & cmask) == cpre) atomicAdd(&s_hist[(inv >> shift) & 255u], 1u);
+                        });
+                        __syncthreads();
+                        if (tid < 32) pick_bin(s_hist, ck, &s_digit, &s_rank);
+                        __syncthreads();
+                        cpre |= s_digit << shift;
+                        ck = s_rank;
+                        cmask |= 255u << shift;
+                        __syncthreads();
+                    }
+                    cstar_inv = cpre;
+                }
             }
             const unsigned long long nk = 1ull + (select ? (unsigned long long)a.top_k : nc);
             if (tid == 0) {
@@ -456,31 +606,29 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
             __syncthreads();
             const long long off = s_off;
             if (off >= 0) {
-                auto emit = [&](uint32_t k, double v) {
-                    bool keep = k == rowc;
-                    if (!keep && is_cand(k, v)) keep = !select || rank_key(v, k) >= kstar;
-                    if (keep) {
-                        const uint32_t p = atomicAdd(&s_wpos, 1u);
-                        a.st_col[off + p] = k;
-                        a.st_val[off + p] = (float)v;
-                    }
+                auto put = [&](uint32_t k, double v) {
+                    const uint32_t p = atomicAdd(&s_wpos, 1u);
+                    a.st_col[off + p] = k;
+                    a.st_val[off + p] = (float)v;
                 };
-                for (int h = tid; h < H; h += B) {
-                    const uint32_t k = s_keys[h];
-                    if (k != kEmpty) emit(k, acc_value<PREC>(s_vals[h], a.N));
+                if (tid == 0) {
+                    // the diagonal (always present: inserted before the walks)
+                    uint32_t h = 4 * hash_home(rowc, a.log2H - 2);
+                    while (s_keys[h] != rowc) h = (h + 1) & (uint32_t)(H - 1);
+                    put(rowc, sval(h));
                 }
-                for (uint32_t e = tid; e < nsp; e += B) {
-                    const uint32_t g = gl[e];
-                    if (!(g & kDead)) emit(gk[g], acc_value<PREC>(gv[g], a.N));
-                }
+                for_cands([&](uint32_t mag, uint32_t col, double v) {
+                    const bool keep = !select || mag > vstar || (mag == vstar && (~col) >= cstar_inv);
+                    if (keep) put(col, v);
+                });
             }
         }
         __syncthreads();
         // ---- reset the accumulator for the next row ----
         for (int h = tid; h < H; h += B) {
             s_keys[h] = kEmpty;
-            s_vals[h] = 0ull;
-            if (DUMP) s_cnt[h] = 0u;
+            s_val[h] = 0ull;
+            if (DUMP || PREC == 64) s_aux[h] = 0u;
         }
         for (uint32_t e = tid; e < nsp; e += B) {
             const uint32_t g = gl[e] & ~kDead;
@@ -492,51 +640,62 @@ __global__ void __launch_bounds__(256) k_walk(WalkArgs a)
     }
 }
 
-template <int PREC, int TABLE, bool DUMP>
+template <int PREC, int TABLE, int ACC, bool DUMP>
 static cudaError_t launch_walk_t(const WalkArgs &a, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    auto fn = k_walk<PREC, TABLE, DUMP>;
+    auto fn = k_walk<PREC, TABLE, ACC, DUMP>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, threads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-size_t walk_smem_bytes(int log2H, bool dump)
+// per slot: 8-B value word, 4-B key, and 4 B of counts / candidate list where needed
+size_t walk_smem_bytes(int precision, int log2H, bool dump)
 {
-    return ((size_t)1 << log2H) * (dump ? 16 : 12);
+    return ((size_t)1 << log2H) * ((dump || precision == 64) ? 16 : 12);
 }
 
-cudaError_t walk_occupancy(int precision, int table, bool dump, int threads, int log2H, int *blocks_per_sm)
+namespace {
+template <bool DUMP>
+const void *walk_fn(int precision, int table, int acc)
 {
-    const size_t smem = walk_smem_bytes(log2H, dump);
-    const void *fn = nullptr;
-#define MCMI_PICK(P, T, D) if (precision == P && table == T && dump == D) fn = (const void *)k_walk<P, T, D>;
-    MCMI_PICK(32, 0, false) MCMI_PICK(32, 1, false) MCMI_PICK(64, 0, false) MCMI_PICK(64, 1, false)
-    MCMI_PICK(32, 0, true) MCMI_PICK(32, 1, true) MCMI_PICK(64, 0, true) MCMI_PICK(64, 1, true)
-#undef MCMI_PICK
-    if (!fn) return cudaErrorInvalidValue;
+    if (precision == 64) return table ? (const void *)k_walk<64, 1, MCMI_ACC_FIXED64, DUMP>
+                                      : (const void *)k_walk<64, 0, MCMI_ACC_FIXED64, DUMP>;
+    if (acc == MCMI_ACC_KAHAN32) return table ? (const void *)k_walk<32, 1, MCMI_ACC_KAHAN32, DUMP>
+                                              : (const void *)k_walk<32, 0, MCMI_ACC_KAHAN32, DUMP>;
+    return table ? (const void *)k_walk<32, 1, MCMI_ACC_FIXED64, DUMP> : (const void *)k_walk<32, 0, MCMI_ACC_FIXED64, DUMP>;
+}
+}  // namespace
+
+cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int threads, int log2H, int *blocks_per_sm)
+{
+    const size_t smem = walk_smem_bytes(precision, log2H, dump);
+    const void *fn = dump ? walk_fn<true>(precision, table, acc) : walk_fn<false>(precision, table, acc);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
 }
 
-cudaError_t launch_walk(const WalkArgs &a, int precision, int table, bool dump, int grid, int threads,
+cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int grid, int threads,
                         cudaStream_t s)
 {
-    const size_t smem = walk_smem_bytes(a.log2H, dump);
+    const size_t smem = walk_smem_bytes(precision, a.log2H, dump);
+#define MCMI_L(P, T, A, D) return launch_walk_t<P, T, A, D>(a, grid, threads, smem, s)
     if (precision == 64) {
-        if (table == MCMI_TABLE_ALIAS)
-            return dump ? launch_walk_t<64, 1, true>(a, grid, threads, smem, s)
-                        : launch_walk_t<64, 1, false>(a, grid, threads, smem, s);
-        return dump ? launch_walk_t<64, 0, true>(a, grid, threads, smem, s)
-                    : launch_walk_t<64, 0, false>(a, grid, threads, smem, s);
+        if (table) { if (dump) MCMI_L(64, 1, 0, true); MCMI_L(64, 1, 0, false); }
+        if (dump) MCMI_L(64, 0, 0, true);
+        MCMI_L(64, 0, 0, false);
     }
-    if (table == MCMI_TABLE_ALIAS)
-        return dump ? launch_walk_t<32, 1, true>(a, grid, threads, smem, s)
-                    : launch_walk_t<32, 1, false>(a, grid, threads, smem, s);
-    return dump ? launch_walk_t<32, 0, true>(a, grid, threads, smem, s)
-                : launch_walk_t<32, 0, false>(a, grid, threads, smem, s);
+    if (acc == MCMI_ACC_KAHAN32) {
+        if (table) { if (dump) MCMI_L(32, 1, 1, true); MCMI_L(32, 1, 1, false); }
+        if (dump) MCMI_L(32, 0, 1, true);
+        MCMI_L(32, 0, 1, false);
+    }
+    if (table) { if (dump) MCMI_L(32, 1, 0, true); MCMI_L(32, 1, 0, false); }
+    if (dump) MCMI_L(32, 0, 0, true);
+    MCMI_L(32, 0, 0, false);
+#undef MCMI_L
 }
 
 }  // namespace mcmi

@@ -90,10 +90,15 @@ WALK_CASES = [
     ("rand_mixed", 32, 0, 300, 80, 1e-4, {}),
     ("rand_mixed", 64, 1, 100, 80, 1e-4, {}),
     ("rand_long", 32, 1, 128, 256, 1e-3, {}),
-    ("rand_long", 32, 0, 128, 256, 1e-3, {"threads": 256}),
+    ("rand_long", 32, 0, 128, 256, 1e-3, {"threads": 128}),
+    ("rand_long", 32, 1, 300, 256, 1e-3, {"threads": 64}),        # refill: 300 chains on 128 lanes
     ("powerlaw_4k", 32, 1, 128, 256, 1e-3, {}),
     ("powerlaw_4k", 32, 0, 128, 256, 1e-3, {"hash_log2": 6}),      # forces the global overflow table
-    ("stencil2d", 32, 0, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 128}),
+    ("stencil2d", 32, 0, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 64}),
+    # the FP32 Kahan accumulator
+    ("stencil3d_12", 32, 0, 256, 128, 1e-2, {"accumulator": 1}),
+    ("rand_mixed", 32, 1, 300, 80, 1e-4, {"accumulator": 1}),
+    ("powerlaw_4k", 32, 1, 128, 256, 1e-3, {"accumulator": 1, "hash_log2": 6}),
 ]
 
 
@@ -126,11 +131,29 @@ def test_sharded_rows_equal_one_launch():
     c = mc.mcmi_walk_dump(B, p, np.arange(7, 19), 4000)
     for x, y in zip(a, b):
         assert np.array_equal(x["col"], y["col"]) and np.array_equal(x["visits"], y["visits"])
-        # FP32 compensated sums in a timing-dependent order: equal up to a few
-        # ulps of the row's largest partial sums (entries may cancel)
-        assert np.allclose(x["val"], y["val"], rtol=1e-6, atol=1e-6 * np.abs(x["val"]).max())
+        # the fixed-point accumulator sums exactly: bit-identical values
+        assert np.array_equal(x["val"], y["val"])
     for k, r in enumerate(c):
         assert np.array_equal(r["col"], a[7 + k]["col"]) and np.array_equal(r["visits"], a[7 + k]["visits"])
+        assert np.array_equal(r["val"], a[7 + k]["val"])
+    # the FP32 Kahan accumulator sums in a timing-dependent order: equal up to
+    # a few ulps of the row's largest partial sums (entries may cancel)
+    pk = mc.params(chains=200, max_len=100, delta=1e-3, seed=9, table=1, accumulator=1)
+    x1 = mc.mcmi_walk_dump(B, pk, np.arange(m.n), 4000)
+    x2 = mc.mcmi_walk_dump(B, pk, np.arange(m.n), 4000)
+    for x, y in zip(x1, x2):
+        assert np.array_equal(x["visits"], y["visits"])
+        assert np.allclose(x["val"], y["val"], rtol=1e-6, atol=1e-6 * np.abs(x["val"]).max())
+
+
+def test_builds_are_bit_reproducible():
+    m = synth.stencil3d_7pt(10, seed=4)
+    B = mc.DeviceCsr.from_host(m)
+    p = mc.params(chains=256, max_len=128, delta=1e-2, top_k=16, seed=3)
+    r1 = [t.cpu().numpy() for t in mc.mcmi_build_ex(B, p).to_torch()]
+    r2 = [t.cpu().numpy() for t in mc.mcmi_build_ex(B, p).to_torch()]
+    for u, v in zip(r1, r2):
+        assert np.array_equal(u, v)
 
 
 # ------------------------------------------------------------------ build (filter + CSR)
@@ -188,6 +211,9 @@ def test_build_staging_regrowth_reruns_rows():
     m = synth.powerlaw_random(2048, seed=8)
     M, rp, col, val = _check_build(m, np.arange(0, m.n, 37), 64, 40, 1e-3, 0.0, 0)
     assert M.stats.deferred_rows > 0
+    # re-run rows are counted once
+    orows, _, _ = _orc().walk(m, chains=64, max_len=40, delta=1e-3, seed=11, table=M.stats.table)
+    assert M.stats.steps == sum(r["steps"] for r in orows)
 
 
 def test_build_row_range():
