@@ -186,6 +186,29 @@ mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *o
                               double *out_s, uint32_t *out_slot, uint32_t *out_a,
                               uint32_t *out_b, uint32_t *out_c, void *stream);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this is a
+ * service for callers that must not allocate device memory at the point of
+ * the call (a caller on a latency budget, where an allocation may block on
+ * the driver; a program that hands out all of its device memory up front
+ * from its own arena; a fixed-size device heap).
+ *
+ * mcmi_exclusive_scan_noalloc: offsets[i] = counts[0] + ... + counts[i-1]
+ * for i = 0..n, so offsets[n] is the total -- the step that turns per-row
+ * entry counts into CSR row pointers.  counts: device int32[n]; offsets:
+ * device int64[n+1]; both owned by the caller.  Asynchronous on `stream`.
+ * It calls no allocator: its scratch is a fixed device array of 16385
+ * int64 words (128 KB) that every GPU loading this library keeps until the
+ * process exits, so n may be at most 33,554,432; larger n returns
+ * MCMI_ERR_ARG with a message naming the limit.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's partial sums:
+ * calls that may overlap on the GPU (other streams, other host threads)
+ * race and must be ordered by the caller.
+ * --------------------------------------------------------------------- */
+mcmi_status mcmi_exclusive_scan_noalloc(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
+
 /* Library version string. */
 const char *mcmi_version(void);
 

@@ -78,8 +78,9 @@ def load():
     lib.mcmi_version.restype = C.c_char_p
     lib.mcmi_walk_dump.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, i64, i64, P, P, P, P, P, P]
     lib.mcmi_debug_tables.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, P, P, P, P, P, P]
+    lib.mcmi_exclusive_scan_noalloc.argtypes = [P, i64, P, P]
     for f in ("mcmi_build", "mcmi_build_ex", "mcmi_matrix_csr", "mcmi_matrix_copy", "mcmi_apply",
-              "mcmi_walk_dump", "mcmi_debug_tables"):
+              "mcmi_walk_dump", "mcmi_debug_tables", "mcmi_exclusive_scan_noalloc"):
         getattr(lib, f).restype = C.c_int
     _lib = lib
     return lib
@@ -218,6 +219,14 @@ def mcmi_debug_tables(B: DeviceCsr, p: mcmi_params, stream=None):
     torch.cuda.synchronize()
     u = lambda t: t.cpu().numpy().view(np.uint32)
     return dict(d=d.cpu().numpy(), s=s.cpu().numpy(), slot=u(slot).reshape(n, 16), a=u(a), b=u(b), c=u(c))
+
+
+def mcmi_exclusive_scan_noalloc(counts, offsets, stream=None):
+    """offsets[i] = sum(counts[:i]) for i = 0..n, without any allocation in
+    the library (for callers that cannot allocate device memory; scratch is a
+    fixed 128 KB device array, n <= 33,554,432; overlapping calls race)."""
+    _check(load().mcmi_exclusive_scan_noalloc(_ptr(counts), counts.numel(), _ptr(offsets), _stream(stream)))
+    return offsets
 
 
 def version() -> str:

@@ -374,6 +374,8 @@ void reset_queue(DevState *st, cudaStream_t s)
 
 }  // namespace
 
+void mcmi::set_error_message(const char *msg) { g_err = msg; }
+
 extern "C" {
 
 const char *mcmi_last_error(void) { return g_err.c_str(); }

@@ -30,6 +30,9 @@ size_t scan_tmp_elems(int64_t n);
 cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t *st_off, const int32_t *st_cnt,
                             const uint32_t *st_col, const float *st_val, int32_t *out_col, float *out_val,
                             cudaStream_t s);
+// message returned by mcmi_last_error() on this host thread
+void set_error_message(const char *msg);
+
 cudaError_t launch_spmv(int64_t rows, const int64_t *rp, const int32_t *col, const float *val, const float *x,
                         float *y, cudaStream_t s);
 
