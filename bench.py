@@ -160,12 +160,19 @@ def _cpu_baseline(m, w, seconds, table):
     sized to about `seconds` of CPU work."""
     import oracle
     cores = os.cpu_count() or 1
-    probe = np.arange(0, m.n, max(1, m.n // 256))[:256]
-    t0 = time.perf_counter()
-    oracle.build(m, rows=probe, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
-                 tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    nrows = int(min(m.n, max(256, len(probe) * seconds / dt)))
+
+    def run(nr):
+        rows = np.linspace(0, m.n - 1, nr).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.build(m, rows=rows, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
+                     tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+        return time.perf_counter() - t0
+    # per-row cost from two probe sizes (each call also builds the tables of
+    # the whole matrix, a fixed cost)
+    n1, n2 = min(m.n, 256), min(m.n, 2048)
+    t1, t2 = run(n1), run(n2)
+    per_row = max((t2 - t1) / max(n2 - n1, 1), 1e-7)
+    nrows = int(min(m.n, max(n2, seconds / per_row)))
     rows = np.linspace(0, m.n - 1, nrows).astype(np.int64)
     t0 = time.perf_counter()
     _, _, _, steps = oracle.build(m, rows=rows, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
@@ -185,12 +192,17 @@ def run_reference(a):
     table = 0 if (m.nnz - m.n) <= 6 * m.n else 1
     cores = os.cpu_count() or 1
     budget = 150.0 / max(1, a.steps + a.warmup)
-    probe = np.arange(0, m.n, max(1, m.n // 128))[:128]
-    t0 = time.perf_counter()
-    oracle.build(m, rows=probe, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
-                 tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    nrows = int(min(m.n, max(128, len(probe) * budget / dt)))
+
+    def run(nr):
+        rr = np.linspace(0, m.n - 1, nr).astype(np.int64)
+        t0 = time.perf_counter()
+        oracle.build(m, rows=rr, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
+                     tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+        return time.perf_counter() - t0
+    n1, n2 = min(m.n, 128), min(m.n, 1024)
+    t1, t2 = run(n1), run(n2)
+    per_row = max((t2 - t1) / max(n2 - n1, 1), 1e-7)
+    nrows = int(min(m.n, max(n2, budget / per_row)))
     rows = np.linspace(0, m.n - 1, nrows).astype(np.int64)
     times, tot = [], 0
     for it in range(a.warmup + a.steps):
@@ -335,6 +347,19 @@ def run_ours(a):
             "bytes_per_unit": "64 B (one 64-B row record, two 32-B sectors) per visited state",
             "walk_kernel_ms": walk_total_ms / max(1, len(walk_ms)),
             "walk_share_of_step": walk_total_ms / tot_ms if world == 1 else None}
+    # gather roofline (one 64-B row record per visited state): dependent
+    # random 64-B record reads over a buffer the size of the row records, at
+    # the walk's launch shape and at full occupancy (outside the timed region)
+    foot = SLOT_BYTES * m.n
+    try:
+        g_walk = mc.mcmi_gather_roofline(foot, 128, 6, 64)
+        g_full = mc.mcmi_gather_roofline(foot, 256, 8, 64)
+        visits_per_s = visits / (walk_total_ms / 1e3)
+        roof["gather"] = {"footprint_bytes": foot, "records_per_s_walk_shape": g_walk,
+                          "records_per_s_full_occupancy": g_full, "walk_visits_per_s": visits_per_s,
+                          "frac_walk_shape": visits_per_s / g_walk, "frac_full_occupancy": visits_per_s / g_full}
+    except Exception as exc:  # measurement only
+        roof["gather"] = {"error": str(exc)}
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = _cpu_baseline(m, w, a.cpu_seconds, last.table)

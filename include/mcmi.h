@@ -148,6 +148,22 @@ mcmi_status mcmi_matrix_copy(mcmi_matrix M, int64_t *row_ptr, int32_t *col, floa
  * Asynchronous on `stream`.                                               */
 mcmi_status mcmi_apply(mcmi_matrix M, const float *x, float *y, void *stream);
 
+/* Krylov judge of the preconditioner (the paper tests its preconditioners
+ * with GMRES and BiCGstab, Sec. VI; the GPU path keeps FP64 for this
+ * residual): solve B x = b with right preconditioning B M y = b, x = M y.
+ * method: MCMI_SOLVE_BICGSTAB or MCMI_SOLVE_GMRES (restarted every
+ * `restart` inner iterations; 0 = 30).  B: device CSR (FP64); M: handle
+ * from mcmi_build* or NULL (no preconditioner; rows outside a row-range M
+ * act as identity); b: device double[n]; x: device double[n], output
+ * (starts from 0).  Stops when the recurrence's residual norm reaches
+ * rtol ||b|| or after maxit iterations (BiCGstab: full iterations; GMRES:
+ * inner iterations).  *iters (host) = iterations done; *relres (host) =
+ * the true FP64 residual ||b - B x|| / ||b|| recomputed at exit.
+ * Synchronises `stream`; allocates its work vectors stream-ordered.      */
+enum { MCMI_SOLVE_BICGSTAB = 0, MCMI_SOLVE_GMRES = 1 };
+mcmi_status mcmi_solve(const mcmi_csr *B, mcmi_matrix M, const double *b, double *x, int method, double rtol,
+                       int32_t maxit, int32_t restart, int32_t *iters, double *relres, void *stream);
+
 /* Release a handle (stream-ordered on the stream it was built on).  NULL ok. */
 void mcmi_free(mcmi_matrix M);
 
@@ -185,6 +201,19 @@ mcmi_status mcmi_walk_dump(const mcmi_csr *B, const mcmi_params *p, const int64_
 mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *out_d,
                               double *out_s, uint32_t *out_slot, uint32_t *out_a,
                               uint32_t *out_b, uint32_t *out_c, void *stream);
+
+/* Gather roofline probe (measurement; the walk's access pattern without its
+ * arithmetic).  Fills a device buffer of footprint_bytes with random
+ * 64-byte records, then every thread of blocks_per_sm x SMs blocks of
+ * threads_per_block threads follows two chains of `steps` dependent random
+ * record reads (two 256-bit loads per record, the next index taken from the
+ * record read).  *records_per_s (host) receives the rate, timed with CUDA
+ * events on `stream`.  Allocates and frees its buffer stream-ordered;
+ * synchronises `stream`.  Errors: MCMI_ERR_ARG (footprint < 4096, bad
+ * launch shape), MCMI_ERR_OOM, MCMI_ERR_CUDA.  The paper names random
+ * memory access as the method's limiter (Sec. I, Sec. IV-B).             */
+mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int threads_per_block, int blocks_per_sm,
+                                 int steps, double *records_per_s, void *stream);
 
 /* ---------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a

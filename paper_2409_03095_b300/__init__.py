@@ -79,6 +79,10 @@ def load():
     lib.mcmi_walk_dump.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, i64, i64, P, P, P, P, P, P]
     lib.mcmi_debug_tables.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, P, P, P, P, P, P]
     lib.mcmi_exclusive_scan_noalloc.argtypes = [P, i64, P, P]
+    lib.mcmi_gather_roofline.argtypes = [u64, i32, i32, i32, C.POINTER(f64), P]
+    lib.mcmi_gather_roofline.restype = C.c_int
+    lib.mcmi_solve.argtypes = [C.POINTER(mcmi_csr), P, P, P, C.c_int, f64, i32, i32, C.POINTER(i32), C.POINTER(f64), P]
+    lib.mcmi_solve.restype = C.c_int
     for f in ("mcmi_build", "mcmi_build_ex", "mcmi_matrix_csr", "mcmi_matrix_copy", "mcmi_apply",
               "mcmi_walk_dump", "mcmi_debug_tables", "mcmi_exclusive_scan_noalloc"):
         getattr(lib, f).restype = C.c_int
@@ -227,6 +231,27 @@ def mcmi_exclusive_scan_noalloc(counts, offsets, stream=None):
     fixed 128 KB device array, n <= 33,554,432; overlapping calls race)."""
     _check(load().mcmi_exclusive_scan_noalloc(_ptr(counts), counts.numel(), _ptr(offsets), _stream(stream)))
     return offsets
+
+
+SOLVE_BICGSTAB, SOLVE_GMRES = 0, 1
+
+
+def mcmi_solve(B: DeviceCsr, M, b, x, method=SOLVE_BICGSTAB, rtol=1e-8, maxit=10000, restart=30, stream=None):
+    """Right-preconditioned BiCGstab / GMRES(restart) on the device (FP64).
+    M: Matrix or None.  Returns (iterations, true relative residual)."""
+    it, rr = C.c_int32(), C.c_double()
+    _check(load().mcmi_solve(C.byref(B.c), M.h if M is not None else None, _ptr(b), _ptr(x), method, rtol, maxit,
+                             restart, C.byref(it), C.byref(rr), _stream(stream)))
+    return it.value, rr.value
+
+
+def mcmi_gather_roofline(footprint_bytes, threads_per_block=128, blocks_per_sm=6, steps=64, stream=None):
+    """Random dependent 64-byte record reads per second over a buffer of the
+    given size at the given occupancy (the walk's access pattern)."""
+    r = C.c_double()
+    _check(load().mcmi_gather_roofline(int(footprint_bytes), threads_per_block, blocks_per_sm, steps, C.byref(r),
+                                       _stream(stream)))
+    return r.value
 
 
 def version() -> str:
