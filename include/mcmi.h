@@ -91,6 +91,8 @@ typedef struct {
     int32_t accumulator; /* MCMI_ACC_*: row sums exact in 64-bit fixed point (default) or FP32 Kahan */
     int64_t row_begin;   /* build rows [row_begin, row_end) only; both 0 = all rows */
     int64_t row_end;
+    int32_t chains_per_thread; /* chains each walk thread advances in turn: 1 or 2 (0 = auto) */
+    int32_t reserved2;
 } mcmi_params;
 
 /* Counters of the last build (all optional outputs).                      */
@@ -131,6 +133,44 @@ mcmi_status mcmi_build(const mcmi_csr *B, double eps, double delta, int32_t chai
 /* As mcmi_build with every parameter given; `stats` may be NULL.           */
 mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
                           mcmi_matrix *M_out, mcmi_stats *stats);
+
+/* Result of mcmi_autotune.                                                */
+typedef struct {
+    int32_t threads;            /* walk threads per block chosen */
+    int32_t chains_per_thread;  /* chains each thread advances */
+    int32_t hash_log2;          /* on-chip accumulator slots (log2) */
+    int32_t table;              /* sampling table type */
+    int32_t trials;             /* configurations timed */
+    float best_ms;              /* walk time of the sample rows, best configuration */
+    float default_ms;           /* same with the defaults (128 threads, 1 chain, 2^11, cumulative) */
+    int32_t reserved;
+    int64_t sample_rows;        /* rows in the timed sample */
+} mcmi_tune_result;
+
+/* Autotuner: times the walk kernel (CUDA events) on a contiguous sample of
+ * about 1/32 of the rows (2048 to 65536 rows, from the middle of the build's
+ * row range) for every launch shape (threads per block 64/128/256, 1 or 2
+ * chains per thread), on-chip accumulator size (2^10 .. 2^13 slots) and --
+ * when p->table is MCMI_TABLE_AUTO -- both table types, with p's other
+ * parameters, and writes the fastest choice into p->threads,
+ * p->chains_per_thread, p->hash_log2 and p->table.  p: in/out (host);
+ * res: optional (host).  Synchronises `stream`; allocates stream-ordered
+ * scratch.  Errors as mcmi_build_ex.                                      */
+mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_tune_result *res);
+
+/* Batched build of `count` independent matrices (each n >= 1) with the same
+ * parameters: the matrices are gathered into one block-diagonal CSR so that
+ * one persistent walk launch drains the rows of all of them from a single
+ * device queue; the walk and the row-offset scan run as one CUDA graph.  A
+ * row's random numbers are keyed by its index inside its own matrix, so
+ * Ms[b] equals what mcmi_build_ex gives for Bs[b] alone with the same
+ * parameters and table type.  If p->threads, p->chains_per_thread and
+ * p->hash_log2 are all 0, mcmi_autotune picks them (and the table type if
+ * AUTO) on the batch.  Bs: host array of device CSRs; Ms: host array of
+ * `count` handles, set on success (NULL on error); stats: optional
+ * aggregate.  Row ranges are not allowed.  Synchronises `stream`.       */
+mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_params *p, void *stream,
+                               mcmi_matrix *Ms, mcmi_stats *stats);
 
 /* Device CSR of M (library-owned, valid until mcmi_free): rows
  * [row_begin, row_end) of the build, columns global, entries sorted by

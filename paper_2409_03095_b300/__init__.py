@@ -38,7 +38,8 @@ class mcmi_params(C.Structure):
     _fields_ = [("eps", C.c_double), ("delta", C.c_double), ("filter_tau", C.c_double), ("alpha", C.c_double),
                 ("seed", C.c_uint64), ("chains", C.c_int32), ("max_len", C.c_int32), ("top_k", C.c_int32),
                 ("precision", C.c_int32), ("table", C.c_int32), ("threads", C.c_int32), ("hash_log2", C.c_int32),
-                ("accumulator", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64)]
+                ("accumulator", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64),
+                ("chains_per_thread", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class mcmi_stats(C.Structure):
@@ -47,6 +48,15 @@ class mcmi_stats(C.Structure):
                 ("spilled", C.c_int64), ("deferred_rows", C.c_int64), ("ms_prepare", C.c_float),
                 ("ms_walk", C.c_float), ("ms_assemble", C.c_float), ("ms_walk_kernel", C.c_float),
                 ("launches", C.c_int32), ("reserved", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
+class mcmi_tune_result(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("chains_per_thread", C.c_int32), ("hash_log2", C.c_int32),
+                ("table", C.c_int32), ("trials", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float),
+                ("reserved", C.c_int32), ("sample_rows", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -83,6 +93,10 @@ def load():
     lib.mcmi_gather_roofline.restype = C.c_int
     lib.mcmi_solve.argtypes = [C.POINTER(mcmi_csr), P, P, P, C.c_int, f64, i32, i32, C.POINTER(i32), C.POINTER(f64), P]
     lib.mcmi_solve.restype = C.c_int
+    lib.mcmi_autotune.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, C.POINTER(mcmi_tune_result)]
+    lib.mcmi_autotune.restype = C.c_int
+    lib.mcmi_build_batched.argtypes = [P, i32, C.POINTER(mcmi_params), P, P, C.POINTER(mcmi_stats)]
+    lib.mcmi_build_batched.restype = C.c_int
     for f in ("mcmi_build", "mcmi_build_ex", "mcmi_matrix_csr", "mcmi_matrix_copy", "mcmi_apply",
               "mcmi_walk_dump", "mcmi_debug_tables", "mcmi_exclusive_scan_noalloc"):
         getattr(lib, f).restype = C.c_int
@@ -181,6 +195,17 @@ def mcmi_build_ex(B: DeviceCsr, p: mcmi_params, stream=None) -> Matrix:
     return Matrix(h, st)
 
 
+def mcmi_build_batched(Bs, p: mcmi_params, stream=None):
+    """Build preconditioners of several matrices in one batched launch.
+    Returns (list of Matrix, aggregate mcmi_stats)."""
+    arr = (mcmi_csr * len(Bs))(*[B.c for B in Bs])
+    hs = (C.c_void_p * len(Bs))()
+    st = mcmi_stats()
+    _check(load().mcmi_build_batched(C.cast(arr, C.c_void_p), len(Bs), C.byref(p), _stream(stream),
+                                     C.cast(hs, C.c_void_p), C.byref(st)))
+    return [Matrix(C.c_void_p(h)) for h in hs], st
+
+
 def mcmi_apply(M: Matrix, x, y, stream=None):
     _check(load().mcmi_apply(M.h, _ptr(x), _ptr(y), _stream(stream)))
     return y
@@ -231,6 +256,14 @@ def mcmi_exclusive_scan_noalloc(counts, offsets, stream=None):
     fixed 128 KB device array, n <= 33,554,432; overlapping calls race)."""
     _check(load().mcmi_exclusive_scan_noalloc(_ptr(counts), counts.numel(), _ptr(offsets), _stream(stream)))
     return offsets
+
+
+def mcmi_autotune(B: DeviceCsr, p: mcmi_params, stream=None):
+    """Times walk configurations on a row sample and writes the fastest into
+    p (threads, chains_per_thread, hash_log2, table); returns the report."""
+    res = mcmi_tune_result()
+    _check(load().mcmi_autotune(C.byref(B.c), C.byref(p), _stream(stream), C.byref(res)))
+    return res
 
 
 SOLVE_BICGSTAB, SOLVE_GMRES = 0, 1

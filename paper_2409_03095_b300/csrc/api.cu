@@ -190,7 +190,12 @@ mcmi_status check_params(const mcmi_params *p)
     if (p->chains == 0 && !(p->eps > 0.0)) return fail(MCMI_ERR_ARG, "chains == 0 needs eps > 0");
     if (p->precision != 32 && p->precision != 64) return fail(MCMI_ERR_ARG, "precision must be 32 or 64");
     if (p->table < -1 || p->table > 1) return fail(MCMI_ERR_ARG, "unknown table type");
-    if (p->threads != 0 && p->threads != 64 && p->threads != 128) return fail(MCMI_ERR_ARG, "threads must be 0, 64 or 128");
+    if (p->chains_per_thread < 0 || p->chains_per_thread > 2)
+        return fail(MCMI_ERR_ARG, "chains_per_thread must be 0, 1 or 2");
+    if (p->threads != 0 && p->threads != 64 && p->threads != 128 && p->threads != 256)
+        return fail(MCMI_ERR_ARG, "threads must be 0, 64, 128 or 256");
+    if (p->threads == 256 && p->chains_per_thread == 2)
+        return fail(MCMI_ERR_ARG, "256 threads per block need chains_per_thread 1");
     if (p->hash_log2 != 0 && (p->hash_log2 < 6 || p->hash_log2 > 13)) return fail(MCMI_ERR_ARG, "hash_log2 out of [6, 13]");
     if (p->accumulator != MCMI_ACC_FIXED64 && p->accumulator != MCMI_ACC_KAHAN32)
         return fail(MCMI_ERR_ARG, "unknown accumulator");
@@ -281,13 +286,16 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
 }
 
 struct WalkPlan {
-    int threads = 256, log2H = 12, log2G = 8, grid = 1;
+    int threads = 128, cpt = 2, log2H = 11, log2G = 8, grid = 1;
 };
 
 mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, bool dump, WalkPlan &W)
 {
-    // two chains per thread: 128 threads keep 256 chains of a row in flight
-    W.threads = p->threads ? p->threads : (P.N > 128 ? 128 : 64);
+    // default: 128 threads with one chain each (8 blocks = 8 rows in flight
+    // per SM with a 2^11-slot table); the autotuner may pick 2 chains per
+    // thread or other block sizes
+    W.cpt = p->chains_per_thread ? p->chains_per_thread : 1;
+    W.threads = p->threads ? p->threads : 128;
     // distinct columns a row can reach: at most N (Lb + 1) visits, at most n columns
     const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
     const uint64_t distinct = reach < (uint64_t)P.n ? reach : (uint64_t)P.n;
@@ -303,7 +311,7 @@ mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, boo
     int l2 = ceil_log2(2 * distinct + 2);
     W.log2G = l2 < 8 ? 8 : l2;
     int bps = 0;
-    cudaError_t e = walk_occupancy(p->precision, P.table, p->accumulator, dump, W.threads, W.log2H, &bps);
+    cudaError_t e = walk_occupancy(p->precision, P.table, p->accumulator, dump, W.cpt, W.threads, W.log2H, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "walk occupancy");
     if (bps < 1) return fail(MCMI_ERR_ARG, "walk kernel does not fit (threads %d, hash 2^%d)", W.threads, W.log2H);
     int dev = 0, sms = 0;
@@ -372,7 +380,112 @@ void reset_queue(DevState *st, cudaStream_t s)
     cudaMemsetAsync(&st->work, 0, sizeof(unsigned long long), s);
 }
 
+// One timed walk launch over rows [rb, re) with plan W (autotuner trial).
+mcmi_status time_walk(const mcmi_params *p, const Prepared &P, const WalkPlan &W, int64_t rb, int64_t re,
+                      cudaStream_t s, float *ms)
+{
+    Scratch S(s);
+    WalkArgs a;
+    fill_walk_args(a, p, P, W);
+    a.row_begin = rb;
+    a.row_end = re;
+    mcmi_status r = alloc_overflow(S, W, a, s);
+    if (r != MCMI_OK) return r;
+    const int64_t rows = re - rb;
+    const uint64_t per_row = p->top_k > 0 ? (uint64_t)(p->top_k + 1) : 512;
+    a.st_cap = (uint64_t)rows * per_row + 1024;
+    a.st_col = S.get<uint32_t>(a.st_cap);
+    a.st_val = S.get<float>(a.st_cap);
+    a.row_off = S.get<int64_t>(rows);
+    a.row_cnt = S.get<int32_t>(rows);
+    a.deferred_list = S.get<int64_t>(rows);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (autotune)");
+    cudaMemsetAsync(&P.st->cursor, 0, 8, s);
+    cudaMemsetAsync(&P.st->deferred, 0, 8, s);
+    reset_queue(P.st, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.cpt, W.grid, W.threads, s);
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    cudaEventElapsedTime(ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(e, "walk kernel (autotune)");
+    DevState h;
+    return read_state(P.st, &h, s);
+}
+
 }  // namespace
+
+extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_tune_result *res)
+{
+    mcmi_status r = check_csr(B);
+    if (r == MCMI_OK) r = check_params(p);
+    if (r != MCMI_OK) return r;
+    if (B->n == 0) return fail(MCMI_ERR_ARG, "empty matrix");
+    const int64_t n = B->n;
+    const int64_t rb0 = (p->row_begin == 0 && p->row_end == 0) ? 0 : p->row_begin;
+    const int64_t re0 = (p->row_begin == 0 && p->row_end == 0) ? n : p->row_end;
+    if (rb0 < 0 || re0 <= rb0 || re0 > n) return fail(MCMI_ERR_ARG, "bad row range");
+    cudaStream_t s = (cudaStream_t)stream;
+    // sample: a contiguous window of about 1/32 of the rows (2048 .. 65536) in the middle
+    int64_t ns = (re0 - rb0) / 32;
+    ns = ns < 2048 ? 2048 : (ns > 65536 ? 65536 : ns);
+    if (ns > re0 - rb0) ns = re0 - rb0;
+    const int64_t sb = rb0 + (re0 - rb0 - ns) / 2, se = sb + ns;
+    struct Shape { int threads, cpt; } shapes[] = {{128, 1}, {256, 1}, {128, 2}, {64, 2}};
+    const int hashes[] = {10, 11, 12, 13};
+    int tables[2] = {MCMI_TABLE_CUMULATIVE, MCMI_TABLE_ALIAS};
+    const int ntab = p->table == MCMI_TABLE_AUTO ? 2 : 1;
+    if (p->table != MCMI_TABLE_AUTO) tables[0] = p->table;
+    float best = 1e30f, dflt = -1.0f;
+    mcmi_params bestp = *p;
+    int trials = 0;
+    for (int ti = 0; ti < ntab; ++ti) {
+        mcmi_params q = *p;
+        q.table = tables[ti];
+        Scratch S(s);
+        if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+        Prepared P;
+        r = prepare(B, &q, s, S, P, false);
+        if (r != MCMI_OK) return r;
+        for (const Shape &sh : shapes)
+            for (int hl : hashes) {
+                q.threads = sh.threads;
+                q.chains_per_thread = sh.cpt;
+                q.hash_log2 = hl;
+                WalkPlan W;
+                if (plan_walk(&q, P, ns, false, W) != MCMI_OK) continue;   // does not fit
+                float ms = 0.0f;
+                r = time_walk(&q, P, W, sb, se, s, &ms);
+                if (r != MCMI_OK) return r;
+                ++trials;
+                if (sh.threads == 128 && sh.cpt == 1 && hl == 11 && ti == 0) dflt = ms;
+                if (ms < best) {
+                    best = ms;
+                    bestp = q;
+                }
+            }
+    }
+    p->threads = bestp.threads;
+    p->chains_per_thread = bestp.chains_per_thread;
+    p->hash_log2 = bestp.hash_log2;
+    p->table = bestp.table;
+    if (res) {
+        res->threads = bestp.threads;
+        res->chains_per_thread = bestp.chains_per_thread;
+        res->hash_log2 = bestp.hash_log2;
+        res->table = bestp.table;
+        res->trials = trials;
+        res->best_ms = best;
+        res->default_ms = dflt;
+        res->sample_rows = ns;
+    }
+    return MCMI_OK;
+}
 
 void mcmi::set_error_message(const char *msg) { g_err = msg; }
 
@@ -479,7 +592,7 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
     if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (staging)"));
     reset_queue(P.st, s);
     cudaEventRecord(ev[4], s);
-    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.grid, W.threads, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.cpt, W.grid, W.threads, s);
     if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch"));
     cudaEventRecord(ev[5], s);
     ++launches;
@@ -511,7 +624,7 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
         reset_queue(P.st, s);
         WalkPlan W2 = W;
         W2.grid = (int)(deferred < W.grid ? deferred : W.grid);
-        e = launch_walk(a, p->precision, P.table, p->accumulator, false, W2.grid, W2.threads, s);
+        e = launch_walk(a, p->precision, P.table, p->accumulator, false, W2.cpt, W2.grid, W2.threads, s);
         if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch (deferred rows)"));
         ++launches;
         r = read_state(P.st, &h, s);
@@ -574,6 +687,228 @@ mcmi_status mcmi_build(const mcmi_csr *B, double eps, double delta, int32_t chai
     p.filter_tau = filter_tau;
     p.seed = seed;
     return mcmi_build_ex(B, &p, stream, M_out, nullptr);
+}
+
+mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_params *p_in, void *stream,
+                               mcmi_matrix *Ms, mcmi_stats *stats)
+{
+    if (!Bs || !Ms || count < 1) return fail(MCMI_ERR_ARG, "batched build needs count >= 1 matrices and outputs");
+    for (int32_t b = 0; b < count; ++b) Ms[b] = nullptr;
+    mcmi_status r = check_params(p_in);
+    if (r != MCMI_OK) return r;
+    if (p_in->row_begin || p_in->row_end) return fail(MCMI_ERR_ARG, "row ranges do not apply to batched builds");
+    std::vector<BatchIn> in(count);
+    std::vector<int64_t> row_base(count + 1), nnz_base(count + 1);
+    int64_t tn = 0, tz = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        r = check_csr(&Bs[b]);
+        if (r != MCMI_OK) return fail(r, "matrix %d: %s", b, g_err.c_str());
+        if (Bs[b].n < 1) return fail(MCMI_ERR_ARG, "matrix %d is empty", b);
+        in[b] = BatchIn{Bs[b].row_ptr, Bs[b].col, Bs[b].val, Bs[b].n, Bs[b].nnz, tn, tz};
+        row_base[b] = tn;
+        nnz_base[b] = tz;
+        tn += Bs[b].n;
+        tz += Bs[b].nnz;
+    }
+    row_base[count] = tn;
+    nnz_base[count] = tz;
+    if (tn >= (1ll << 31) - 1 || tz >= (1ll << 32)) return fail(MCMI_ERR_ARG, "batch too large (rows < 2^31, nnz < 2^32)");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    cudaEvent_t ev[6];
+    for (auto &e : ev) cudaEventCreate(&e);
+    struct EvGuard { cudaEvent_t *e; ~EvGuard() { for (int i = 0; i < 6; ++i) cudaEventDestroy(e[i]); } } evg{ev};
+    cudaEventRecord(ev[0], s);
+
+    // block-diagonal concatenation (global column = local column + row base)
+    BatchIn *d_in = S.get<BatchIn>(count);
+    int64_t *d_row_base = S.get<int64_t>(count + 1), *d_nnz_base = S.get<int64_t>(count + 1);
+    int64_t *rp_all = S.get<int64_t>(tn + 1);
+    int32_t *col_all = S.get<int32_t>(tz);
+    double *val_all = S.get<double>(tz);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (batch)");
+    cudaMemcpyAsync(d_in, in.data(), sizeof(BatchIn) * count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_row_base, row_base.data(), 8 * (count + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_nnz_base, nnz_base.data(), 8 * (count + 1), cudaMemcpyHostToDevice, s);
+    cudaError_t e = launch_concat(d_in, count, d_row_base, d_nnz_base, tn, tz, rp_all, col_all, val_all, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batch concatenation");
+    mcmi_csr Ball{tn, tz, rp_all, col_all, val_all};
+    int launches = 2;
+
+    // launch shape: the autotuner, unless the caller fixed it
+    mcmi_params q = *p_in;
+    mcmi_tune_result tune{};
+    if (q.threads == 0 && q.chains_per_thread == 0 && q.hash_log2 == 0) {
+        r = mcmi_autotune(&Ball, &q, stream, &tune);
+        if (r != MCMI_OK) return r;
+    }
+    Prepared P;
+    r = prepare(&Ball, &q, s, S, P, false);
+    if (r != MCMI_OK) return r;
+    launches += 3 + (q.alpha > 0.0 ? 1 : 0);
+    cudaEventRecord(ev[1], s);
+    WalkPlan W;
+    r = plan_walk(&q, P, tn, false, W);
+    if (r != MCMI_OK) return r;
+    WalkArgs a;
+    fill_walk_args(a, &q, P, W);
+    a.row_begin = 0;
+    a.row_end = tn;
+    a.batch_row_base = d_row_base;
+    a.batch_count = count;
+    r = alloc_overflow(S, W, a, s);
+    if (r != MCMI_OK) return r;
+    const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
+    const uint64_t distinct = reach < (uint64_t)tn ? reach : (uint64_t)tn;
+    uint64_t per_row = q.top_k > 0 ? (uint64_t)(q.top_k + 1) : 512;
+    if (per_row > distinct + 1) per_row = distinct + 1;
+    uint64_t cap = (uint64_t)tn * per_row + 1024;
+    if (q.top_k == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && cap * 8 > fr / 4) cap = fr / 32 + 1024;
+    }
+    a.st_col = S.get<uint32_t>(cap);
+    a.st_val = S.get<float>(cap);
+    a.st_cap = cap;
+    a.row_off = S.get<int64_t>(tn);
+    a.row_cnt = S.get<int32_t>(tn);
+    a.deferred_list = S.get<int64_t>(tn);
+    int64_t *rpM = S.get<int64_t>(tn + 1);
+    int64_t *tmp = S.get<int64_t>(scan_tmp_elems(tn));
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (batch staging)");
+
+    // walk + scan as one CUDA graph on a private stream ordered after `s`
+    cudaStream_t cs = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, ev[2], 0);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(&P.st->work, 0, 8, cs);
+        cudaMemsetAsync(&P.st->cursor, 0, 8, cs);
+        cudaMemsetAsync(&P.st->deferred, 0, 8, cs);
+        cudaEventRecord(ev[4], cs);
+        cudaError_t e1 = launch_walk(a, q.precision, P.table, q.accumulator, false, W.cpt, W.grid, W.threads, cs);
+        cudaEventRecord(ev[5], cs);
+        cudaError_t e2 = scan_counts(a.row_cnt, tn, rpM, tmp, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gexec, cs);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[3], 0);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    if (cs) {
+        cudaStreamSynchronize(cs);
+        cudaStreamDestroy(cs);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batched walk graph");
+    launches += 4;
+    DevState h;
+    r = read_state(P.st, &h, s);
+    if (r != MCMI_OK) return r;
+    const int64_t deferred = (int64_t)h.deferred;
+    if (deferred > 0) {
+        // rows whose output did not fit: run again (same walks) into a larger buffer
+        const uint64_t need = h.cursor + (uint64_t)deferred * (distinct + 1);
+        uint32_t *col2 = S.get<uint32_t>(need);
+        float *val2 = S.get<float>(need);
+        int64_t *list2 = S.get<int64_t>(deferred);
+        if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (staging regrowth)");
+        cudaMemcpyAsync(col2, a.st_col, cap * 4, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(val2, a.st_val, cap * 4, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(list2, a.deferred_list, deferred * 8, cudaMemcpyDeviceToDevice, s);
+        a.st_col = col2;
+        a.st_val = val2;
+        a.st_cap = need;
+        a.row_list = list2;
+        a.n_list = deferred;
+        a.out_by_row = 1;
+        a.count_steps = 0;
+        cudaMemsetAsync(&P.st->deferred, 0, 8, s);
+        reset_queue(P.st, s);
+        const int g2 = (int)(deferred < W.grid ? deferred : W.grid);
+        e = launch_walk(a, q.precision, P.table, q.accumulator, false, W.cpt, g2, W.threads, s);
+        if (e == cudaSuccess) e = scan_counts(a.row_cnt, tn, rpM, tmp, s);
+        if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch (deferred rows)");
+        launches += 4;
+        r = read_state(P.st, &h, s);
+        if (r != MCMI_OK) return r;
+        if (h.deferred) return fail(MCMI_ERR_CAPACITY, "staging buffer still full");
+    }
+    // batched M, then one CSR per matrix
+    std::vector<int64_t> nnzM_base(count + 1);
+    for (int32_t b = 0; b <= count; ++b)
+        cudaMemcpyAsync(&nnzM_base[b], rpM + row_base[b], 8, cudaMemcpyDeviceToHost, s);
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "nnz read");
+    const int64_t nnzM = nnzM_base[count];
+    int32_t *colM = S.get<int32_t>(nnzM);
+    float *valM = S.get<float>(nnzM);
+    BatchOut *d_out = S.get<BatchOut>(count);
+    int64_t *d_nnzM_base = S.get<int64_t>(count + 1);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (batched M)");
+    e = launch_assemble(tn, rpM, a.row_off, a.row_cnt, a.st_col, a.st_val, colM, valM, s);
+    if (e != cudaSuccess) return cuda_fail(e, "assembly");
+    std::vector<BatchOut> out(count);
+    std::vector<mcmi_matrix> made;
+    auto undo = [&](mcmi_status st) {
+        for (auto m : made) mcmi_free(m);
+        for (int32_t b = 0; b < count; ++b) Ms[b] = nullptr;
+        return st;
+    };
+    for (int32_t b = 0; b < count; ++b) {
+        mcmi_matrix M = new mcmi_matrix_s();
+        M->rows = Bs[b].n;
+        M->row_begin = 0;
+        M->n_cols = Bs[b].n;
+        M->nnz = nnzM_base[b + 1] - nnzM_base[b];
+        M->stream = s;
+        cudaGetDevice(&M->device);
+        M->rp = S.get<int64_t>(M->rows + 1);
+        M->col = S.get<int32_t>(M->nnz);
+        M->val = S.get<float>(M->nnz);
+        made.push_back(M);
+        if (S.err != cudaSuccess) return undo(cuda_fail(S.err, "allocation (outputs)"));
+        S.keep(M->rp);
+        S.keep(M->col);
+        S.keep(M->val);
+        out[b] = BatchOut{M->rp, M->col, M->val, M->rows, row_base[b], nnzM_base[b]};
+    }
+    cudaMemcpyAsync(d_out, out.data(), sizeof(BatchOut) * count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_nnzM_base, nnzM_base.data(), 8 * (count + 1), cudaMemcpyHostToDevice, s);
+    e = launch_split(d_out, count, d_row_base, d_nnzM_base, tn, nnzM, rpM, colM, valM, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return undo(cuda_fail(e, "batch split"));
+    launches += 3;
+    for (int32_t b = 0; b < count; ++b) Ms[b] = made[b];
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->steps = h.steps;
+        stats->rows = tn;
+        stats->nnz = nnzM;
+        stats->max_s = P.smax;
+        stats->chains = P.N;
+        stats->max_len_bound = P.Lb;
+        stats->table = P.table;
+        stats->hash_log2 = W.log2H;
+        stats->spilled = (int64_t)h.spilled;
+        stats->deferred_rows = deferred;
+        cudaEventElapsedTime(&stats->ms_prepare, ev[0], ev[1]);
+        // the walk, timed by the event nodes inside the graph (else the whole graph)
+        if (cudaEventElapsedTime(&stats->ms_walk_kernel, ev[4], ev[5]) != cudaSuccess) {
+            cudaGetLastError();
+            cudaEventElapsedTime(&stats->ms_walk_kernel, ev[2], ev[3]);
+        }
+        cudaEventElapsedTime(&stats->ms_walk, ev[2], ev[3]);
+        stats->launches = launches;
+    }
+    return MCMI_OK;
 }
 
 mcmi_status mcmi_matrix_csr(mcmi_matrix M, int64_t *rows, int64_t *row_begin, int64_t *nnz,
@@ -659,7 +994,7 @@ mcmi_status mcmi_walk_dump(const mcmi_csr *B, const mcmi_params *p, const int64_
     a.d_cap = cap;
     a.row_steps = out_steps;
     reset_queue(P.st, s);
-    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, true, W.grid, W.threads, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, true, W.cpt, W.grid, W.threads, s);
     if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     DevState h;
     return read_state(P.st, &h, s);

@@ -19,9 +19,10 @@ void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const doubl
                    cudaStream_t s);
 
 size_t walk_smem_bytes(int precision, int log2H, bool dump);
-cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int threads, int log2H, int *blocks_per_sm);
-cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int grid, int threads,
-                        cudaStream_t s);
+cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int cpt, int threads, int log2H,
+                           int *blocks_per_sm);
+cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int cpt, int grid,
+                        int threads, cudaStream_t s);
 
 // exclusive scan of int32 counts into int64 offsets (out has n+1 entries)
 cudaError_t scan_counts(const int32_t *counts, int64_t n, int64_t *out, int64_t *block_tmp, cudaStream_t s);
@@ -32,6 +33,26 @@ cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t 
                             cudaStream_t s);
 // message returned by mcmi_last_error() on this host thread
 void set_error_message(const char *msg);
+
+// batched builds: one matrix of the batch, in and out
+struct BatchIn {
+    const int64_t *rp;
+    const int32_t *col;
+    const double *val;
+    int64_t n, nnz, row_base, nnz_base;
+};
+struct BatchOut {
+    int64_t *rp;
+    int32_t *col;
+    float *val;
+    int64_t n, row_base, nnz_base;   // nnz_base: first entry of this matrix in the batched M
+};
+cudaError_t launch_concat(const BatchIn *in, int count, const int64_t *row_base, const int64_t *nnz_base,
+                          int64_t total_rows, int64_t total_nnz, int64_t *rp, int32_t *col, double *val,
+                          cudaStream_t s);
+cudaError_t launch_split(const BatchOut *out, int count, const int64_t *row_base, const int64_t *nnzM_base,
+                         int64_t total_rows, int64_t total_nnz, const int64_t *rpM, const int32_t *colM,
+                         const float *valM, cudaStream_t s);
 
 cudaError_t launch_spmv(int64_t rows, const int64_t *rp, const int32_t *col, const float *val, const float *x,
                         float *y, cudaStream_t s);

@@ -64,6 +64,8 @@ struct WalkArgs {
     int64_t n_list;
     int out_by_row;               // list mode: outputs indexed by row - row_begin
     int count_steps;              // add the rows' transitions to the device counter
+    const int64_t *batch_row_base; // block-diagonal batch: first row of each matrix (nullptr: one matrix)
+    int batch_count;
     int32_t N, L;
     float delta_f;                // smallest float >= delta
     int fix_shift;                // fixed-point accumulator scale: weight w is added as round(w 2^F)

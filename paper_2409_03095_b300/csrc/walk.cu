@@ -151,8 +151,8 @@ __device__ __forceinline__ void load_slot(const uint4 *sp, uint32_t (&w)[16])
 
 }  // namespace
 
-template <int PREC, int TABLE, int ACC, bool DUMP>
-__global__ void __launch_bounds__(kWalkThreadsMax, kWalkMinBlocks) k_walk(WalkArgs a)
+template <int PREC, int TABLE, int ACC, bool DUMP, int CPT>
+__global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk(WalkArgs a)
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kWalkThreadsMax, kWalkMinBlocks) k_walk(WalkAr
         return PREC == 64 ? s_aux[p] : reinterpret_cast<uint32_t *>(s_val + p)[1];
     };
 
-    __shared__ long long s_row, s_pos;
+    __shared__ long long s_row, s_pos, s_key_row;
     __shared__ int s_next_chain;
     __shared__ uint32_t s_nspill, s_fill, s_wpos, s_ncand;
     __shared__ long long s_off;
@@ -255,7 +255,18 @@ __global__ void __launch_bounds__(kWalkThreadsMax, kWalkMinBlocks) k_walk(WalkAr
             const long long pos = (long long)atomicAdd(&a.st->work, 1ull);
             s_pos = pos < total ? pos : -1;
             s_row = pos < total ? (a.row_list ? a.row_list[pos] : a.row_begin + pos) : -1;
-            s_next_chain = 2 * B;   // chains tid and tid + B start at once
+            // random-number key of the row: its index inside its own matrix
+            // when several matrices are built as one block-diagonal batch
+            s_key_row = s_row;
+            if (s_row >= 0 && a.batch_row_base) {
+                int lo = 0, hi = a.batch_count - 1;   // last matrix whose first row <= s_row
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.batch_row_base[mid] <= s_row) lo = mid; else hi = mid - 1;
+                }
+                s_key_row = s_row - a.batch_row_base[lo];
+            }
+            s_next_chain = CPT * B;   // chains tid, tid + B, ... start at once
             if (s_row >= 0) {
                 // t = 0 visits of all N chains: weight 1 at the row itself
                 const uint32_t r = (uint32_t)s_row;
@@ -280,19 +291,19 @@ __global__ void __launch_bounds__(kWalkThreadsMax, kWalkMinBlocks) k_walk(WalkAr
         const long long row = s_row, pos = s_pos;
         if (row < 0) break;
         const long long idx = (a.row_list && !a.out_by_row) ? pos : row - a.row_begin;
-        const uint32_t rlo = (uint32_t)row, rhi = (uint32_t)((unsigned long long)row >> 32);
+        const uint32_t rlo = (uint32_t)s_key_row, rhi = (uint32_t)((unsigned long long)s_key_row >> 32);
 
         // ---- walks (Eq. 2): each thread advances two chains in turn, so that
         // two dependent gathers are in flight per thread; a chain that stops
         // is replaced by the row's next chain index ----
         unsigned long long my_steps = 0;
-        uint32_t st[2];
-        float w[2];            // FP32 weight (the FP64 path keeps it as the stop shadow)
-        double w64[2];
-        uint4 r4[2];
-        int t[2], k[2];
+        uint32_t st[CPT];
+        float w[CPT];            // FP32 weight (the FP64 path keeps it as the stop shadow)
+        double w64[CPT];
+        uint4 r4[CPT];
+        int t[CPT], k[CPT];
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < CPT; ++j) {
             k[j] = tid + j * B;
             st[j] = (uint32_t)row;
             w[j] = 1.0f;
@@ -301,17 +312,17 @@ __global__ void __launch_bounds__(kWalkThreadsMax, kWalkMinBlocks) k_walk(WalkAr
             r4[j] = make_uint4(0, 0, 0, 0);
         }
 #pragma unroll 1
-        while (k[0] < a.N || k[1] < a.N) {
-            uint32_t s[2][16];
-            double2 rd[2];
+        while (k[0] < a.N || (CPT > 1 && k[CPT - 1] < a.N)) {
+            uint32_t s[CPT][16];
+            double2 rd[CPT];
 #pragma unroll
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < CPT; ++j)
                 if (k[j] < a.N) {
                     load_slot(a.slots + 4 * (size_t)st[j], s[j]);
                     if (PREC == 64) rd[j] = __ldg(a.rowd + st[j]);
                 }
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < CPT; ++j) {
                 if (k[j] >= a.N) continue;
                 if (t[j] > 0) {
                     if (FIX)
@@ -640,16 +651,6 @@ __global__ void __launch_bounds__(kWalkThreadsMax, kWalkMinBlocks) k_walk(WalkAr
     }
 }
 
-template <int PREC, int TABLE, int ACC, bool DUMP>
-static cudaError_t launch_walk_t(const WalkArgs &a, int grid, int threads, size_t smem, cudaStream_t s)
-{
-    auto fn = k_walk<PREC, TABLE, ACC, DUMP>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, threads, smem, s>>>(a);
-    return cudaGetLastError();
-}
-
 // per slot: 8-B value word, 4-B key, and 4 B of counts / candidate list where needed
 size_t walk_smem_bytes(int precision, int log2H, bool dump)
 {
@@ -657,45 +658,46 @@ size_t walk_smem_bytes(int precision, int log2H, bool dump)
 }
 
 namespace {
-template <bool DUMP>
-const void *walk_fn(int precision, int table, int acc)
+using WalkFn = void (*)(WalkArgs);
+
+template <bool D, int C>
+WalkFn pick_walk(int precision, int table, int acc)
 {
-    if (precision == 64) return table ? (const void *)k_walk<64, 1, MCMI_ACC_FIXED64, DUMP>
-                                      : (const void *)k_walk<64, 0, MCMI_ACC_FIXED64, DUMP>;
-    if (acc == MCMI_ACC_KAHAN32) return table ? (const void *)k_walk<32, 1, MCMI_ACC_KAHAN32, DUMP>
-                                              : (const void *)k_walk<32, 0, MCMI_ACC_KAHAN32, DUMP>;
-    return table ? (const void *)k_walk<32, 1, MCMI_ACC_FIXED64, DUMP> : (const void *)k_walk<32, 0, MCMI_ACC_FIXED64, DUMP>;
+    if (precision == 64) return table ? k_walk<64, 1, MCMI_ACC_FIXED64, D, C> : k_walk<64, 0, MCMI_ACC_FIXED64, D, C>;
+    if (acc == MCMI_ACC_KAHAN32) return table ? k_walk<32, 1, MCMI_ACC_KAHAN32, D, C> : k_walk<32, 0, MCMI_ACC_KAHAN32, D, C>;
+    return table ? k_walk<32, 1, MCMI_ACC_FIXED64, D, C> : k_walk<32, 0, MCMI_ACC_FIXED64, D, C>;
+}
+
+WalkFn walk_kernel(int precision, int table, int acc, bool dump, int cpt)
+{
+    if (cpt == 1) return dump ? pick_walk<true, 1>(precision, table, acc) : pick_walk<false, 1>(precision, table, acc);
+    return dump ? pick_walk<true, 2>(precision, table, acc) : pick_walk<false, 2>(precision, table, acc);
 }
 }  // namespace
 
-cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int threads, int log2H, int *blocks_per_sm)
+cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int cpt, int threads, int log2H,
+                           int *blocks_per_sm)
 {
     const size_t smem = walk_smem_bytes(precision, log2H, dump);
-    const void *fn = dump ? walk_fn<true>(precision, table, acc) : walk_fn<false>(precision, table, acc);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const WalkFn fn = walk_kernel(precision, table, acc, dump, cpt);
+    cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)fn, threads, smem);
 }
 
-cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int grid, int threads,
-                        cudaStream_t s)
+cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int cpt, int grid,
+                        int threads, cudaStream_t s)
 {
     const size_t smem = walk_smem_bytes(precision, a.log2H, dump);
-#define MCMI_L(P, T, A, D) return launch_walk_t<P, T, A, D>(a, grid, threads, smem, s)
-    if (precision == 64) {
-        if (table) { if (dump) MCMI_L(64, 1, 0, true); MCMI_L(64, 1, 0, false); }
-        if (dump) MCMI_L(64, 0, 0, true);
-        MCMI_L(64, 0, 0, false);
+    const WalkFn fn = walk_kernel(precision, table, acc, dump, cpt);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (cap == cudaStreamCaptureStatusNone) {   // during graph capture it was set by walk_occupancy
+        cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
-    if (acc == MCMI_ACC_KAHAN32) {
-        if (table) { if (dump) MCMI_L(32, 1, 1, true); MCMI_L(32, 1, 1, false); }
-        if (dump) MCMI_L(32, 0, 1, true);
-        MCMI_L(32, 0, 1, false);
-    }
-    if (table) { if (dump) MCMI_L(32, 1, 0, true); MCMI_L(32, 1, 0, false); }
-    if (dump) MCMI_L(32, 0, 0, true);
-    MCMI_L(32, 0, 0, false);
-#undef MCMI_L
+    fn<<<grid, threads, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace mcmi

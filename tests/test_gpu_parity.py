@@ -91,7 +91,9 @@ WALK_CASES = [
     ("rand_mixed", 64, 1, 100, 80, 1e-4, {}),
     ("rand_long", 32, 1, 128, 256, 1e-3, {}),
     ("rand_long", 32, 0, 128, 256, 1e-3, {"threads": 128}),
-    ("rand_long", 32, 1, 300, 256, 1e-3, {"threads": 64}),        # refill: 300 chains on 128 lanes
+    ("rand_long", 32, 1, 300, 256, 1e-3, {"threads": 64, "chains_per_thread": 2}),   # refill: 300 chains on 128 slots
+    ("stencil3d_12", 32, 0, 256, 128, 1e-2, {"threads": 256, "chains_per_thread": 1}),
+    ("stencil2d", 64, 1, 1000, 64, 1e-3, {"threads": 128, "chains_per_thread": 2}),
     ("powerlaw_4k", 32, 1, 128, 256, 1e-3, {}),
     ("powerlaw_4k", 32, 0, 128, 256, 1e-3, {"hash_log2": 6}),      # forces the global overflow table
     ("stencil2d", 32, 0, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 64}),
