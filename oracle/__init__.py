@@ -59,11 +59,17 @@ def _L():
         lib.orc_chains_from_eps.argtypes = [f64, f64]
         lib.orc_chains_from_eps.restype = i64
         lib.orc_walk_rows.argtypes = [i64, P, P, P, P, P, i32, P, i64, i64, i64, f64, u64, i64, i32,
-                                      P, P, P, P, P, P]
+                                      P, P, P, P, P, P, P]
         lib.orc_walk_rows.restype = i32
         lib.orc_build_rows.argtypes = [i64, P, P, P, P, P, i32, P, i64, i64, i64, f64, u64, f64, i64,
-                                       i64, i32, P, P, P, P]
+                                       i64, i32, P, P, P, P, P]
         lib.orc_build_rows.restype = i32
+        lib.orc_learned_tables.argtypes = [i64, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_learned_tables.restype = i32
+        lib.orc_mlp_g.argtypes = [P, P]
+        lib.orc_mlp_g.restype = C.c_float
+        lib.orc_row_moments.argtypes = [i64, P, P, P, P, P, i32, P, i64, i64, i64, f64, u64, i32, P, P]
+        lib.orc_row_moments.restype = i32
         lib.orc_filter_row.argtypes = [i64, P, P, i64, f64, i64, P, P]
         lib.orc_filter_row.restype = i64
         lib.orc_spmv.argtypes = [i64, P, P, P, P, P]
@@ -171,15 +177,25 @@ def _rows(m, rows):
     return np.ascontiguousarray(rows, dtype=np.int64)
 
 
+def _theta(theta):
+    return None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+
+
+def _tp(theta):
+    return _p(theta) if theta is not None else None
+
+
 def walk(m, rows=None, chains=100, max_len=64, delta=1e-3, seed=1, table=TABLE_CUMULATIVE,
-         alpha=0.0, threads=0):
+         alpha=0.0, threads=0, theta=None):
     """Eq. 2 estimator, unfiltered: for each listed row a dict with the visited
     columns (sorted), X = (1/N) sum W, A = (1/N) sum |W|, V = visit counts,
-    and the number of transitions taken."""
+    and the number of transitions taken.  theta: learned-proposal parameters
+    (see learned_tables), None for p = |c|/s."""
     rp, col, val = _csr(m)
     d, s = split(m, alpha)
     rows = _rows(m, rows)
-    tb = max_walk_len(s.max() if m.n else 0.0, delta, max_len)
+    theta = _theta(theta)
+    tb = max_walk_len(s.max() if m.n else 0.0, delta, max_len) if theta is None else max_len
     cap = int(min(m.n, chains * (tb + 1)))
     nr = len(rows)
     count = np.zeros(nr, dtype=np.int64)
@@ -190,7 +206,7 @@ def walk(m, rows=None, chains=100, max_len=64, delta=1e-3, seed=1, table=TABLE_C
     oV = np.zeros(nr * cap, dtype=np.uint32)
     st = _L().orc_walk_rows(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), table, _p(rows), nr,
                             chains, max_len, delta, seed, cap, threads, _p(count), _p(steps),
-                            _p(oc), _p(oX), _p(oA), _p(oV))
+                            _p(oc), _p(oX), _p(oA), _p(oV), _tp(theta))
     if st:
         raise OracleError(st)
     out = []
@@ -212,14 +228,15 @@ def filter_row(i, cols, mvals, tau=0.0, top_k=0):
 
 
 def build(m, rows=None, chains=100, max_len=64, delta=1e-3, seed=1, tau=0.0, top_k=0,
-          table=TABLE_CUMULATIVE, alpha=0.0, threads=0):
+          table=TABLE_CUMULATIVE, alpha=0.0, threads=0, theta=None):
     """Preconditioner rows: Eq. 2 walks, column scaling by 1/d_j (phase 4),
     Sec. IV-B filter.  Returns (row_ptr, col, val, steps_per_row) for the
     listed rows (in the given order)."""
     rp, col, val = _csr(m)
     d, s = split(m, alpha)
     rows = _rows(m, rows)
-    tb = max_walk_len(s.max() if m.n else 0.0, delta, max_len)
+    theta = _theta(theta)
+    tb = max_walk_len(s.max() if m.n else 0.0, delta, max_len) if theta is None else max_len
     cap = int(min(m.n, chains * (tb + 1)))
     if top_k > 0:
         cap = min(cap, top_k + 1)
@@ -230,7 +247,7 @@ def build(m, rows=None, chains=100, max_len=64, delta=1e-3, seed=1, tau=0.0, top
     ov = np.zeros(nr * cap)
     st = _L().orc_build_rows(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), table, _p(rows), nr,
                              chains, max_len, delta, seed, tau, top_k, cap, threads,
-                             _p(count), _p(steps), _p(oc), _p(ov))
+                             _p(count), _p(steps), _p(oc), _p(ov), _tp(theta))
     if st:
         raise OracleError(st)
     orp = np.zeros(nr + 1, dtype=np.int64)
@@ -247,3 +264,70 @@ def spmv(rp, col, val, x):
     y = np.zeros(len(rp) - 1)
     _L().orc_spmv(len(rp) - 1, _p(rp), _p(col), _p(val), _p(x), _p(y))
     return y
+
+
+# ---------------------------------------------------------------- learned proposal
+# (an extension of the method: |c_ij| reweighted by an MLP g_ij > 0, weight
+#  update c_ij / p_ij with the table's own probability, so Eq. 2 stays unbiased)
+
+MLP_NPARAM = 32 * 8 + 32 + 32 * 32 + 32 + 32 + 1
+
+
+def learned_tables(m, theta, alpha=0.0):
+    """Integer weights q, factors f = c Q / q and MLP outputs g of every
+    off-diagonal entry (CSR order) under the learned proposal theta."""
+    rp, col, val = _csr(m)
+    d, s = split(m, alpha)
+    theta = _theta(theta)
+    noff = int(rp[-1]) - int(np.sum(col == np.repeat(np.arange(m.n), np.diff(rp))))
+    off = np.zeros(m.n + 1, dtype=np.int64)
+    Q = np.zeros(m.n, dtype=np.uint64)
+    q = np.zeros(max(noff, 1), dtype=np.uint32)
+    fac = np.zeros(max(noff, 1))
+    g = np.zeros(max(noff, 1), dtype=np.float32)
+    _L().orc_learned_tables(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), _p(theta), _p(off), _p(Q), _p(q),
+                            _p(fac), _p(g))
+    return dict(off=off, Q=Q, q=q[:noff], fac=fac[:noff], g=g[:noff], d=d, s=s)
+
+
+def mlp_g(theta, feat):
+    """The BF16 MLP of the learned proposal on one FP32 feature vector."""
+    theta = _theta(theta)
+    f = np.ascontiguousarray(feat, dtype=np.float32)
+    return float(_L().orc_mlp_g(_p(theta), _p(f)))
+
+
+def row_moments(m, rows=None, chains=64, max_len=64, delta=1e-3, seed=1, table=TABLE_CUMULATIVE, alpha=0.0,
+                theta=None, threads=0):
+    """m_i = (1/N) sum over the N chains of row i of sum_t W_t^2."""
+    rp, col, val = _csr(m)
+    d, s = split(m, alpha)
+    rows = _rows(m, rows)
+    theta = _theta(theta)
+    out = np.zeros(len(rows))
+    _L().orc_row_moments(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), table, _p(rows), len(rows), chains,
+                         max_len, delta, seed, threads, _p(out), _tp(theta))
+    return out
+
+
+def proposal_loss(theta, feat, row_of_edge, p_edge, m_edge):
+    """FP64 training loss of the learned proposal (no BF16 rounding):
+    mean over rows of (sum_j p g)(sum_j p m / g) / (sum_j p sqrt(m))^2, which
+    is >= 1 with equality iff g is proportional to sqrt(m) within each row
+    (Cauchy-Schwarz); p = |c|/s per edge, m = second moment of the target row."""
+    th = np.asarray(theta, dtype=np.float64)
+    W1, b1 = th[:256].reshape(32, 8), th[256:288]
+    W2, b2 = th[288:1312].reshape(32, 32), th[1312:1344]
+    w3, b3 = th[1344:1376], th[1376]
+    x = np.asarray(feat, dtype=np.float64)
+    h1 = np.maximum(x @ W1.T + b1, 0.0)
+    h2 = np.maximum(h1 @ W2.T + b2, 0.0)
+    z = h2 @ w3 + b3
+    g = np.clip(0.5 * (z + np.sqrt(z * z + 4.0)), 0.0625, 16.0)
+    r = np.asarray(row_of_edge, dtype=np.int64)
+    nr = int(r.max()) + 1 if r.size else 0
+    A = np.bincount(r, p_edge * g, nr)
+    Bv = np.bincount(r, p_edge * m_edge / g, nr)
+    Cv = np.bincount(r, p_edge * np.sqrt(m_edge), nr) ** 2
+    ok = Cv > 0
+    return float(np.mean(A[ok] * Bv[ok] / Cv[ok]))

@@ -247,6 +247,146 @@ int64_t orc_chains_from_eps(double eps, double smax)
 }
 
 /* ---------------------------------------------------------------------- */
+/* Learned proposal (an extension of the method, not in the paper): the    */
+/* transition weights |c_ij| are multiplied by g_ij > 0 from a small MLP of */
+/* per-edge features, and the weight update uses c_ij / p_ij with the      */
+/* table's own probability p_ij = q_ij / Q_i, so the estimator of Eq. 2     */
+/* stays unbiased.  The MLP is evaluated as a BF16 network: inputs, weights */
+/* and hidden activations rounded to bfloat16 (nearest, ties to even),      */
+/* products exact in FP32, sums in FP32 in index order, biases FP32.        */
+/* Parameters (FP32), in order: W1[32][8], b1[32], W2[32][32], b2[32],      */
+/* w3[32], b3.                                                              */
+/* ---------------------------------------------------------------------- */
+enum { MLP_IN = 8, MLP_H = 32, MLP_NPARAM = 32 * 8 + 32 + 32 * 32 + 32 + 32 + 1 };
+
+static float bf16_round(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    memcpy(&x, &u, 4);
+    return x;
+}
+
+/* g = squareplus(z) = (z + sqrt(z^2 + 4)) / 2, clamped to [1/16, 16]. */
+float orc_mlp_g(const float *th, const float *feat)
+{
+    const float *W1 = th, *b1 = th + 256, *W2 = th + 288, *b2 = th + 1312, *w3 = th + 1344, *b3 = th + 1376;
+    float x[MLP_IN], h1[MLP_H], h2[MLP_H];
+    for (int k = 0; k < MLP_IN; ++k) x[k] = bf16_round(feat[k]);
+    for (int o = 0; o < MLP_H; ++o) {
+        float acc = b1[o];
+        for (int k = 0; k < MLP_IN; ++k) acc = acc + bf16_round(W1[o * MLP_IN + k]) * x[k];
+        h1[o] = bf16_round(acc > 0.0f ? acc : 0.0f);
+    }
+    for (int o = 0; o < MLP_H; ++o) {
+        float acc = b2[o];
+        for (int k = 0; k < MLP_H; ++k) acc = acc + bf16_round(W2[o * MLP_H + k]) * h1[k];
+        h2[o] = bf16_round(acc > 0.0f ? acc : 0.0f);
+    }
+    float z = b3[0];
+    for (int k = 0; k < MLP_H; ++k) z = z + bf16_round(w3[k]) * h2[k];
+    float g = 0.5f * (z + sqrtf(z * z + 4.0f));
+    if (g < 0.0625f) g = 0.0625f;
+    if (g > 16.0f) g = 16.0f;
+    return g;
+}
+
+/* Features of edge (i, j): p_ij = |c_ij|/s_i, s_i, s_j, 1/deg_i, 1/deg_j,  */
+/* |d_i|/(|d_i|+|d_j|), |c_ij|/max_k|c_ik|, sign(c_ij); FP64 then FP32.     */
+static void edge_features(double c, double si, double sj, int64_t degi, int64_t degj, double di, double dj,
+                          double maxabs, float *f)
+{
+    f[0] = (float)(fabs(c) / si);
+    f[1] = (float)si;
+    f[2] = (float)sj;
+    f[3] = (float)(1.0 / (double)degi);
+    f[4] = degj > 0 ? (float)(1.0 / (double)degj) : 0.0f;
+    f[5] = (float)(fabs(di) / (fabs(di) + fabs(dj)));
+    f[6] = (float)(fabs(c) / maxabs);
+    f[7] = c < 0.0 ? -1.0f : 1.0f;
+}
+
+static int64_t off_degree(int64_t i, const int64_t *rp, const int32_t *col)
+{
+    int64_t m = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) m += col[k] != i;
+    return m;
+}
+
+/* Row i with a learned proposal: q_ij = max(1, floor(w_ij / sum_k w_ik 2^31))  */
+/* for w_ij = |c_ij| g_ij (0 if c_ij == 0); factor f_ij = c_ij Q_i / q_ij.       */
+static int64_t row_weights_learned(int64_t i, const int64_t *rp, const int32_t *col, const double *val,
+                                   const double *d, const double *s, const int64_t *deg, const float *th,
+                                   uint32_t *q, int32_t *cols, uint8_t *neg, double *fac, float *gout,
+                                   uint64_t *Q)
+{
+    const double di = d[i], si = s[i];
+    double maxabs = 0.0, wsum = 0.0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+        if (col[k] != i && fabs(-val[k] / di) > maxabs) maxabs = fabs(-val[k] / di);
+    int64_t m = 0;
+    double *w = (double *)malloc(sizeof(double) * (size_t)(rp[i + 1] - rp[i] + 1));
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        if (col[k] == i) continue;
+        const int64_t j = col[k];
+        const double c = -val[k] / di;
+        float g = 0.0f;
+        if (c != 0.0) {
+            float f[MLP_IN];
+            edge_features(c, si, s[j], deg[i], deg[j], di, d[j], maxabs, f);
+            g = orc_mlp_g(th, f);
+        }
+        if (gout) gout[m] = g;
+        w[m] = fabs(c) * (double)g;
+        wsum += w[m];
+        if (cols) cols[m] = (int32_t)j;
+        if (neg) neg[m] = c < 0.0;
+        ++m;
+    }
+    uint64_t tot = 0;
+    for (int64_t t = 0; t < m; ++t) {
+        uint32_t qq = 0;
+        if (w[t] > 0.0) {
+            const double x = floor(w[t] / wsum * 2147483648.0);
+            qq = (uint32_t)x;
+            if (qq < 1u) qq = 1u;
+        }
+        q[t] = qq;
+        tot += qq;
+    }
+    m = 0;
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+        if (col[k] == i) continue;
+        const double c = -val[k] / di;
+        fac[m] = q[m] > 0 ? (c * (double)tot) / (double)q[m] : 0.0;
+        ++m;
+    }
+    free(w);
+    *Q = tot;
+    return m;
+}
+
+/* Learned tables of every row (for the table-parity tests): per off-diagonal */
+/* entry in CSR order q, the factor f = c Q / q and g.                         */
+int orc_learned_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
+                       const double *s, const float *th, int64_t *off, uint64_t *Q, uint32_t *q, double *fac,
+                       float *g)
+{
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) deg[i] = off_degree(i, rp, col);
+    int64_t o = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        off[i] = o;
+        o += row_weights_learned(i, rp, col, val, d, s, deg, th, q + o, NULL, NULL, fac + o, g + o, &Q[i]);
+    }
+    off[n] = o;
+    free(deg);
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Eq. 2 walks.                                                           */
 /* ---------------------------------------------------------------------- */
 typedef struct {
@@ -255,6 +395,7 @@ typedef struct {
     const int32_t *col;
     const double *val;
     const double *d, *s;
+    const float *theta;   /* learned proposal parameters, or NULL for p = |c|/s */
     /* derived, per row: offsets into the off-diagonal arrays */
     int64_t *off;
     uint64_t *Q;
@@ -263,6 +404,7 @@ typedef struct {
     uint8_t *neg;
     uint32_t *prob;
     int32_t *alias;
+    double *fac;          /* learned proposal: weight factor c/p per entry */
 } orc_mat;
 
 static int mat_prepare(orc_mat *M, int table)
@@ -280,23 +422,33 @@ static int mat_prepare(orc_mat *M, int table)
     M->neg = (uint8_t *)malloc(sz);
     M->prob = table == ORC_TABLE_ALIAS ? (uint32_t *)malloc(sizeof(uint32_t) * sz) : NULL;
     M->alias = table == ORC_TABLE_ALIAS ? (int32_t *)malloc(sizeof(int32_t) * sz) : NULL;
+    M->fac = M->theta ? (double *)malloc(sizeof(double) * sz) : NULL;
+    int64_t *degs = NULL;
+    if (M->theta) {
+        degs = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+        for (int64_t i = 0; i < n; ++i) degs[i] = off_degree(i, M->rp, M->col);
+    }
     int64_t o = 0;
     for (int64_t i = 0; i < n; ++i) {
         M->off[i] = o;
-        int64_t deg = row_weights(i, M->rp, M->col, M->val, M->d, M->s, M->q + o, M->ocol + o,
-                                  M->neg + o, &M->Q[i]);
+        int64_t deg = M->theta
+                          ? row_weights_learned(i, M->rp, M->col, M->val, M->d, M->s, degs, M->theta, M->q + o,
+                                                M->ocol + o, M->neg + o, M->fac + o, NULL, &M->Q[i])
+                          : row_weights(i, M->rp, M->col, M->val, M->d, M->s, M->q + o, M->ocol + o, M->neg + o,
+                                        &M->Q[i]);
         if (table == ORC_TABLE_ALIAS && deg > 0)
             orc_alias_build(M->q + o, deg, M->Q[i], M->prob + o, M->alias + o);
         o += deg;
     }
     M->off[n] = o;
+    free(degs);
     return ORC_OK;
 }
 
 static void mat_release(orc_mat *M)
 {
     free(M->off); free(M->Q); free(M->q); free(M->ocol); free(M->neg);
-    free(M->prob); free(M->alias);
+    free(M->prob); free(M->alias); free(M->fac);
 }
 
 typedef struct {
@@ -346,11 +498,18 @@ static uint64_t walk_row(const orc_mat *M, int table, int64_t i, int64_t N, int6
             int64_t m = table == ORC_TABLE_ALIAS
                             ? pick_alias(r, deg, M->Q[state], M->prob + o, M->alias + o)
                             : pick_cumulative(r, M->q + o, deg, M->Q[state]);
-            double sj = M->s[state];
-            int negative = M->neg[o + m];
-            w = w * (negative ? -sj : sj);
-            float f32 = (float)sj;
-            w32 = w32 * (negative ? -f32 : f32);
+            if (M->fac) {
+                /* learned proposal: W <- W c/p with the table's probability */
+                const double f = M->fac[o + m];
+                w = w * f;
+                w32 = w32 * (float)f;
+            } else {
+                double sj = M->s[state];
+                int negative = M->neg[o + m];
+                w = w * (negative ? -sj : sj);
+                float f32 = (float)sj;
+                w32 = w32 * (negative ? -f32 : f32);
+            }
             state = M->ocol[o + m];
             ++t;
             acc_add(acc, state, w);
@@ -390,15 +549,66 @@ static void set_threads(int threads)
 #endif
 }
 
+/* Second moment of each listed row's chains, m_i = (1/N) sum_chains       */
+/* sum_t W_t^2 (the weights of Eq. 2 along each path, t = 0 included): the  */
+/* training signal of the learned proposal, whose variance-optimal one-step */
+/* choice is p_ij proportional to |c_ij| sqrt(m_j).                          */
+int orc_row_moments(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
+                    const double *s, int table, const int64_t *rows, int64_t nrows, int64_t N, int64_t L,
+                    double delta, uint64_t seed, int threads, double *m_out, const float *theta)
+{
+    orc_mat M = {n, rp, col, val, d, s, theta};
+    mat_prepare(&M, table);
+    set_threads(threads);
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < nrows; ++p) {
+        const int64_t i = rows[p];
+        double sum = 0.0;
+        for (int64_t k = 0; k < N; ++k) {
+            int64_t state = i, t = 0;
+            double w = 1.0;
+            float w32 = 1.0f;
+            uint32_t r4[4] = {0, 0, 0, 0};
+            sum += w * w;
+            while (t != L && !((double)fabsf(w32) < delta) && M.Q[state] != 0) {
+                if (t % 4 == 0) {
+                    uint32_t ctr[4] = {(uint32_t)(t / 4), (uint32_t)k, (uint32_t)i, (uint32_t)((uint64_t)i >> 32)};
+                    orc_philox4x32_10(ctr, key, r4);
+                }
+                const int64_t o = M.off[state], deg = M.off[state + 1] - o;
+                const int64_t m = table == ORC_TABLE_ALIAS
+                                      ? pick_alias(r4[t % 4], deg, M.Q[state], M.prob + o, M.alias + o)
+                                      : pick_cumulative(r4[t % 4], M.q + o, deg, M.Q[state]);
+                double f;
+                if (M.fac) {
+                    f = M.fac[o + m];
+                } else {
+                    f = M.neg[o + m] ? -M.s[state] : M.s[state];
+                }
+                w = w * f;
+                w32 = w32 * (M.fac ? (float)f : (M.neg[o + m] ? -(float)M.s[state] : (float)M.s[state]));
+                state = M.ocol[o + m];
+                ++t;
+                sum += w * w;
+            }
+        }
+        m_out[p] = sum / (double)N;
+    }
+    mat_release(&M);
+    return ORC_OK;
+}
+
 /* Raw accumulators of the listed rows: for row r (position p in rows[]),    */
 /* entries p*cap .. p*cap+count[p]-1 hold (column, X/N, A/N, V) sorted by    */
 /* column, where A is the sum of |W| (the scale used to judge cancellation). */
 int orc_walk_rows(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                   const double *d, const double *s, int table, const int64_t *rows, int64_t nrows,
                   int64_t N, int64_t L, double delta, uint64_t seed, int64_t cap, int threads,
-                  int64_t *count, uint64_t *steps, int32_t *ocol, double *oX, double *oA, uint32_t *oV)
+                  int64_t *count, uint64_t *steps, int32_t *ocol, double *oX, double *oA, uint32_t *oV,
+                  const float *theta)
 {
-    orc_mat M = {n, rp, col, val, d, s};
+    orc_mat M = {n, rp, col, val, d, s, theta};
     mat_prepare(&M, table);
     int status = ORC_OK;
     set_threads(threads);
@@ -489,9 +699,9 @@ int orc_build_rows(int64_t n, const int64_t *rp, const int32_t *col, const doubl
                    const double *d, const double *s, int table, const int64_t *rows, int64_t nrows,
                    int64_t N, int64_t L, double delta, uint64_t seed, double tau, int64_t top_k,
                    int64_t cap, int threads, int64_t *count, uint64_t *steps,
-                   int32_t *out_col, double *out_val)
+                   int32_t *out_col, double *out_val, const float *theta)
 {
-    orc_mat M = {n, rp, col, val, d, s};
+    orc_mat M = {n, rp, col, val, d, s, theta};
     mat_prepare(&M, table);
     int status = ORC_OK;
     set_threads(threads);
