@@ -93,6 +93,7 @@ typedef struct {
     int64_t row_end;
     int32_t chains_per_thread; /* chains each walk thread advances in turn: 1 or 2 (0 = auto) */
     int32_t reserved2;
+    const struct mcmi_proposal_s *proposal; /* learned proposal (mcmi_proposal_*), NULL = p_ij = |c_ij|/s_i */
 } mcmi_params;
 
 /* Counters of the last build (all optional outputs).                      */
@@ -171,6 +172,65 @@ mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_
  * aggregate.  Row ranges are not allowed.  Synchronises `stream`.       */
 mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_params *p, void *stream,
                                mcmi_matrix *Ms, mcmi_stats *stats);
+
+/* ---------------------------------------------------------------------
+ * Learned proposal (an extension, not in the paper).  An 8-32-32-1 MLP
+ * evaluated as a BF16 network (inputs, weights and hidden activations
+ * rounded to bfloat16, exact products, FP32 sums in index order, FP32
+ * biases) maps edge features -- p_ij = |c_ij|/s_i, s_i, s_j, 1/deg_i,
+ * 1/deg_j, |d_i|/(|d_i|+|d_j|), |c_ij|/max_k|c_ik|, sign(c_ij) -- to
+ * g_ij = squareplus(z) clamped to [1/16, 16].  The table samples
+ * q_ij proportional to |c_ij| g_ij and the walk multiplies the weight by
+ * c_ij Q_i / q_ij, so the Eq. 2 estimator stays unbiased.  Set
+ * mcmi_params.proposal to use it (precision 32; alias tables).
+ * Parameters (MCMI_MLP_PARAMS floats): W1[32][8], b1[32], W2[32][32],
+ * b2[32], w3[32], b3.
+ * --------------------------------------------------------------------- */
+#define MCMI_MLP_PARAMS 1377
+typedef struct mcmi_proposal_s *mcmi_proposal;
+
+/* params: host float[MCMI_MLP_PARAMS], or NULL for the default start
+ * (Glorot-uniform weights from a fixed sequence, zero biases).  Allocates
+ * the device copy with cudaMalloc on the current device.                */
+mcmi_status mcmi_proposal_create(const float *params, mcmi_proposal *out);
+/* Current parameters to host float[MCMI_MLP_PARAMS] (synchronous).        */
+mcmi_status mcmi_proposal_get(mcmi_proposal P, float *params);
+void mcmi_proposal_free(mcmi_proposal P);
+
+/* Training signal: m_i = (1/N) sum over row i's N chains of sum_t W_t^2
+ * (t = 0 included; the walks of p, same paths as mcmi_build_ex).
+ * m: device float[n].  Synchronises `stream`.                            */
+mcmi_status mcmi_row_moments(const mcmi_csr *B, const mcmi_params *p, float *m, void *stream);
+
+/* Training loss of the proposal on one matrix, given row moments m_rows
+ * (device float[n]): the mean over rows with edges of
+ * (sum_j p_ij g_ij)(sum_j p_ij m_j / g_ij) / (sum_j p_ij sqrt(m_j))^2,
+ * >= 1, = 1 when g is proportional to sqrt(m) in every row (the
+ * second-moment-optimal one-step proposal).  *loss (host); grad (host
+ * float[MCMI_MLP_PARAMS] or NULL) receives d loss / d params (BF16
+ * roundings taken as identity).  round_bf16 = 0 runs the network in FP32.
+ * p supplies alpha for the split.  Synchronises `stream`.               */
+mcmi_status mcmi_proposal_loss_grad(const mcmi_csr *B, const float *m_rows, const mcmi_params *p, mcmi_proposal P,
+                                    int round_bf16, float *loss, float *grad, void *stream);
+
+typedef struct {
+    int32_t steps;      /* Adam steps over the whole training set */
+    float lr;           /* Adam learning rate */
+    int32_t chains;     /* chains per row for the row moments */
+    int32_t max_len;    /* walk length limit for the row moments */
+    double delta;       /* weight cutoff for the row moments */
+    double alpha;       /* Eq. 1 augmentation of the training matrices */
+    uint64_t seed;      /* Philox key of the walks */
+    int32_t round_bf16; /* 1: train the BF16 network used at inference */
+    int32_t reserved;
+} mcmi_train_params;
+
+/* Train P in place on `count` matrices (device CSRs): row moments from the
+ * |c|-proposal walks, then tp->steps Adam steps on the loss above, with
+ * the project's forward/backward kernels.  loss_history: host
+ * float[tp->steps] or NULL.  Synchronises `stream`.                      */
+mcmi_status mcmi_proposal_train(const mcmi_csr *Bs, int32_t count, const mcmi_train_params *tp, mcmi_proposal P,
+                                float *loss_history, void *stream);
 
 /* Device CSR of M (library-owned, valid until mcmi_free): rows
  * [row_begin, row_end) of the build, columns global, entries sorted by

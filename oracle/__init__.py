@@ -70,6 +70,8 @@ def _L():
         lib.orc_mlp_g.restype = C.c_float
         lib.orc_row_moments.argtypes = [i64, P, P, P, P, P, i32, P, i64, i64, i64, f64, u64, i32, P, P]
         lib.orc_row_moments.restype = i32
+        lib.orc_train_edges.argtypes = [i64, P, P, P, P, P, P, P, P, P]
+        lib.orc_train_edges.restype = i32
         lib.orc_filter_row.argtypes = [i64, P, P, i64, f64, i64, P, P]
         lib.orc_filter_row.restype = i64
         lib.orc_spmv.argtypes = [i64, P, P, P, P, P]
@@ -331,3 +333,17 @@ def proposal_loss(theta, feat, row_of_edge, p_edge, m_edge):
     Cv = np.bincount(r, p_edge * np.sqrt(m_edge), nr) ** 2
     ok = Cv > 0
     return float(np.mean(A[ok] * Bv[ok] / Cv[ok]))
+
+
+def train_edges(m, alpha=0.0):
+    """Training edges in CSR order: features (FP32), p = |c|/s (FP64), target
+    column and row (diagonal slots: p = 0)."""
+    rp, col, val = _csr(m)
+    d, s = split(m, alpha)
+    E = int(rp[-1])
+    feat = np.zeros((max(E, 1), 8), dtype=np.float32)
+    p = np.zeros(max(E, 1))
+    tgt = np.zeros(max(E, 1), dtype=np.int64)
+    row = np.zeros(max(E, 1), dtype=np.int64)
+    _L().orc_train_edges(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), _p(feat), _p(p), _p(tgt), _p(row))
+    return feat[:E], p[:E], tgt[:E], row[:E]

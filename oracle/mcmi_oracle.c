@@ -386,6 +386,34 @@ int orc_learned_tables(int64_t n, const int64_t *rp, const int32_t *col, const d
     return ORC_OK;
 }
 
+/* Training edges in CSR order (diagonal slots are dummies with p = 0):      */
+/* features, p_ij = |c_ij|/s_i, the target column j and the row i.           */
+int orc_train_edges(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
+                    const double *s, float *feat, double *p, int64_t *target, int64_t *row)
+{
+    int64_t *deg = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t i = 0; i < n; ++i) deg[i] = off_degree(i, rp, col);
+    for (int64_t i = 0; i < n; ++i) {
+        double maxabs = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (col[k] != i && fabs(-val[k] / d[i]) > maxabs) maxabs = fabs(-val[k] / d[i]);
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            row[k] = i;
+            target[k] = col[k];
+            const double c = col[k] == i ? 0.0 : -val[k] / d[i];
+            if (c == 0.0 || !(s[i] > 0.0)) {
+                for (int u = 0; u < MLP_IN; ++u) feat[8 * k + u] = 0.0f;
+                p[k] = 0.0;
+                continue;
+            }
+            edge_features(c, s[i], s[col[k]], deg[i], deg[col[k]], d[i], d[col[k]], maxabs, feat + 8 * k);
+            p[k] = fabs(c) / s[i];
+        }
+    }
+    free(deg);
+    return ORC_OK;
+}
+
 /* ---------------------------------------------------------------------- */
 /* Eq. 2 walks.                                                           */
 /* ---------------------------------------------------------------------- */

@@ -39,7 +39,13 @@ class mcmi_params(C.Structure):
                 ("seed", C.c_uint64), ("chains", C.c_int32), ("max_len", C.c_int32), ("top_k", C.c_int32),
                 ("precision", C.c_int32), ("table", C.c_int32), ("threads", C.c_int32), ("hash_log2", C.c_int32),
                 ("accumulator", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64),
-                ("chains_per_thread", C.c_int32), ("reserved2", C.c_int32)]
+                ("chains_per_thread", C.c_int32), ("reserved2", C.c_int32), ("proposal", C.c_void_p)]
+
+
+class mcmi_train_params(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("lr", C.c_float), ("chains", C.c_int32), ("max_len", C.c_int32),
+                ("delta", C.c_double), ("alpha", C.c_double), ("seed", C.c_uint64), ("round_bf16", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class mcmi_stats(C.Structure):
@@ -97,6 +103,17 @@ def load():
     lib.mcmi_autotune.restype = C.c_int
     lib.mcmi_build_batched.argtypes = [P, i32, C.POINTER(mcmi_params), P, P, C.POINTER(mcmi_stats)]
     lib.mcmi_build_batched.restype = C.c_int
+    lib.mcmi_proposal_create.argtypes = [P, C.POINTER(P)]
+    lib.mcmi_proposal_get.argtypes = [P, P]
+    lib.mcmi_proposal_free.argtypes = [P]
+    lib.mcmi_proposal_free.restype = None
+    lib.mcmi_row_moments.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, P]
+    lib.mcmi_proposal_loss_grad.argtypes = [C.POINTER(mcmi_csr), P, C.POINTER(mcmi_params), P, C.c_int,
+                                            C.POINTER(C.c_float), P, P]
+    lib.mcmi_proposal_train.argtypes = [P, i32, C.POINTER(mcmi_train_params), P, P, P]
+    for f in ("mcmi_proposal_create", "mcmi_proposal_get", "mcmi_row_moments", "mcmi_proposal_loss_grad",
+              "mcmi_proposal_train"):
+        getattr(lib, f).restype = C.c_int
     for f in ("mcmi_build", "mcmi_build_ex", "mcmi_matrix_csr", "mcmi_matrix_copy", "mcmi_apply",
               "mcmi_walk_dump", "mcmi_debug_tables", "mcmi_exclusive_scan_noalloc"):
         getattr(lib, f).restype = C.c_int
@@ -127,6 +144,8 @@ def params(**kw) -> mcmi_params:
     for k, v in kw.items():
         if not hasattr(p, k):
             raise TypeError(f"unknown parameter {k}")
+        if k == "proposal" and hasattr(v, "h"):
+            v = v.h
         setattr(p, k, v)
     return p
 
@@ -264,6 +283,62 @@ def mcmi_autotune(B: DeviceCsr, p: mcmi_params, stream=None):
     res = mcmi_tune_result()
     _check(load().mcmi_autotune(C.byref(B.c), C.byref(p), _stream(stream), C.byref(res)))
     return res
+
+
+MLP_PARAMS = 1377
+
+
+class Proposal:
+    """Learned proposal (BF16 MLP over edge features); pass as
+    params(proposal=P.h) or use P.params(...)."""
+
+    def __init__(self, params=None):
+        self.h = C.c_void_p()
+        arr = None
+        if params is not None:
+            arr = np.ascontiguousarray(params, dtype=np.float32)
+            assert arr.size == MLP_PARAMS
+        _check(load().mcmi_proposal_create(arr.ctypes.data_as(C.c_void_p) if arr is not None else None,
+                                           C.byref(self.h)))
+
+    def get(self):
+        out = np.zeros(MLP_PARAMS, dtype=np.float32)
+        _check(load().mcmi_proposal_get(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
+
+    def close(self):
+        if self.h:
+            load().mcmi_proposal_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mcmi_row_moments(B: DeviceCsr, p: mcmi_params, stream=None):
+    import torch
+    m = torch.zeros(B.n, dtype=torch.float32, device="cuda")
+    _check(load().mcmi_row_moments(C.byref(B.c), C.byref(p), _ptr(m), _stream(stream)))
+    return m
+
+
+def mcmi_proposal_loss_grad(B: DeviceCsr, m_rows, p: mcmi_params, P: Proposal, round_bf16=1, grad=True, stream=None):
+    loss = C.c_float()
+    g = np.zeros(MLP_PARAMS, dtype=np.float32) if grad else None
+    _check(load().mcmi_proposal_loss_grad(C.byref(B.c), _ptr(m_rows), C.byref(p), P.h, round_bf16, C.byref(loss),
+                                          g.ctypes.data_as(C.c_void_p) if grad else None, _stream(stream)))
+    return loss.value, g
+
+
+def mcmi_proposal_train(Bs, tp: mcmi_train_params, P: Proposal, stream=None):
+    arr = (mcmi_csr * len(Bs))(*[B.c for B in Bs])
+    hist = np.zeros(max(tp.steps, 1), dtype=np.float32)
+    _check(load().mcmi_proposal_train(C.cast(arr, C.c_void_p), len(Bs), C.byref(tp), P.h,
+                                      hist.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return hist[:tp.steps]
 
 
 SOLVE_BICGSTAB, SOLVE_GMRES = 0, 1

@@ -163,6 +163,8 @@ struct Prepared {
     uint4 *slots = nullptr;
     uint32_t *a = nullptr, *b = nullptr, *c = nullptr;
     uint4 *bkt = nullptr;
+    uint4 *lbkt = nullptr;       // learned proposal: 32-byte buckets
+    bool learned = false;
     double2 *rowd = nullptr;
     double smax = 0.0, smin = 0.0;
     int table = MCMI_TABLE_CUMULATIVE;
@@ -201,6 +203,8 @@ mcmi_status check_params(const mcmi_params *p)
         return fail(MCMI_ERR_ARG, "unknown accumulator");
     if (p->accumulator == MCMI_ACC_KAHAN32 && p->precision != 32)
         return fail(MCMI_ERR_ARG, "the Kahan FP32 accumulator needs precision 32");
+    if (p->proposal && p->precision != 32) return fail(MCMI_ERR_ARG, "a learned proposal needs precision 32");
+    if (p->proposal && !p->proposal->d_params) return fail(MCMI_ERR_ARG, "proposal has no parameters");
     return MCMI_OK;
 }
 
@@ -247,7 +251,9 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     // load per step); long rows the alias table (two loads, no search)
     int table = p->table;
     if (table == MCMI_TABLE_AUTO) table = (nnz - (int64_t)h.ndiag) <= 6 * n ? MCMI_TABLE_CUMULATIVE : MCMI_TABLE_ALIAS;
+    if (p->proposal) table = MCMI_TABLE_ALIAS;   // learned proposals use 32-byte alias buckets
     P.table = table;
+    P.learned = p->proposal != nullptr;
     if (p->chains > 0) {
         P.N = p->chains;
     } else {
@@ -255,7 +261,8 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
         const double N = std::ceil(v * v);
         P.N = N > (double)(1 << 24) ? (1 << 24) : (int32_t)N;
     }
-    P.Lb = walk_len_bound(smax, p->delta, p->max_len);
+    // learned weights are not bounded by max_i s_i: no shorter bound than L
+    P.Lb = P.learned ? p->max_len : walk_len_bound(smax, p->delta, p->max_len);
     P.slots = S.get<uint4>((size_t)n * 4);
     P.a = S.get<uint32_t>(nnz);
     P.b = S.get<uint32_t>(nnz);
@@ -269,14 +276,27 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
         lstk = S.get<uint32_t>(nnz);
     }
     if (p->precision == 64) P.rowd = S.get<double2>(n);
+    int *deg = nullptr;
+    if (P.learned) {
+        P.lbkt = S.get<uint4>((size_t)nnz * 2);
+        deg = S.get<int>(n);
+    }
     if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
     if (keep_debug) {
         cudaMemsetAsync(P.a, 0, nnz * 4, s);
         cudaMemsetAsync(P.b, 0, nnz * 4, s);
         cudaMemsetAsync(P.c, 0, nnz * 4, s);
     }
-    launch_tables(n, B->row_ptr, B->col, B->val, P.d, P.s, table, P.slots, P.a, P.b, P.c, P.bkt, wscr, sstk,
-                  lstk, P.rowd, s);
+    if (P.learned) {
+        // the network's inference fused into the table build
+        launch_degree(n, B->row_ptr, B->col, deg, s);
+        launch_tables_learned(n, B->row_ptr, B->col, B->val, P.d, P.s, deg, p->proposal->d_params, P.slots, P.a,
+                              P.b, P.c, P.lbkt, wscr, sstk, lstk, s);
+        S.release(deg);
+    } else {
+        launch_tables(n, B->row_ptr, B->col, B->val, P.d, P.s, table, P.slots, P.a, P.b, P.c, P.bkt, wscr, sstk,
+                      lstk, P.rowd, s);
+    }
     if (wscr) S.release(wscr);
     if (sstk) S.release(sstk);
     if (lstk) S.release(lstk);
@@ -330,6 +350,8 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     a.ool_a = P.a;
     a.ool_b = P.b;
     a.ool_bkt = P.bkt;
+    a.lbkt = P.lbkt;
+    a.w_limit = 1024.0f;
     a.rowd = P.rowd;
     a.N = P.N;
     a.L = p->max_len;
@@ -345,8 +367,10 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     // of every accumulated weight below 2^-25 relative: weights are >= delta
     // until the last step of a chain, which is >= delta * min_i s_i.  A small
     // F keeps most weights below 2^32, so the high-word atomic is rare.
+    // A learned proposal's weights may exceed 1: 10 more bits of head-room,
+    // and the kernel reports MCMI_ERR_CAPACITY if |W| ever passes 1024.
     const double visits = (double)P.N * (double)(P.Lb + 1) + 1.0;
-    const int Fmax = 62 - (int)std::ceil(std::log2(visits));
+    const int Fmax = 62 - (int)std::ceil(std::log2(visits)) - (P.learned ? 10 : 0);
     int F = Fmax;
     const double wmin = p->delta * (double)(float)P.smin;
     if (wmin > 0.0) {
@@ -1024,6 +1048,201 @@ mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *o
     cudaMemcpyAsync(out_c, P.c, nnz * 4, cudaMemcpyDeviceToDevice, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "table export");
+    return MCMI_OK;
+}
+
+// ---------------------------------------------------------------- learned proposal
+
+mcmi_status mcmi_proposal_create(const float *params, mcmi_proposal *out)
+{
+    if (!out) return fail(MCMI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    mcmi_proposal P = new mcmi_proposal_s();
+    if (params) {
+        memcpy(P->h_params, params, sizeof(P->h_params));
+    } else {
+        // Glorot-uniform weights from a fixed split-mix sequence, zero biases:
+        // g starts near 1 (the |c| proposal)
+        uint64_t x = 0x9E3779B97F4A7C15ull;
+        auto next = [&]() {
+            x += 0x9E3779B97F4A7C15ull;
+            uint64_t z = x;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return (double)((z ^ (z >> 31)) >> 11) * 0x1.0p-53;
+        };
+        memset(P->h_params, 0, sizeof(P->h_params));
+        const int lay[3][3] = {{0, 8, 32}, {288, 32, 32}, {1344, 32, 1}};   // offset, fan-in, fan-out
+        for (auto &L : lay) {
+            const double a = std::sqrt(6.0 / (L[1] + L[2]));
+            for (int i = 0; i < L[1] * L[2]; ++i) P->h_params[L[0] + i] = (float)((2.0 * next() - 1.0) * a);
+        }
+    }
+    cudaGetDevice(&P->device);
+    cudaError_t e = cudaMalloc(&P->d_params, kMlpParams * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(P->d_params, P->h_params, kMlpParams * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        if (P->d_params) cudaFree(P->d_params);
+        delete P;
+        return cuda_fail(e, "proposal parameters");
+    }
+    *out = P;
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_proposal_get(mcmi_proposal P, float *params)
+{
+    if (!P || !params) return fail(MCMI_ERR_ARG, "NULL argument");
+    cudaError_t e = cudaMemcpy(P->h_params, P->d_params, kMlpParams * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "proposal parameters");
+    memcpy(params, P->h_params, sizeof(P->h_params));
+    return MCMI_OK;
+}
+
+void mcmi_proposal_free(mcmi_proposal P)
+{
+    if (!P) return;
+    if (P->d_params) cudaFree(P->d_params);
+    delete P;
+}
+
+mcmi_status mcmi_row_moments(const mcmi_csr *B, const mcmi_params *p, float *m, void *stream)
+{
+    mcmi_status r = check_csr(B);
+    if (r == MCMI_OK) r = check_params(p);
+    if (r != MCMI_OK) return r;
+    if (!m) return fail(MCMI_ERR_ARG, "m is NULL");
+    if (B->n == 0) return MCMI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    Prepared P;
+    r = prepare(B, p, s, S, P, false);
+    if (r != MCMI_OK) return r;
+    WalkPlan W;
+    WalkArgs a;
+    fill_walk_args(a, p, P, W);
+    cudaMemsetAsync(m, 0, B->n * sizeof(float), s);
+    cudaError_t e = launch_row_moments(a, P.table, B->n, m, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "row moments");
+    return MCMI_OK;
+}
+
+namespace {
+
+// training edges of one matrix appended at edge_base / row_base
+mcmi_status train_edges_of(const mcmi_csr *B, const mcmi_params *p, const float *m_rows, int64_t row_base,
+                           int64_t edge_base, float *feat, float *pe, float *mt, int32_t *rid, cudaStream_t s)
+{
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    DevState *st = S.get<DevState>(1);
+    double *d = S.get<double>(B->n), *sv = S.get<double>(B->n);
+    int *deg = S.get<int>(B->n);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
+    cudaMemsetAsync(st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(&st->err, 0xFF, 8, s);
+    launch_validate(B->n, B->nnz, B->row_ptr, B->col, B->val, st, s);
+    if (p->alpha > 0.0) launch_rownorm(B->n, B->row_ptr, B->val, st, s);
+    launch_split(B->n, B->row_ptr, B->col, B->val, p->alpha, d, sv, st, s);
+    DevState h;
+    mcmi_status r = read_state(st, &h, s);
+    if (r != MCMI_OK) return r;
+    launch_degree(B->n, B->row_ptr, B->col, deg, s);
+    cudaError_t e = launch_train_edges(B->n, B->row_ptr, B->col, B->val, d, sv, deg, m_rows, row_base, edge_base, feat,
+                                       pe, mt, rid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "training edges");
+    return MCMI_OK;
+}
+
+}  // namespace
+
+mcmi_status mcmi_proposal_loss_grad(const mcmi_csr *B, const float *m_rows, const mcmi_params *p, mcmi_proposal P,
+                                    int round_bf16, float *loss, float *grad, void *stream)
+{
+    mcmi_status r = check_csr(B);
+    if (r == MCMI_OK) r = check_params(p);
+    if (r != MCMI_OK) return r;
+    if (!P || !m_rows || !loss || B->n == 0) return fail(MCMI_ERR_ARG, "bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    const int64_t E = B->nnz, R = B->n;
+    float *feat = S.get<float>(E * 8), *pe = S.get<float>(E), *mt = S.get<float>(E);
+    int32_t *rid = S.get<int32_t>(E);
+    float *A = S.get<float>(R), *Bs = S.get<float>(R), *Cs = S.get<float>(R), *lb = S.get<float>(2);
+    float *g = grad ? S.get<float>(kMlpParams) : nullptr;
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
+    r = train_edges_of(B, p, m_rows, 0, 0, feat, pe, mt, rid, s);
+    if (r != MCMI_OK) return r;
+    cudaError_t e = train_pass(E, R, feat, pe, mt, rid, P->d_params, A, Bs, Cs, lb, g, true, round_bf16, s);
+    float h[2] = {0.0f, 0.0f};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, lb, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, g, kMlpParams * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "training pass");
+    *loss = h[1] > 0.0f ? h[0] / h[1] : 0.0f;
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_proposal_train(const mcmi_csr *Bs, int32_t count, const mcmi_train_params *tp, mcmi_proposal P,
+                                float *loss_history, void *stream)
+{
+    if (!Bs || count < 1 || !tp || !P || tp->steps < 0 || !(tp->lr > 0.0f) || tp->chains < 1)
+        return fail(MCMI_ERR_ARG, "bad training argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    int64_t E = 0, R = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        mcmi_status r = check_csr(&Bs[b]);
+        if (r != MCMI_OK) return r;
+        E += Bs[b].nnz;
+        R += Bs[b].n;
+    }
+    float *feat = S.get<float>(E * 8), *pe = S.get<float>(E), *mt = S.get<float>(E);
+    int32_t *rid = S.get<int32_t>(E);
+    float *A = S.get<float>(R), *Bv = S.get<float>(R), *Cs = S.get<float>(R), *lb = S.get<float>(2);
+    float *g = S.get<float>(kMlpParams), *m1 = S.get<float>(kMlpParams), *m2 = S.get<float>(kMlpParams);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (training set)");
+    // training signal: second moments of the |c|-proposal walks of every row
+    mcmi_params wp;
+    mcmi_params_default(&wp);
+    wp.chains = tp->chains;
+    wp.max_len = tp->max_len;
+    wp.delta = tp->delta;
+    wp.alpha = tp->alpha;
+    wp.seed = tp->seed;
+    int64_t eb = 0, rb = 0;
+    for (int32_t b = 0; b < count; ++b) {
+        Scratch T(s);
+        float *mrow = T.get<float>(Bs[b].n);
+        if (T.err != cudaSuccess) return cuda_fail(T.err, "allocation");
+        mcmi_status r = mcmi_row_moments(&Bs[b], &wp, mrow, stream);
+        if (r == MCMI_OK) r = train_edges_of(&Bs[b], &wp, mrow, rb, eb, feat, pe, mt, rid, s);
+        if (r != MCMI_OK) return fail(r, "training matrix %d: %s", b, g_err.c_str());
+        eb += Bs[b].nnz;
+        rb += Bs[b].n;
+    }
+    cudaMemsetAsync(m1, 0, kMlpParams * 4, s);
+    cudaMemsetAsync(m2, 0, kMlpParams * 4, s);
+    const int rnd = tp->round_bf16;
+    for (int32_t it = 0; it < tp->steps; ++it) {
+        cudaError_t e = train_pass(E, R, feat, pe, mt, rid, P->d_params, A, Bv, Cs, lb, g, it == 0, rnd, s);
+        if (e == cudaSuccess) e = launch_adam(P->d_params, g, m1, m2, tp->lr, it + 1, s);
+        if (e != cudaSuccess) return cuda_fail(e, "training step");
+        if (loss_history) {
+            float h[2];
+            e = cudaMemcpyAsync(h, lb, 8, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) return cuda_fail(e, "training loss");
+            loss_history[it] = h[1] > 0.0f ? h[0] / h[1] : 0.0f;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(P->h_params, P->d_params, kMlpParams * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "training");
     return MCMI_OK;
 }
 

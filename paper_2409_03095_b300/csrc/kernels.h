@@ -34,6 +34,21 @@ cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t 
 // message returned by mcmi_last_error() on this host thread
 void set_error_message(const char *msg);
 
+// learned proposal
+cudaError_t launch_degree(int64_t n, const int64_t *rp, const int32_t *col, int *deg, cudaStream_t s);
+cudaError_t launch_tables_learned(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                                  const double *d, const double *sv, const int *deg, const float *th, uint4 *slots,
+                                  uint32_t *a, uint32_t *b, uint32_t *c, uint4 *lbkt, unsigned long long *wscr,
+                                  uint32_t *sstk, uint32_t *lstk, cudaStream_t s);
+cudaError_t launch_row_moments(const WalkArgs &a, int table, int64_t n, float *m, cudaStream_t s);
+cudaError_t launch_train_edges(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
+                               const double *sv, const int *deg, const float *mrow, int64_t row_base,
+                               int64_t edge_base, float *feat, float *p, float *mt, int32_t *rid, cudaStream_t s);
+cudaError_t train_pass(int64_t E, int64_t R, const float *feat, const float *p, const float *mt, const int32_t *rid,
+                       const float *th, float *A, float *Bs, float *Cs, float *lossbuf, float *grad, bool need_c,
+                       int round_bf16, cudaStream_t s);
+cudaError_t launch_adam(float *th, const float *grad, float *m1, float *m2, float lr, int step, cudaStream_t s);
+
 // batched builds: one matrix of the batch, in and out
 struct BatchIn {
     const int64_t *rp;

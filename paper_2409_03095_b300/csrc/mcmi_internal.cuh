@@ -6,6 +6,13 @@
 
 #include "mcmi.h"
 
+// Learned proposal: the network's parameters on the device (and a host copy).
+struct mcmi_proposal_s {
+    float *d_params = nullptr;
+    float h_params[1377];
+    int device = 0;
+};
+
 namespace mcmi {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;      // empty accumulator key
@@ -13,8 +20,7 @@ constexpr uint32_t kOolFlag = 0x80000000u;    // slot word 3: table stored out o
 constexpr uint32_t kNegBit = 0x80000000u;     // record: sign of c_ij
 constexpr int kInlineCum = 6;                 // cumulative pairs that fit a 64-byte slot
 constexpr int kInlineAlias = 4;               // alias triples that fit a 64-byte slot
-constexpr int kWalkThreadsMax = 128;          // walk kernel: threads per block (two chains each)
-constexpr int kWalkMinBlocks = 6;             // resident blocks per SM the register budget targets
+constexpr int kMlpParams = 1377;              // learned proposal: 8-32-32-1 network parameters
 
 // Device-side counters and the first error of a launch sequence.
 struct DevState {
@@ -58,6 +64,8 @@ struct WalkArgs {
     const uint4 *slots;           // 4 x uint4 per row
     const uint32_t *ool_a, *ool_b;    // cumulative out-of-line: thresholds, col|sign
     const uint4 *ool_bkt;             // alias out-of-line buckets {prob, own, alias, 0}
+    const uint4 *lbkt;                // learned proposal: 32-byte alias buckets with weight factors
+    float w_limit;                    // learned proposal: largest |W| the fixed-point sums can take
     const double2 *rowd;          // FP64 path: {s_i, 1/d_i}
     int64_t row_begin, row_end;   // rows when row_list == nullptr
     const int64_t *row_list;      // explicit rows (global indices)
@@ -97,5 +105,65 @@ struct WalkArgs {
     int64_t d_cap;
     DevState *st;
 };
+
+// One transition out of the row whose 64-byte record is s[16], driven by the
+// 32-bit random word r.  Returns col | neg << 31 of the picked entry and the
+// FP32 weight factor in *f: sign(c) fl32(s_i) for the |c| proposal, the
+// stored fl32(c Q / q) for a learned one.
+//   cumulative: x = floor(r Q / 2^32), the smallest m with x < T_m (inline
+//               pairs, or a binary search out of line);
+//   alias:      bucket b = floor(r deg / 2^32), the low 32 bits of r deg
+//               scaled to [0, Q) against the bucket's threshold.
+template <int TABLE>
+__device__ __forceinline__ uint32_t pick_transition(const uint32_t (&s)[16], uint32_t r, const WalkArgs &a,
+                                                    float *f)
+{
+    const uint32_t Q = s[0];
+    const uint32_t deg = s[3] & ~kOolFlag;
+    uint32_t cs;
+    if (TABLE == MCMI_TABLE_CUMULATIVE) {
+        const uint32_t x = __umulhi(r, Q);
+        if (!(s[3] & kOolFlag)) {
+            const uint32_t m = (s[4] <= x) + (s[6] <= x) + (s[8] <= x) + (s[10] <= x) + (s[12] <= x) + (s[14] <= x);
+            cs = m == 0 ? s[5] : m == 1 ? s[7] : m == 2 ? s[9] : m == 3 ? s[11] : m == 4 ? s[13] : s[15];
+        } else {
+            const uint32_t *T = a.ool_a + s[4];
+            uint32_t lo = 0, hi = deg - 1;
+#pragma unroll 1
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (x < __ldg(T + mid)) hi = mid; else lo = mid + 1;
+            }
+            cs = __ldg(a.ool_b + s[4] + lo);
+        }
+    } else {
+        const unsigned long long pr = (unsigned long long)r * deg;
+        const uint32_t b = (uint32_t)(pr >> 32);
+        const uint32_t y = __umulhi((uint32_t)pr, Q);
+        uint32_t prob, own, al;
+        if (!(s[3] & kOolFlag)) {
+            prob = b == 0 ? s[4] : b == 1 ? s[7] : b == 2 ? s[10] : s[13];
+            own = b == 0 ? s[5] : b == 1 ? s[8] : b == 2 ? s[11] : s[14];
+            al = b == 0 ? s[6] : b == 1 ? s[9] : b == 2 ? s[12] : s[15];
+        } else if (a.lbkt) {
+            // learned bucket: {prob, own, alias, f_own, f_alias, 0, 0, 0}
+            uint32_t v[8];
+            asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7])
+                         : "l"(a.lbkt + 2 * ((size_t)s[4] + b)));
+            const bool own_pick = y < v[0];
+            *f = __uint_as_float(own_pick ? v[3] : v[4]);
+            return own_pick ? v[1] : v[2];
+        } else {
+            const uint4 bk = __ldg(a.ool_bkt + s[4] + b);
+            prob = bk.x; own = bk.y; al = bk.z;
+        }
+        cs = y < prob ? own : al;
+    }
+    const float fs = __uint_as_float(s[1]);
+    *f = (cs & kNegBit) ? -fs : fs;
+    return cs;
+}
 
 }  // namespace mcmi

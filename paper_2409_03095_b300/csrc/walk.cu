@@ -41,7 +41,7 @@ __device__ __forceinline__ long long fix_f32(float w, int F)
     const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
     const int s = e - 150 + F;
     long long v;
-    if (s >= 0) v = m << s;
+    if (s >= 0) v = m << (s < 39 ? s : 39);   // |w| beyond the scale's range is reported by the caller
     else if (s > -40) v = (m + (1ll << (-s - 1))) >> (-s);
     else v = 0;
     return (b >> 31) ? -v : v;
@@ -325,6 +325,9 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             for (int j = 0; j < CPT; ++j) {
                 if (k[j] >= a.N) continue;
                 if (t[j] > 0) {
+                    // a learned proposal's weights are not bounded by 1: the host
+                    // leaves head-room in the fixed-point scale up to w_limit
+                    if (FIX && a.lbkt && !(fabsf(w[j]) <= a.w_limit)) report(a.st, s_row, MCMI_ERR_CAPACITY);
                     if (FIX)
                         accumulate(st[j], PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F), 0.0f);
                     else
@@ -344,43 +347,10 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                     r4[j] = philox4x32_10(make_uint4((uint32_t)(t[j] >> 2), (uint32_t)k[j], rlo, rhi), a.key0, a.key1);
                 const int ph = t[j] & 3;
                 const uint32_t r = ph == 0 ? r4[j].x : ph == 1 ? r4[j].y : ph == 2 ? r4[j].z : r4[j].w;
-                const uint32_t *sj = s[j];
-                const uint32_t deg = sj[3] & ~kOolFlag;
-                uint32_t cs;
-                if (TABLE == MCMI_TABLE_CUMULATIVE) {
-                    const uint32_t x = __umulhi(r, Q);
-                    if (!(sj[3] & kOolFlag)) {
-                        const uint32_t m = (sj[4] <= x) + (sj[6] <= x) + (sj[8] <= x) + (sj[10] <= x) +
-                                           (sj[12] <= x) + (sj[14] <= x);
-                        cs = m == 0 ? sj[5] : m == 1 ? sj[7] : m == 2 ? sj[9] : m == 3 ? sj[11] : m == 4 ? sj[13] : sj[15];
-                    } else {
-                        const uint32_t *T = a.ool_a + sj[4];
-                        uint32_t lo = 0, hi = deg - 1;
-#pragma unroll 1
-                        while (lo < hi) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if (x < __ldg(T + mid)) hi = mid; else lo = mid + 1;
-                        }
-                        cs = __ldg(a.ool_b + sj[4] + lo);
-                    }
-                } else {
-                    const unsigned long long pr = (unsigned long long)r * deg;
-                    const uint32_t b = (uint32_t)(pr >> 32);
-                    const uint32_t y = __umulhi((uint32_t)pr, Q);
-                    uint32_t prob, own, al;
-                    if (!(sj[3] & kOolFlag)) {
-                        prob = b == 0 ? sj[4] : b == 1 ? sj[7] : b == 2 ? sj[10] : sj[13];
-                        own = b == 0 ? sj[5] : b == 1 ? sj[8] : b == 2 ? sj[11] : sj[14];
-                        al = b == 0 ? sj[6] : b == 1 ? sj[9] : b == 2 ? sj[12] : sj[15];
-                    } else {
-                        const uint4 bk = __ldg(a.ool_bkt + sj[4] + b);
-                        prob = bk.x; own = bk.y; al = bk.z;
-                    }
-                    cs = y < prob ? own : al;
-                }
-                const float f = __uint_as_float(sj[1]);
+                float fl;
+                const uint32_t cs = pick_transition<TABLE>(s[j], r, a, &fl);
                 const bool neg = (cs & kNegBit) != 0u;
-                w[j] = __fmul_rn(w[j], neg ? -f : f);
+                w[j] = __fmul_rn(w[j], fl);
                 if (PREC == 64) w64[j] = __dmul_rn(w64[j], neg ? -rd[j].x : rd[j].x);
                 st[j] = cs & ~kNegBit;
                 ++t[j];
