@@ -59,6 +59,10 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--learned", action="store_true",
+                    help="learned vs |c| proposal on the anisotropic 1024^2 problem (one JSON line)")
+    ap.add_argument("--train-count", type=int, default=2000)
+    ap.add_argument("--train-steps", type=int, default=100)
     return ap.parse_args()
 
 
@@ -380,10 +384,114 @@ def run_ours(a):
     return 0
 
 
+def _pick_alpha(mc, B):
+    """Smallest alpha in {0, 0.05, 0.1, ...} with max_i s_i <= 0.95 (Eq. 1 augmentation)."""
+    for k in range(0, 41):
+        alpha = 0.05 * k
+        try:
+            M = mc.mcmi_build_ex(B, mc.params(chains=1, max_len=0, alpha=alpha))
+        except mc.McmiError:
+            continue
+        if M.stats.max_s <= 0.95:
+            return alpha
+    raise RuntimeError("no alpha <= 2 makes the matrix contractive")
+
+
+def run_learned(a):
+    """Learned proposal vs the |c| proposal on the anisotropic 1024^2
+    problem: training on `--train-count` smaller matrices of the family,
+    estimator error against exact rows (FP64 BiCGstab on Bhat^T), walk steps
+    at equal error, and BiCGstab iterations to 1e-8 with each M."""
+    import torch
+    import scipy.sparse as sp
+    import paper_2409_03095_b300 as mc
+    torch.cuda.set_device(0)
+    mc.load()
+    out = {"metric": METRIC, "unit": "steps/s", "workload": "aniso2d_9pt 1024^2 (n=1048576), 32x32-block rotated "
+           "anisotropy 1e-3; learned BF16 MLP proposal vs |c| proposal", "data": "synthetic"}
+    t0 = time.perf_counter()
+    train = [synth.aniso2d_9pt(int(nx), seed=2001 + k)
+             for k, nx in enumerate(np.random.default_rng(2000).integers(32, 129, a.train_count))]
+    Bt = [mc.DeviceCsr.from_host(m) for m in train]
+    P = mc.Proposal()
+    tp = mc.mcmi_train_params(steps=a.train_steps, lr=3e-3, chains=64, max_len=256, delta=1e-3, alpha=0.3, seed=7,
+                              round_bf16=1)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    hist = mc.mcmi_proposal_train(Bt, tp, P)
+    torch.cuda.synchronize()
+    out["training"] = {"matrices": len(train), "rows": int(sum(m.n for m in train)),
+                       "edges": int(sum(m.nnz for m in train)), "steps": a.train_steps,
+                       "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+                       "seconds": time.perf_counter() - t1, "generation_s": t1 - t0}
+    del Bt
+    m = synth.aniso2d_9pt(1024, seed=1005)
+    B = mc.DeviceCsr.from_host(m)
+    alpha = _pick_alpha(mc, B)
+    out["alpha"] = alpha
+    N, L, delta, tau = 128, 256, 1e-3, 1e-2
+    # exact rows of Bhat^-1 for sample rows: row i = (Bhat^-T e_i)^T, by the
+    # FP64 BiCGstab of the library on Bhat^T (assembled on the host)
+    Bh = m.to_scipy().tolil()
+    dd = m.to_scipy().diagonal()
+    bn = float(np.abs(m.to_scipy()).sum(axis=1).max())
+    Bh.setdiag(dd + alpha * bn * np.where(dd < 0, -1.0, 1.0))
+    BhT = Bh.tocsr().T.tocsr()
+    BhT.sort_indices()
+    from synth import Csr
+    BT = mc.DeviceCsr.from_host(Csr(m.n, BhT.indptr.astype(np.int64), BhT.indices.astype(np.int32), BhT.data))
+    rows = np.random.default_rng(1).choice(m.n, 32, replace=False)
+    exact = []
+    for r in rows:
+        e = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+        e[r] = 1.0
+        x = torch.zeros_like(e)
+        it, rr = mc.mcmi_solve(BT, None, e, x, mc.SOLVE_BICGSTAB, rtol=1e-11, maxit=20000)
+        exact.append(x.cpu().numpy())
+    res = {}
+    for name, prop in (("plain", None), ("learned", P)):
+        p = mc.params(chains=N, max_len=L, delta=delta, seed=11, alpha=alpha, filter_tau=tau,
+                      table=mc.TABLE_ALIAS, proposal=prop)
+        dump = mc.mcmi_walk_dump(B, p, rows, 200000)
+        errs = []
+        for g, xe in zip(dump, exact):
+            est = np.zeros(m.n)
+            est[g["col"]] = g["val"]
+            errs.append(np.linalg.norm(est - xe) / np.linalg.norm(xe))
+        steps_sample = sum(g["steps"] for g in dump)
+        # timed builds of the whole matrix
+        for _ in range(2):
+            M = mc.mcmi_build_ex(B, p)
+        ts = []
+        for _ in range(3):
+            M = mc.mcmi_build_ex(B, p)
+            ts.append(M.stats.ms_prepare + M.stats.ms_walk + M.stats.ms_assemble)
+        st = M.stats
+        bvec = torch.from_numpy(np.random.default_rng(2).standard_normal(m.n)).cuda()
+        x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+        its, relres = mc.mcmi_solve(B, M, bvec, x, mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
+        res[name] = {"eps_hat": float(np.mean(errs)), "steps_per_row": steps_sample / len(rows),
+                     "build_ms": float(np.median(ts)), "steps": int(st.steps),
+                     "steps_per_s": st.steps / (np.median(ts) / 1e3), "nnz_M": int(st.nnz),
+                     "bicgstab_iters": int(its), "relres": float(relres)}
+    its0, _ = mc.mcmi_solve(B, None, bvec, torch.zeros_like(bvec), mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
+    pl, le = res["plain"], res["learned"]
+    # steps needed for the plain proposal's error (error ~ N^-1/2 at fixed walk lengths)
+    eq = (le["eps_hat"] / pl["eps_hat"]) ** 2
+    out.update({"plain": pl, "learned": le, "bicgstab_iters_unpreconditioned": int(its0),
+                "learned_steps_at_equal_error_over_plain": eq * le["steps_per_row"] / pl["steps_per_row"],
+                "learned_iters_over_plain": le["bicgstab_iters"] / max(1, pl["bicgstab_iters"]),
+                "chains": N, "max_len": L, "delta": delta, "tau": tau})
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    if a.learned:
+        return run_learned(a)
     return run_ours(a)
 
 
