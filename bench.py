@@ -44,6 +44,9 @@ WORKLOADS = {
                        "cutoff 1e-3, max length 64, tau 1e-2",
     "powerlaw_1m": "random sparse nonsymmetric n=1048576, power-law rows (alpha 2.5, 4..256), N(0,1) values, "
                    "dominance 0.85; 128 chains/row, cutoff 1e-3, max length 256, tau 5e-3",
+    "batch_512": "512 matrices, n log-uniform in [1e3, 2e5], cycling 2D 5-point / 3D 7-point / power-law random, "
+                 "dominance U[0.8, 0.95]; 128 chains/row, cutoff 1e-3, max length 128, top-16; one batched build "
+                 "(graph-captured persistent walk, autotuned shape)",
 }
 SLOT_BYTES = 64   # one row record (two 32-B sectors) read per visited state
 METRIC = "MC walk steps/s"
@@ -486,12 +489,81 @@ def run_learned(a):
     return 0
 
 
+def run_batched(a):
+    """One batched build of 512 uneven matrices per step (config of the
+    batched path); the autotuned launch shape from the warm-up is reused."""
+    import torch
+    import paper_2409_03095_b300 as mc
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    mc.load()
+    t0 = time.perf_counter()
+    mats = synth.batch_mix(512, seed=1004 + rank)
+    gen_s = time.perf_counter() - t0
+    Bs = [mc.DeviceCsr.from_host(m) for m in mats]
+    p = mc.params(chains=128, max_len=128, delta=1e-3, top_k=16, seed=1000 + rank)
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    Ms, st = mc.mcmi_build_batched(Bs, p)          # warm-up with the autotuner
+    del Ms
+    p.threads, p.chains_per_thread, p.hash_log2, p.table = st.threads, st.chains_per_thread, st.hash_log2, st.table
+    for _ in range(max(0, a.warmup - 1)):
+        Ms, st = mc.mcmi_build_batched(Bs, p)
+        del Ms
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    times, steps, walk_ms, launches = [], 0, [], 0
+    stream = torch.cuda.current_stream()
+    for it in range(a.steps):
+        flush.fill_(float(it))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Ms, st = mc.mcmi_build_batched(Bs, p, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        steps += st.steps
+        walk_ms.append(st.ms_walk_kernel)
+        launches += st.launches
+        del Ms
+    if clocks:
+        clocks.end()
+    ck = clocks.stop() if clocks else None
+    tot_ms = sum(times)
+    value = steps / (tot_ms / 1e3)
+    if rank != 0:
+        return 0
+    peaks, peak_src = _peaks()
+    visits = steps + 128 * st.rows * a.steps
+    achieved = SLOT_BYTES * visits / (sum(walk_ms) / 1e3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch_512: {WORKLOADS['batch_512']}", "matrices": len(mats),
+                       "rows": int(st.rows), "rows_per_s": st.rows * a.steps / (tot_ms / 1e3),
+                       "steps_per_build": int(st.steps), "generation_s": gen_s,
+                       "autotuned": {"threads": st.threads, "chains_per_thread": st.chains_per_thread,
+                                     "hash_log2": st.hash_log2, "table": ["cumulative", "alias"][st.table]},
+                       "walk_ms": float(np.median(walk_ms)), "l2": "flushed between timed steps (256 MiB write)"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_walk (batched)",
+                         "peak_source": f"{peak_src} HBM copy bandwidth",
+                         "bytes_per_unit": "64 B per visited state"},
+            "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
     if a.learned:
         return run_learned(a)
+    if a.workload == "batch_512":
+        return run_batched(a)
     return run_ours(a)
 
 

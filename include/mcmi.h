@@ -113,6 +113,8 @@ typedef struct {
     float ms_assemble;      /* CSR assembly */
     float ms_walk_kernel;   /* the first walk kernel launch alone */
     int32_t launches;       /* kernels this build launched */
+    int32_t threads;        /* walk threads per block used */
+    int32_t chains_per_thread; /* chains each walk thread advanced */
     int32_t reserved;
 } mcmi_stats;
 

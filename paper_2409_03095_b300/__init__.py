@@ -53,7 +53,8 @@ class mcmi_stats(C.Structure):
                 ("chains", C.c_int32), ("max_len_bound", C.c_int32), ("table", C.c_int32), ("hash_log2", C.c_int32),
                 ("spilled", C.c_int64), ("deferred_rows", C.c_int64), ("ms_prepare", C.c_float),
                 ("ms_walk", C.c_float), ("ms_assemble", C.c_float), ("ms_walk_kernel", C.c_float),
-                ("launches", C.c_int32), ("reserved", C.c_int32)]
+                ("launches", C.c_int32), ("threads", C.c_int32), ("chains_per_thread", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

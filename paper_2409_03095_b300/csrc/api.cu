@@ -695,6 +695,8 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
         cudaEventElapsedTime(&stats->ms_assemble, ev[2], ev[3]);
         cudaEventElapsedTime(&stats->ms_walk_kernel, ev[4], ev[5]);
         stats->launches = launches;
+        stats->threads = W.threads;
+        stats->chains_per_thread = W.cpt;
     }
     *M_out = M;
     return MCMI_OK;
@@ -931,6 +933,8 @@ mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_par
         }
         cudaEventElapsedTime(&stats->ms_walk, ev[2], ev[3]);
         stats->launches = launches;
+        stats->threads = W.threads;
+        stats->chains_per_thread = W.cpt;
     }
     return MCMI_OK;
 }
