@@ -44,6 +44,7 @@ WORKLOADS = {
                        "cutoff 1e-3, max length 64, tau 1e-2",
     "powerlaw_1m": "random sparse nonsymmetric n=1048576, power-law rows (alpha 2.5, 4..256), N(0,1) values, "
                    "dominance 0.85; 128 chains/row, cutoff 1e-3, max length 256, tau 5e-3",
+    "powerlaw_128k": "power-law random as powerlaw_1m with n=131072: profiling-size case",
     "batch_512": "512 matrices, n log-uniform in [1e3, 2e5], cycling 2D 5-point / 3D 7-point / power-law random, "
                  "dominance U[0.8, 0.95]; 128 chains/row, cutoff 1e-3, max length 128, top-16; one batched build "
                  "(graph-captured persistent walk, autotuned shape)",

@@ -106,10 +106,10 @@ typedef struct {
     int32_t max_len_bound;  /* no chain can take more transitions than this */
     int32_t table;          /* table type used */
     int32_t hash_log2;      /* accumulator slots used (log2) */
-    int64_t spilled;        /* accumulator entries that went to the global overflow table */
+    int64_t spilled;        /* distinct columns whose visits overflowed the on-chip table (reduced from the log) */
     int64_t deferred_rows;  /* rows re-run because the first output buffer was full */
     float ms_prepare;       /* split + tables (CUDA events on the build stream) */
-    float ms_walk;          /* walk stage incl. overflow-table set-up and deferred rows */
+    float ms_walk;          /* walk stage incl. overflow-log set-up and deferred rows */
     float ms_assemble;      /* CSR assembly */
     float ms_walk_kernel;   /* the first walk kernel launch alone */
     int32_t launches;       /* kernels this build launched */

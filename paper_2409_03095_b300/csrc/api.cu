@@ -306,7 +306,7 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
 }
 
 struct WalkPlan {
-    int threads = 128, cpt = 2, log2H = 11, log2G = 8, grid = 1;
+    int threads = 128, cpt = 2, log2H = 11, grid = 1;
 };
 
 mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, bool dump, WalkPlan &W)
@@ -323,13 +323,11 @@ mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, boo
         W.log2H = p->hash_log2;
     } else {
         // on-chip table at most ~75% full for the reachable columns, capped at
-        // 2^11 slots (24 KB) so that six blocks share an SM; rows that reach
-        // more columns put the excess in the global overflow table
+        // 2^11 slots (24 KB) so that eight blocks share an SM; rows that reach
+        // more columns log the excess visits and reduce them after the walks
         int l = ceil_log2((distinct * 4) / 3 + 1);
         W.log2H = l < 8 ? 8 : (l > 11 ? 11 : l);
     }
-    int l2 = ceil_log2(2 * distinct + 2);
-    W.log2G = l2 < 8 ? 8 : l2;
     int bps = 0;
     cudaError_t e = walk_occupancy(p->precision, P.table, p->accumulator, dump, W.cpt, W.threads, W.log2H, &bps);
     if (e != cudaSuccess) return cuda_fail(e, "walk occupancy");
@@ -359,7 +357,6 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     a.key0 = (uint32_t)p->seed;
     a.key1 = (uint32_t)(p->seed >> 32);
     a.log2H = W.log2H;
-    a.log2G = W.log2G;
     a.tau = p->filter_tau;
     // fixed-point scale: N (L_bound + 1) weights of magnitude <= 1 stay below 2^62
     // Fixed-point scale 2^F: the largest F for which N (L_bound + 1) weights
@@ -380,22 +377,37 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     }
     a.fix_shift = F < 8 ? 8 : (F > 62 ? 62 : F);
     a.fix_inv = std::ldexp(1.0, -a.fix_shift);
+    a.fin_scale = (float)(a.fix_inv / (double)P.N);
     a.top_k = p->top_k;
     a.st = P.st;
     a.count_steps = 1;
 }
 
-mcmi_status alloc_overflow(Scratch &S, const WalkPlan &W, WalkArgs &a, cudaStream_t s)
+// Per-block overflow log (visits in arrival order, then bucketed: two
+// regions) and entry list.  A row makes at most N Lb visits after t = 0, so
+// the log never fills; the list takes the on-chip entries and the log's
+// distinct columns.  When the regions of all blocks would pass a quarter of
+// the free device memory, fewer blocks are launched.
+mcmi_status alloc_overflow(Scratch &S, WalkPlan &W, const Prepared &P, bool dump, WalkArgs &a)
 {
-    const size_t G = (size_t)W.grid << W.log2G;
-    a.g_keys = S.get<uint32_t>(G);
-    a.g_vals = S.get<unsigned long long>(G);
-    a.g_cnt = S.get<uint32_t>(G);
-    a.g_list = S.get<uint32_t>(G);
-    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (overflow table)");
-    cudaMemsetAsync(a.g_keys, 0xFF, G * 4, s);
-    cudaMemsetAsync(a.g_vals, 0, G * 8, s);
-    cudaMemsetAsync(a.g_cnt, 0, G * 4, s);
+    const uint64_t logc = (uint64_t)P.N * (uint64_t)(P.Lb + 1);
+    const uint64_t entc = logc + ((uint64_t)1 << W.log2H);
+    if (entc > 0xFFFFFFF0ull) return fail(MCMI_ERR_ARG, "N (L + 1) = %llu visits per row is too large", (unsigned long long)logc);
+    a.log_cap = (uint32_t)logc;
+    a.ent_cap = (uint32_t)entc;
+    const size_t per_block = (size_t)logc * 2 * 12 + (size_t)entc * (dump ? 16 : 12);
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (size_t)W.grid * per_block > fr / 4) {
+        const size_t g = (fr / 4) / per_block;
+        W.grid = g < 1 ? 1 : (int)g;
+    }
+    const size_t G = (size_t)W.grid;
+    a.log_col = S.get<uint32_t>(G * 2 * logc);
+    a.log_val = S.get<unsigned long long>(G * 2 * logc);
+    a.ent_col = S.get<uint32_t>(G * entc);
+    a.ent_val = S.get<unsigned long long>(G * entc);
+    a.ent_cnt = dump ? S.get<uint32_t>(G * entc) : nullptr;
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (overflow log)");
     return MCMI_OK;
 }
 
@@ -405,7 +417,7 @@ void reset_queue(DevState *st, cudaStream_t s)
 }
 
 // One timed walk launch over rows [rb, re) with plan W (autotuner trial).
-mcmi_status time_walk(const mcmi_params *p, const Prepared &P, const WalkPlan &W, int64_t rb, int64_t re,
+mcmi_status time_walk(const mcmi_params *p, const Prepared &P, WalkPlan W, int64_t rb, int64_t re,
                       cudaStream_t s, float *ms)
 {
     Scratch S(s);
@@ -413,7 +425,7 @@ mcmi_status time_walk(const mcmi_params *p, const Prepared &P, const WalkPlan &W
     fill_walk_args(a, p, P, W);
     a.row_begin = rb;
     a.row_end = re;
-    mcmi_status r = alloc_overflow(S, W, a, s);
+    mcmi_status r = alloc_overflow(S, W, P, false, a);
     if (r != MCMI_OK) return r;
     const int64_t rows = re - rb;
     const uint64_t per_row = p->top_k > 0 ? (uint64_t)(p->top_k + 1) : 512;
@@ -593,7 +605,7 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
     fill_walk_args(a, p, P, W);
     a.row_begin = rb;
     a.row_end = re;
-    r = alloc_overflow(S, W, a, s);
+    r = alloc_overflow(S, W, P, false, a);
     if (r != MCMI_OK) return give_up(r);
     const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
     const uint64_t distinct = reach < (uint64_t)n ? reach : (uint64_t)n;
@@ -783,7 +795,7 @@ mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_par
     a.row_end = tn;
     a.batch_row_base = d_row_base;
     a.batch_count = count;
-    r = alloc_overflow(S, W, a, s);
+    r = alloc_overflow(S, W, P, false, a);
     if (r != MCMI_OK) return r;
     const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
     const uint64_t distinct = reach < (uint64_t)tn ? reach : (uint64_t)tn;
@@ -1013,7 +1025,7 @@ mcmi_status mcmi_walk_dump(const mcmi_csr *B, const mcmi_params *p, const int64_
     a.row_begin = 0;
     a.row_end = B->n;
     a.out_by_row = 0;
-    r = alloc_overflow(S, W, a, s);
+    r = alloc_overflow(S, W, P, true, a);
     if (r != MCMI_OK) return r;
     a.d_count = out_count;
     a.d_col = out_col;

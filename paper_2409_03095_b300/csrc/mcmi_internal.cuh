@@ -29,7 +29,7 @@ struct DevState {
     unsigned long long smin_bits;  // bits of min over s_i > 0 (~0 if none)
     unsigned long long bnorm_bits; // bits of ||B||_inf
     unsigned long long steps;      // transitions taken
-    unsigned long long spilled;    // entries placed in the global overflow table
+    unsigned long long spilled;    // distinct columns reduced from the overflow log
     unsigned long long cursor;     // staging entries claimed
     unsigned long long deferred;   // rows that found the staging buffer full
     unsigned long long work;       // next row-queue position
@@ -78,14 +78,19 @@ struct WalkArgs {
     float delta_f;                // smallest float >= delta
     int fix_shift;                // fixed-point accumulator scale: weight w is added as round(w 2^F)
     double fix_inv;               // 2^-F
+    float fin_scale;              // 2^-F / N in FP32 (finished values of FP32 builds)
     uint32_t key0, key1;
     int log2H;                    // on-chip slots per block
-    // global overflow accumulator, one region per block
-    uint32_t *g_keys;
-    unsigned long long *g_vals;
-    uint32_t *g_cnt;
-    uint32_t *g_list;
-    int log2G;
+    // visits that find the on-chip table full go to a per-block log (column,
+    // addend); after the walks the log is reduced on chip, in hash-range
+    // passes, into a per-block list of the row's distinct entries
+    uint32_t *log_col;
+    unsigned long long *log_val;
+    uint32_t log_cap;             // log entries per block (>= the visits of one row)
+    uint32_t *ent_col;
+    unsigned long long *ent_val;  // finished values M_ij (FP64 bits, or FP32 bits in the low word)
+    uint32_t *ent_cnt;            // parity dump: visit counts
+    uint32_t ent_cap;             // entries per block (>= log_cap + on-chip slots)
     // filter
     double tau;
     int32_t top_k;

@@ -1,7 +1,7 @@
 // Stages a3-a5 of the hot path in one kernel: the random walks of Eq. 2,
-// the row accumulator (on-chip hash + global overflow table), the phase-4
-// column scaling by 1/d_j and the Sec. IV-B filter, writing each row's kept
-// entries to a staging buffer.
+// the row accumulator (on-chip hash + overflow log), the phase-4 column
+// scaling by 1/d_j and the Sec. IV-B filter, writing each row's kept entries
+// to a staging buffer.
 //
 // One block per row at a time (rows taken from a device queue), threads as
 // chains: a thread that finishes a chain takes the next chain index of the
@@ -17,15 +17,30 @@
 //  ACC_KAHAN32: FP32 sums of W/d_j with a compensation word; the rounding
 //    error of each addition is computed exactly from the returned previous
 //    sum (Knuth's TwoSum) and added to the compensation.
+//
+// Rows that reach more columns than the on-chip table holds (random sparse
+// matrices: nearly every visit after the first steps is a new column) append
+// the visits that find the table full to a per-block log in global memory:
+// one store, off the chain's dependent path.  After the walks, log entries of
+// columns on chip are added there; if any remain, the on-chip entries are
+// moved to a per-block entry list and the rest of the log is reduced on chip
+// in passes over disjoint hash ranges of the column index (a pass whose
+// columns do not fit is retried on half its range), each pass appending its
+// finished entries to the list.
+#include <cooperative_groups.h>
+#include <type_traits>
+
 #include "mcmi_internal.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace mcmi {
 
 namespace {
 
 constexpr int kProbeOnChip = 32;   // on-chip probe window before overflowing
-constexpr uint32_t kDead = 0x80000000u;
+constexpr uint32_t kPartMul = 0x85EBCA77u;   // odd: col -> col * kPartMul permutes the 32-bit keys
 
 __device__ __forceinline__ uint32_t hash_home(uint32_t key, int log2)
 {
@@ -60,6 +75,26 @@ __device__ __forceinline__ long long fix_f64(double w, int F)
     else if (s > -63) v = (m + (1ll << (-s - 1))) >> (-s);
     else v = 0;
     return (b >> 63) ? -v : v;
+}
+
+// u (a 64-bit magnitude) rounded to the nearest FP32 value, ties to even,
+// with integer instructions.  Being correctly rounded, the result scales
+// exactly with powers of two of u, so finished values do not depend on the
+// fixed-point scale.
+__device__ __forceinline__ float u64_to_f32_rn(unsigned long long u)
+{
+    if (u == 0ull) return 0.0f;
+    const int lz = __clzll((long long)u);
+    const unsigned long long n = u << lz;            // leading one at bit 63
+    uint32_t mant = (uint32_t)(n >> 40);             // 24 significant bits
+    const unsigned long long rest = n << 24;         // the 40 bits below them, at the top
+    if (rest > 0x8000000000000000ull || (rest == 0x8000000000000000ull && (mant & 1u))) ++mant;
+    int e = 63 - lz;
+    if (mant == (1u << 24)) {
+        mant >>= 1;
+        ++e;
+    }
+    return __uint_as_float(((uint32_t)(e + 127) << 23) | (mant & 0x7FFFFFu));
 }
 
 // Exact 64-bit add into a shared word from two native 32-bit atomics.
@@ -155,6 +190,10 @@ template <int PREC, int TABLE, int ACC, bool DUMP, int CPT>
 __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk(WalkArgs a)
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
+    // finished values and the filter work in the build's precision: FP32
+    // builds use no FP64 instruction per entry (FP64 issues at a small
+    // fraction of the FP32 rate)
+    using VT = typename std::conditional<PREC == 64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const int H = 1 << a.log2H;
     // per slot: an 8-byte value word (fixed-point sum, or FP32 {sum, comp};
@@ -170,37 +209,44 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
 
     __shared__ long long s_row, s_pos, s_key_row;
     __shared__ int s_next_chain;
-    __shared__ uint32_t s_nspill, s_fill, s_wpos, s_ncand;
+    __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent;
     __shared__ long long s_off;
+    __shared__ double s_diag;
     __shared__ float s_redf[32];
     __shared__ unsigned long long s_redu[32];
     __shared__ uint32_t s_hist[256];
+    __shared__ uint32_t s_bstart[257];
     __shared__ uint32_t s_digit, s_rank;
 
     const int tid = threadIdx.x, B = blockDim.x;
     const uint32_t fill_cap = (uint32_t)(H - (H >> 2));      // on-chip table kept <= 75% full
-    const int G = 1 << a.log2G;
-    const size_t gbase = (size_t)blockIdx.x << a.log2G;
-    uint32_t *gk = a.g_keys + gbase;
-    uint32_t *gc = a.g_cnt + gbase;
-    uint32_t *gl = a.g_list + gbase;
-    unsigned long long *gv = a.g_vals + gbase;
+    // log: the visits in arrival order, then the same entries bucketed by hash range
+    uint32_t *lc = a.log_col + (size_t)blockIdx.x * 2 * a.log_cap;
+    unsigned long long *lv = a.log_val + (size_t)blockIdx.x * 2 * a.log_cap;
+    uint32_t *lc2 = lc + a.log_cap;
+    unsigned long long *lv2 = lv + a.log_cap;
+    uint32_t *ec = a.ent_col + (size_t)blockIdx.x * a.ent_cap;
+    unsigned long long *ev = a.ent_val + (size_t)blockIdx.x * a.ent_cap;
+    uint32_t *ecn = DUMP ? a.ent_cnt + (size_t)blockIdx.x * a.ent_cap : nullptr;
     const long long total = a.row_list ? a.n_list : a.row_end - a.row_begin;
     const int F = a.fix_shift;
+    const bool use_tau = a.tau > 0.0;
 
     for (int h = tid; h < H; h += B) {
         s_keys[h] = kEmpty;
         s_val[h] = 0ull;
         if (DUMP) s_aux[h] = 0u;
     }
-    if (tid == 0) { s_nspill = 0; s_fill = 0; }
+    if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; }
 
-    // Adds the visit of column col with weight w (FP32) / w64 (FP64); the
-    // Kahan accumulator takes the column-scaled value v = w / d_col.
-    auto accumulate = [&](uint32_t col, long long fx, float v) {
-        // linear probing over 4-slot buckets, one 16-byte read per bucket; a
-        // key always takes the first empty slot in probe order, so a search
-        // that meets an empty slot before the key knows the key is absent
+    // Adds one visit to the on-chip table.  The addend is the fixed-point
+    // weight, or the FP32 bits of W / d_j for the Kahan accumulator.  Linear
+    // probing over 4-slot buckets, one 16-byte read per bucket; a key always
+    // takes the first empty slot in probe order, so a search that meets an
+    // empty slot before the key knows the key is absent.  Returns false when
+    // the column is absent and cannot be inserted (table at its fill cap, or
+    // no free slot within the probe window).
+    auto onchip_add = [&](uint32_t col, unsigned long long add) -> bool {
         uint32_t bkt = hash_home(col, a.log2H - 2);
         const uint32_t nb = (uint32_t)(H >> 2);
 #pragma unroll 1
@@ -213,7 +259,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             if (slot < 0) {
                 const int e = kv.x == kEmpty ? 0 : kv.y == kEmpty ? 1 : kv.z == kEmpty ? 2 : kv.w == kEmpty ? 3 : -1;
                 if (e >= 0) {
-                    if (*(volatile uint32_t *)&s_fill >= fill_cap) break;
+                    if (*(volatile uint32_t *)&s_fill >= fill_cap) return false;
                     const uint32_t old = atomicCAS(&s_keys[4 * bkt + e], kEmpty, col);
                     if (old == kEmpty) atomicAdd(&s_fill, 1u);
                     if (old == kEmpty || old == col) slot = e;
@@ -222,31 +268,41 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             }
             if (slot >= 0) {
                 const uint32_t h = 4 * bkt + (uint32_t)slot;
-                if (FIX) fix_add_shared(&s_val[h], fx); else comp_add(&s_val[h], v);
+                if (FIX) fix_add_shared(&s_val[h], (long long)add);
+                else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
                 if (DUMP) atomicAdd(&s_aux[h], 1u);
-                return;
+                return true;
             }
             bkt = (bkt + 1) & (nb - 1);
         }
-        // global overflow table (never more than half full by its sizing)
-        uint32_t g = hash_home(col, a.log2G);
-#pragma unroll 1
-        for (int p = 0; p < G; ++p) {
-            const uint32_t k = ((volatile uint32_t *)gk)[g];
-            bool hit = k == col;
-            if (!hit && k == kEmpty) {
-                const uint32_t old = atomicCAS(&gk[g], kEmpty, col);
-                if (old == kEmpty) gl[atomicAdd(&s_nspill, 1u)] = g;
-                hit = old == kEmpty || old == col;
-            }
-            if (hit) {
-                if (FIX) atomicAdd(&gv[g], (unsigned long long)fx); else comp_add(&gv[g], v);
-                if (DUMP) atomicAdd(&gc[g], 1u);
-                return;
-            }
-            g = (g + 1) & (uint32_t)(G - 1);
+        return false;
+    };
+    // Slot of col on chip, or -1; no insertion (used once no insertions run).
+    auto onchip_find = [&](uint32_t col) -> int {
+        uint32_t h = 4 * hash_home(col, a.log2H - 2);
+        for (int p = 0; p < kProbeOnChip; ++p) {
+            const uint32_t k = s_keys[h];
+            if (k == col) return (int)h;
+            if (k == kEmpty) return -1;
+            h = (h + 1) & (uint32_t)(H - 1);
         }
-        report(a.st, s_row, MCMI_ERR_CAPACITY);
+        return -1;
+    };
+    // A visit that does not fit on chip is appended to the log; the lanes
+    // that arrive together reserve their positions with one atomic.
+    auto accumulate = [&](uint32_t col, unsigned long long add) {
+        if (onchip_add(col, add)) return;
+        cg::coalesced_group g = cg::coalesced_threads();
+        uint32_t base = 0;
+        if (g.thread_rank() == 0) base = atomicAdd(&s_nlog, g.size());
+        base = g.shfl(base, 0);
+        const uint32_t pos = base + g.thread_rank();
+        if (pos < a.log_cap) {
+            lc[pos] = col;
+            lv[pos] = add;
+        } else {
+            report(a.st, s_row, MCMI_ERR_CAPACITY);   // cannot happen: a row makes at most N Lb visits
+        }
     };
 
     for (;;) {
@@ -293,8 +349,8 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
         const long long idx = (a.row_list && !a.out_by_row) ? pos : row - a.row_begin;
         const uint32_t rlo = (uint32_t)s_key_row, rhi = (uint32_t)((unsigned long long)s_key_row >> 32);
 
-        // ---- walks (Eq. 2): each thread advances two chains in turn, so that
-        // two dependent gathers are in flight per thread; a chain that stops
+        // ---- walks (Eq. 2): each thread advances CPT chains in turn, so that
+        // CPT dependent gathers are in flight per thread; a chain that stops
         // is replaced by the row's next chain index ----
         unsigned long long my_steps = 0;
         uint32_t st[CPT];
@@ -329,9 +385,9 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                     // leaves head-room in the fixed-point scale up to w_limit
                     if (FIX && a.lbkt && !(fabsf(w[j]) <= a.w_limit)) report(a.st, s_row, MCMI_ERR_CAPACITY);
                     if (FIX)
-                        accumulate(st[j], PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F), 0.0f);
+                        accumulate(st[j], (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F)));
                     else
-                        accumulate(st[j], 0, __fmul_rn(w[j], __uint_as_float(s[j][2])));
+                        accumulate(st[j], (unsigned long long)__float_as_uint(__fmul_rn(w[j], __uint_as_float(s[j][2]))));
                 }
                 const uint32_t Q = s[j][0];
                 if (t[j] == a.L || !(fabsf(w[j]) >= a.delta_f) || Q == 0u) {
@@ -359,89 +415,187 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
         __syncthreads();
 
         // ---- row statistics ----
+        for (int b = tid; b < 256; b += B) s_hist[b] = 0;
         const unsigned long long row_steps = block_sum(my_steps, s_redu);
         if (tid == 0) {
             if (a.count_steps) atomicAdd(&a.st->steps, row_steps);
             if (a.row_steps) a.row_steps[idx] = row_steps;
-            if (s_nspill) atomicAdd(&a.st->spilled, (unsigned long long)s_nspill);
             s_wpos = 0;
             s_ncand = 0;
         }
-        const uint32_t nsp = s_nspill;
-        // overflow entries whose key also sits on chip are merged into it
-        for (uint32_t e = tid; e < nsp; e += B) {
-            const uint32_t g = gl[e];
-            const uint32_t key = gk[g];
-            uint32_t h = 4 * hash_home(key, a.log2H - 2);
-            for (int p = 0; p < kProbeOnChip; ++p) {
-                const uint32_t k = s_keys[h];
-                if (k == kEmpty) break;
-                if (k == key) {
-                    if (FIX) {
-                        fix_add_shared(&s_val[h], (long long)gv[g]);
-                    } else {
-                        comp_add(&s_val[h], __uint_as_float((uint32_t)gv[g]));
-                        comp_add(&s_val[h], __uint_as_float((uint32_t)(gv[g] >> 32)));
-                    }
-                    if (DUMP) atomicAdd(&s_aux[h], gc[g]);
-                    gl[e] = g | kDead;
-                    break;
-                }
-                h = (h + 1) & (uint32_t)(H - 1);
-            }
-        }
-        __syncthreads();
+        const uint32_t nlog = min(s_nlog, a.log_cap);
 
-        // finished values M_ij = (1/N) X_ij / d_j, written over the value words
-        auto finish = [&](unsigned long long raw, uint32_t col) -> double {
-            if (FIX) {
+        // finished values M_ij = (1/N) X_ij / d_j of the raw accumulator words
+        auto finish = [&](unsigned long long raw, uint32_t col) -> VT {
+            if (PREC == 64) {
                 const double X = __dmul_rn(__ll2double_rn((long long)raw), a.fix_inv);   // exact scaling
-                const double invd = PREC == 64 ? __ldg(&a.rowd[col].y)
-                                               : (double)__uint_as_float(__ldg(&a.slots[4 * (size_t)col].z));
-                return __dmul_rn(__ddiv_rn(X, (double)a.N), invd);
+                return __dmul_rn(__ddiv_rn(X, (double)a.N), __ldg(&a.rowd[col].y));
+            } else if (FIX) {
+                // fl32(|X| 2^F), then (2^-F / N) and 1/d_j: three FP32 roundings
+                const long long x = (long long)raw;
+                const float m = u64_to_f32_rn((unsigned long long)(x < 0 ? -x : x));
+                const float invd = __uint_as_float(__ldg(&a.slots[4 * (size_t)col].z));
+                const float v = __fmul_rn(__fmul_rn(m, a.fin_scale), invd);
+                return (VT)(x < 0 ? -v : v);
+            } else {
+                const float sum = __uint_as_float((uint32_t)raw), c = __uint_as_float((uint32_t)(raw >> 32));
+                return (VT)__fdiv_rn(__fadd_rn(sum, c), (float)a.N);
             }
-            const float sum = __uint_as_float((uint32_t)raw), c = __uint_as_float((uint32_t)(raw >> 32));
-            return (double)__fdiv_rn(__fadd_rn(sum, c), (float)a.N);
         };
-        auto store = [&](unsigned long long *p, double v) {
-            if (PREC == 64) *p = (unsigned long long)__double_as_longlong(v);
-            else *reinterpret_cast<float *>(p) = (float)v;
+        // a finished value as stored: FP64 bits, or FP32 bits in the low word
+        auto enc = [&](VT v) -> unsigned long long {
+            if (PREC == 64) return (unsigned long long)__double_as_longlong((double)v);
+            return (unsigned long long)__float_as_uint((float)v);
         };
-        for (int h = tid; h < H; h += B)
-            if (s_keys[h] != kEmpty) store(&s_val[h], finish(s_val[h], s_keys[h]));
-        for (uint32_t e = tid; e < nsp; e += B) {
-            const uint32_t g = gl[e];
-            if (!(g & kDead)) store(&gv[g], finish(gv[g], gk[g]));
+        auto dec = [&](unsigned long long b) -> VT {
+            if (PREC == 64) return (VT)__longlong_as_double((long long)b);
+            return (VT)__uint_as_float((uint32_t)b);
+        };
+        auto sval = [&](uint32_t h) -> VT { return dec(s_val[h]); };
+        auto clear_table = [&]() {
+            for (int h = tid; h < H; h += B) {
+                s_keys[h] = kEmpty;
+                s_val[h] = 0ull;
+                if (DUMP || PREC == 64) s_aux[h] = 0u;
+            }
+        };
+        // finished on-chip entries appended to the entry list; the table is cleared
+        auto flush = [&]() {
+            for (int h = tid; h < H; h += B) {
+                const uint32_t key = s_keys[h];
+                if (key == kEmpty) continue;
+                const VT v = finish(s_val[h], key);
+                if (key == (uint32_t)row) s_diag = (double)v;
+                const uint32_t p = atomicAdd(&s_nent, 1u);
+                ec[p] = key;
+                ev[p] = enc(v);
+                if (DUMP) ecn[p] = s_aux[h];
+                s_keys[h] = kEmpty;
+                s_val[h] = 0ull;
+                if (DUMP || PREC == 64) s_aux[h] = 0u;
+            }
+        };
+
+        // ---- the overflow log ----
+        uint32_t nrem = 0;
+        if (nlog) {   // block-uniform
+            // entries whose column is on chip are added there; the others are
+            // counted per hash-range bucket (top 8 bits of col * kPartMul)
+            for (uint32_t e = tid; e < nlog; e += B) {
+                const uint32_t key = lc[e];
+                const int h = onchip_find(key);
+                if (h >= 0) {
+                    const unsigned long long add = lv[e];
+                    if (FIX) fix_add_shared(&s_val[h], (long long)add);
+                    else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
+                    if (DUMP) atomicAdd(&s_aux[h], 1u);
+                    lc[e] = kEmpty;
+                } else {
+                    ++nrem;
+                    atomicAdd(&s_hist[(key * kPartMul) >> 24], 1u);
+                }
+            }
+            nrem = (uint32_t)block_sum(nrem, s_redu);
+        }
+        if (nrem) {   // block-uniform
+            flush();
+            // bucket starts: exclusive scan of the 256 counts (warp 0, 8 per lane)
+            if (tid < 32) {
+                uint32_t c8[8], tot = 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    c8[u] = s_hist[8 * tid + u];
+                    tot += c8[u];
+                }
+                uint32_t incl = tot;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (tid >= o) incl += nb;
+                }
+                uint32_t run = incl - tot;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    s_bstart[8 * tid + u] = run;
+                    s_hist[8 * tid + u] = run;   // scatter cursor
+                    run += c8[u];
+                }
+                if (tid == 31) s_bstart[256] = run;
+            }
+            __syncthreads();
+            const uint32_t n_first = s_nent;   // on-chip entries moved to the list
+            for (uint32_t e = tid; e < nlog; e += B) {
+                const uint32_t key = lc[e];
+                if (key == kEmpty) continue;
+                const uint32_t p = atomicAdd(&s_hist[(key * kPartMul) >> 24], 1u);
+                lc2[p] = key;
+                lv2[p] = lv[e];
+            }
+            if (tid == 0) s_fill = 0;
+            // passes over hash ranges [lo, hi) of at most per_pass log entries
+            // (so at most per_pass distinct columns); a pass that still does
+            // not fit is retried on the lower half of its range
+            const uint32_t per_pass = fill_cap - (fill_cap >> 2);
+            unsigned long long lo = 0, retry_hi = 0;
+            while (lo < (1ull << 32)) {
+                __syncthreads();
+                unsigned long long hi = retry_hi;
+                if (!hi) {
+                    const uint32_t b0 = (uint32_t)(lo >> 24);
+                    uint32_t b1 = b0 + 1;
+                    while (b1 < 256u && s_bstart[b1 + 1] - s_bstart[b0] <= per_pass) ++b1;
+                    hi = (unsigned long long)b1 << 24;
+                }
+                const uint32_t e0 = s_bstart[lo >> 24], e1 = s_bstart[((hi - 1) >> 24) + 1];
+                bool ok = true;
+                for (uint32_t e = e0 + tid; e < e1; e += B) {
+                    const uint32_t key = lc2[e];
+                    const unsigned long long hv = key * kPartMul;
+                    if (hv < lo || hv >= hi) continue;
+                    if (!onchip_add(key, lv2[e])) { ok = false; break; }
+                }
+                if (__syncthreads_or(!ok)) {
+                    clear_table();
+                    if (hi - lo > 1) {
+                        retry_hi = lo + ((hi - lo) >> 1);
+                    } else {   // one hash value is one column, which always fits: not reached
+                        report(a.st, row, MCMI_ERR_CAPACITY);
+                        retry_hi = 0;
+                        lo = hi;
+                    }
+                } else {
+                    flush();
+                    retry_hi = 0;
+                    lo = hi;
+                }
+                __syncthreads();
+                if (tid == 0) s_fill = 0;
+            }
+            __syncthreads();
+            if (tid == 0) atomicAdd(&a.st->spilled, (unsigned long long)(s_nent - n_first));
+        } else {
+            for (int h = tid; h < H; h += B) {
+                const uint32_t key = s_keys[h];
+                if (key == kEmpty) continue;
+                const VT v = finish(s_val[h], key);
+                if (key == (uint32_t)row) s_diag = (double)v;
+                s_val[h] = enc(v);
+            }
         }
         __syncthreads();
-        auto sval = [&](uint32_t h) -> double {
-            return PREC == 64 ? __longlong_as_double((long long)s_val[h]) : (double)*reinterpret_cast<const float *>(&s_val[h]);
-        };
-        auto gval = [&](uint32_t g) -> double {
-            return PREC == 64 ? __longlong_as_double((long long)gv[g]) : (double)*reinterpret_cast<const float *>(&gv[g]);
-        };
+        const uint32_t nent = s_nent;
 
         if (DUMP) {
-            for (int h = tid; h < H; h += B) {
-                const uint32_t k = s_keys[h];
-                if (k == kEmpty) continue;
+            auto dump = [&](uint32_t col, VT v, uint32_t vis) {
                 const uint32_t p = atomicAdd(&s_wpos, 1u);
                 if (p < (uint32_t)a.d_cap) {
-                    a.d_col[idx * a.d_cap + p] = (int32_t)k;
-                    a.d_val[idx * a.d_cap + p] = sval(h);
-                    a.d_vis[idx * a.d_cap + p] = s_aux[h];
+                    a.d_col[idx * a.d_cap + p] = (int32_t)col;
+                    a.d_val[idx * a.d_cap + p] = (double)v;
+                    a.d_vis[idx * a.d_cap + p] = vis;
                 }
-            }
-            for (uint32_t e = tid; e < nsp; e += B) {
-                const uint32_t g = gl[e];
-                if (g & kDead) continue;
-                const uint32_t p = atomicAdd(&s_wpos, 1u);
-                if (p < (uint32_t)a.d_cap) {
-                    a.d_col[idx * a.d_cap + p] = (int32_t)gk[g];
-                    a.d_val[idx * a.d_cap + p] = gval(g);
-                    a.d_vis[idx * a.d_cap + p] = gc[g];
-                }
-            }
+            };
+            for (int h = tid; h < H; h += B)
+                if (s_keys[h] != kEmpty) dump(s_keys[h], sval(h), s_aux[h]);
+            for (uint32_t e = tid; e < nent; e += B) dump(ec[e], dec(ev[e]), ecn[e]);
             __syncthreads();
             if (tid == 0) {
                 const uint32_t c = s_wpos;
@@ -450,34 +604,36 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             }
         } else {
             // ---- Sec. IV-B filter: diagonal kept; tau rule; top-k ----
-            double rowmax;
+            VT rowmax;
             if (PREC == 64) {
                 unsigned long long lm = 0;
                 for (int h = tid; h < H; h += B)
-                    if (s_keys[h] != kEmpty) lm = max(lm, (unsigned long long)__double_as_longlong(fabs(sval(h))));
-                for (uint32_t e = tid; e < nsp; e += B)
-                    if (!(gl[e] & kDead)) lm = max(lm, (unsigned long long)__double_as_longlong(fabs(gval(gl[e]))));
+                    if (s_keys[h] != kEmpty) lm = max(lm, (unsigned long long)__double_as_longlong(fabs((double)sval(h))));
+                for (uint32_t e = tid; e < nent; e += B)
+                    lm = max(lm, (unsigned long long)__double_as_longlong(fabs((double)dec(ev[e]))));
                 for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
                 __syncthreads();
                 if ((tid & 31) == 0) s_redu[tid >> 5] = lm;
                 __syncthreads();
                 lm = 0;
                 for (int w = 0; w < (B >> 5); ++w) lm = max(lm, s_redu[w]);
-                rowmax = __longlong_as_double((long long)lm);
+                rowmax = (VT)__longlong_as_double((long long)lm);
             } else {
                 float lmax = 0.0f;
                 for (int h = tid; h < H; h += B)
                     if (s_keys[h] != kEmpty) lmax = fmaxf(lmax, fabsf((float)sval(h)));
-                for (uint32_t e = tid; e < nsp; e += B)
-                    if (!(gl[e] & kDead)) lmax = fmaxf(lmax, fabsf((float)gval(gl[e])));
-                rowmax = (double)block_max(lmax, s_redf);
+                for (uint32_t e = tid; e < nent; e += B) lmax = fmaxf(lmax, fabsf((float)dec(ev[e])));
+                rowmax = (VT)block_max(lmax, s_redf);
             }
-            const double thr = a.tau > 0.0 ? __dmul_rn(a.tau, rowmax) : 0.0;
+            // threshold tau * rowmax in FP64; an FP32 build compares against the
+            // smallest float >= it, which keeps exactly the same entries
+            const double thr64 = use_tau ? __dmul_rn(a.tau, (double)rowmax) : 0.0;
+            const VT thr = PREC == 64 ? (VT)thr64 : (VT)__double2float_ru(thr64);
             const uint32_t rowc = (uint32_t)row;
-            auto is_cand = [&](uint32_t k, double v) -> bool {
-                return k != rowc && (a.tau <= 0.0 || fabs(v) >= thr);
+            auto is_cand = [&](uint32_t k, VT v) -> bool {
+                return k != rowc && (!use_tau || fabs(v) >= thr);
             };
-            // candidates: on-chip slot h as h, overflow list entry e as H + e
+            // candidates: on-chip slot h as h, entry-list element e as H + e
             const uint32_t list_cap = (uint32_t)H;
             for (int h = tid; h < H; h += B) {
                 const uint32_t k = s_keys[h];
@@ -486,9 +642,8 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                     if (p < list_cap) list_at(p) = (uint32_t)h;
                 }
             }
-            for (uint32_t e = tid; e < nsp; e += B) {
-                const uint32_t g = gl[e];
-                if (!(g & kDead) && is_cand(gk[g], gval(g))) {
+            for (uint32_t e = tid; e < nent; e += B) {
+                if (is_cand(ec[e], dec(ev[e]))) {
                     const uint32_t p = atomicAdd(&s_ncand, 1u);
                     if (p < list_cap) list_at(p) = (uint32_t)H + e;
                 }
@@ -502,27 +657,20 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                 if (compact) {
                     for (uint32_t i = tid; i < nc; i += B) {
                         const uint32_t c = list_at(i);
-                        if (c < (uint32_t)H) {
-                            const double v = sval(c);
-                            fn(__float_as_uint(fabsf((float)v)), s_keys[c], v);
-                        } else {
-                            const uint32_t g = gl[c - H] & ~kDead;
-                            const double v = gval(g);
-                            fn(__float_as_uint(fabsf((float)v)), gk[g], v);
-                        }
+                        const uint32_t col = c < (uint32_t)H ? s_keys[c] : ec[c - H];
+                        const VT v = c < (uint32_t)H ? sval(c) : dec(ev[c - H]);
+                        fn(__float_as_uint(fabsf((float)v)), col, v);
                     }
                 } else {
                     for (int h = tid; h < H; h += B) {
                         const uint32_t k = s_keys[h];
                         if (k == kEmpty) continue;
-                        const double v = sval(h);
+                        const VT v = sval(h);
                         if (is_cand(k, v)) fn(__float_as_uint(fabsf((float)v)), k, v);
                     }
-                    for (uint32_t e = tid; e < nsp; e += B) {
-                        const uint32_t g = gl[e];
-                        if (g & kDead) continue;
-                        const double v = gval(g);
-                        if (is_cand(gk[g], v)) fn(__float_as_uint(fabsf((float)v)), gk[g], v);
+                    for (uint32_t e = tid; e < nent; e += B) {
+                        const VT v = dec(ev[e]);
+                        if (is_cand(ec[e], v)) fn(__float_as_uint(fabsf((float)v)), ec[e], v);
                     }
                 }
             };
@@ -533,7 +681,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                 for (int shift = 24; shift >= 0; shift -= 8) {
                     for (int b = tid; b < 256; b += B) s_hist[b] = 0;
                     __syncthreads();
-                    for_cands([&](uint32_t mag, uint32_t, double) {
+                    for_cands([&](uint32_t mag, uint32_t, VT) {
                         if ((mag & mask) == pre) atomicAdd(&s_hist[(mag >> shift) & 255u], 1u);
                     });
                     __syncthreads();
@@ -547,7 +695,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                 vstar = pre;               // magnitude bits of the top_k-th largest
                 const uint32_t keep_ties = kk;
                 unsigned long long eq_l = 0;
-                for_cands([&](uint32_t mag, uint32_t, double) { eq_l += (mag == vstar); });
+                for_cands([&](uint32_t mag, uint32_t, VT) { eq_l += (mag == vstar); });
                 const unsigned long long neq = block_sum(eq_l, s_redu);
                 if (neq > keep_ties) {
                     // equal magnitudes: keep the keep_ties smallest columns (radix select on ~col)
@@ -555,7 +703,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                     for (int shift = 24; shift >= 0; shift -= 8) {
                         for (int b = tid; b < 256; b += B) s_hist[b] = 0;
                         __syncthreads();
-                        for_cands([&](uint32_t mag, uint32_t col, double) {
+                        for_cands([&](uint32_t mag, uint32_t col, VT) {
                             const uint32_t inv = ~col;
                             if (mag == vstar && (inv & cmask) == cpre) atomicAdd(&s_hist[(inv >> shift) & 255u], 1u);
                         });
@@ -587,18 +735,14 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             __syncthreads();
             const long long off = s_off;
             if (off >= 0) {
-                auto put = [&](uint32_t k, double v) {
+                auto put = [&](uint32_t k, VT v) {
                     const uint32_t p = atomicAdd(&s_wpos, 1u);
                     a.st_col[off + p] = k;
                     a.st_val[off + p] = (float)v;
                 };
-                if (tid == 0) {
-                    // the diagonal (always present: inserted before the walks)
-                    uint32_t h = 4 * hash_home(rowc, a.log2H - 2);
-                    while (s_keys[h] != rowc) h = (h + 1) & (uint32_t)(H - 1);
-                    put(rowc, sval(h));
-                }
-                for_cands([&](uint32_t mag, uint32_t col, double v) {
+                // the diagonal (always present: inserted before the walks)
+                if (tid == 0) put(rowc, (VT)s_diag);
+                for_cands([&](uint32_t mag, uint32_t col, VT v) {
                     const bool keep = !select || mag > vstar || (mag == vstar && (~col) >= cstar_inv);
                     if (keep) put(col, v);
                 });
@@ -606,18 +750,8 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
         }
         __syncthreads();
         // ---- reset the accumulator for the next row ----
-        for (int h = tid; h < H; h += B) {
-            s_keys[h] = kEmpty;
-            s_val[h] = 0ull;
-            if (DUMP || PREC == 64) s_aux[h] = 0u;
-        }
-        for (uint32_t e = tid; e < nsp; e += B) {
-            const uint32_t g = gl[e] & ~kDead;
-            gk[g] = kEmpty;
-            gv[g] = 0ull;
-            gc[g] = 0u;
-        }
-        if (tid == 0) { s_nspill = 0; s_fill = 0; }
+        clear_table();
+        if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; }
     }
 }
 

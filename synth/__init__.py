@@ -306,6 +306,8 @@ WORKLOADS = {
                          delta=1e-2, max_len=128, tau=0.0, top_k=16),
     "powerlaw_1m": dict(gen=lambda: powerlaw_random(1 << 20, seed=1003), chains=128,
                         delta=1e-3, max_len=256, tau=5e-3, top_k=0),
+    "powerlaw_128k": dict(gen=lambda: powerlaw_random(1 << 17, seed=1003), chains=128,
+                          delta=1e-3, max_len=256, tau=5e-3, top_k=0),
 }
 
 

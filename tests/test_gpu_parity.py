@@ -95,7 +95,9 @@ WALK_CASES = [
     ("stencil3d_12", 32, 0, 256, 128, 1e-2, {"threads": 256, "chains_per_thread": 1}),
     ("stencil2d", 64, 1, 1000, 64, 1e-3, {"threads": 128, "chains_per_thread": 2}),
     ("powerlaw_4k", 32, 1, 128, 256, 1e-3, {}),
-    ("powerlaw_4k", 32, 0, 128, 256, 1e-3, {"hash_log2": 6}),      # forces the global overflow table
+    ("powerlaw_4k", 32, 0, 128, 256, 1e-3, {"hash_log2": 6}),      # forces the overflow log
+    ("powerlaw_4k", 64, 1, 128, 256, 1e-3, {"hash_log2": 6}),
+    ("rand_long", 32, 1, 300, 256, 1e-3, {"hash_log2": 8, "threads": 64, "chains_per_thread": 2}),
     ("stencil2d", 32, 0, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 64}),
     # the FP32 Kahan accumulator
     ("stencil3d_12", 32, 0, 256, 128, 1e-2, {"accumulator": 1}),
@@ -216,6 +218,18 @@ def test_build_staging_regrowth_reruns_rows():
     # re-run rows are counted once
     orows, _, _ = _orc().walk(m, chains=64, max_len=40, delta=1e-3, seed=11, table=M.stats.table)
     assert M.stats.steps == sum(r["steps"] for r in orows)
+
+
+def test_build_through_the_overflow_log():
+    """Rows that reach far more columns than a 64-slot on-chip table: visits
+    go to the log and are reduced in several hash-range passes."""
+    m = _cases_small()["powerlaw_4k"]
+    rows = np.arange(0, m.n, 41)
+    for prec in (32, 64):
+        for tau, k in [(5e-3, 0), (0.0, 8)]:
+            M, *_ = _check_build(m, rows, 128, 256, 1e-3, tau, k, prec=prec, extra={"hash_log2": 6},
+                                 seed=17)
+            assert M.stats.spilled > 0
 
 
 def test_build_row_range():
