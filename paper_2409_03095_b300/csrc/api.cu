@@ -395,14 +395,14 @@ mcmi_status alloc_overflow(Scratch &S, WalkPlan &W, const Prepared &P, bool dump
     if (entc > 0xFFFFFFF0ull) return fail(MCMI_ERR_ARG, "N (L + 1) = %llu visits per row is too large", (unsigned long long)logc);
     a.log_cap = (uint32_t)logc;
     a.ent_cap = (uint32_t)entc;
-    const size_t per_block = (size_t)logc * 2 * 12 + (size_t)entc * (dump ? 16 : 12);
+    const size_t per_block = (size_t)logc * 2 * 16 + (size_t)entc * (dump ? 16 : 12);
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && (size_t)W.grid * per_block > fr / 4) {
         const size_t g = (fr / 4) / per_block;
         W.grid = g < 1 ? 1 : (int)g;
     }
     const size_t G = (size_t)W.grid;
-    a.log_col = S.get<uint32_t>(G * 2 * logc);
+    a.log_key = S.get<uint2>(G * 2 * logc);
     a.log_val = S.get<unsigned long long>(G * 2 * logc);
     a.ent_col = S.get<uint32_t>(G * entc);
     a.ent_val = S.get<unsigned long long>(G * entc);

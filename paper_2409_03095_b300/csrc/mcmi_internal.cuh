@@ -84,7 +84,7 @@ struct WalkArgs {
     // visits that find the on-chip table full go to a per-block log (column,
     // addend); after the walks the log is reduced on chip, in hash-range
     // passes, into a per-block list of the row's distinct entries
-    uint32_t *log_col;
+    uint2 *log_key;               // {column, FP32 bits of its 1/d_j}
     unsigned long long *log_val;
     uint32_t log_cap;             // log entries per block (>= the visits of one row)
     uint32_t *ent_col;

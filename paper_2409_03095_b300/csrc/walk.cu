@@ -27,13 +27,11 @@
 // in passes over disjoint hash ranges of the column index (a pass whose
 // columns do not fit is retried on half its range), each pass appending its
 // finished entries to the list.
-#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "mcmi_internal.cuh"
 #include "kernels.h"
 
-namespace cg = cooperative_groups;
 
 namespace mcmi {
 
@@ -212,6 +210,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
     __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent;
     __shared__ long long s_off;
     __shared__ double s_diag;
+    __shared__ unsigned long long s_pass_lo, s_pass_hi;
     __shared__ float s_redf[32];
     __shared__ unsigned long long s_redu[32];
     __shared__ uint32_t s_hist[256];
@@ -221,9 +220,9 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
     const int tid = threadIdx.x, B = blockDim.x;
     const uint32_t fill_cap = (uint32_t)(H - (H >> 2));      // on-chip table kept <= 75% full
     // log: the visits in arrival order, then the same entries bucketed by hash range
-    uint32_t *lc = a.log_col + (size_t)blockIdx.x * 2 * a.log_cap;
+    uint2 *lc = a.log_key + (size_t)blockIdx.x * 2 * a.log_cap;
     unsigned long long *lv = a.log_val + (size_t)blockIdx.x * 2 * a.log_cap;
-    uint32_t *lc2 = lc + a.log_cap;
+    uint2 *lc2 = lc + a.log_cap;
     unsigned long long *lv2 = lv + a.log_cap;
     uint32_t *ec = a.ent_col + (size_t)blockIdx.x * a.ent_cap;
     unsigned long long *ev = a.ent_val + (size_t)blockIdx.x * a.ent_cap;
@@ -244,8 +243,9 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
     // probing over 4-slot buckets, one 16-byte read per bucket; a key always
     // takes the first empty slot in probe order, so a search that meets an
     // empty slot before the key knows the key is absent.  Returns false when
-    // the column is absent and cannot be inserted (table at its fill cap, or
-    // no free slot within the probe window).
+    // the visit was not added: the column is absent and cannot be inserted
+    // (table at its fill cap, or no free slot within the probe window), or the
+    // table is at its cap and the column was not in the buckets searched.
     auto onchip_add = [&](uint32_t col, unsigned long long add) -> bool {
         uint32_t bkt = hash_home(col, a.log2H - 2);
         const uint32_t nb = (uint32_t)(H >> 2);
@@ -273,32 +273,44 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                 if (DUMP) atomicAdd(&s_aux[h], 1u);
                 return true;
             }
+            // a full bucket without the key: once the table is at its cap, the
+            // search stops here (the visit is logged; the merge after the walks
+            // finds the key if it sits further on)
+            if (*(volatile uint32_t *)&s_fill >= fill_cap) return false;
             bkt = (bkt + 1) & (nb - 1);
         }
         return false;
     };
-    // Slot of col on chip, or -1; no insertion (used once no insertions run).
+    // Slot of col on chip, or -1; no insertion (used once no insertions run):
+    // the bucket probe of onchip_add, ended by the first bucket with a free slot.
     auto onchip_find = [&](uint32_t col) -> int {
-        uint32_t h = 4 * hash_home(col, a.log2H - 2);
-        for (int p = 0; p < kProbeOnChip; ++p) {
-            const uint32_t k = s_keys[h];
-            if (k == col) return (int)h;
-            if (k == kEmpty) return -1;
-            h = (h + 1) & (uint32_t)(H - 1);
+        uint32_t bkt = hash_home(col, a.log2H - 2);
+        const uint32_t nb = (uint32_t)(H >> 2);
+        for (int p = 0; p < kProbeOnChip / 4; ++p) {
+            const uint4 kv = *reinterpret_cast<const uint4 *>(s_keys + 4 * bkt);
+            if (kv.x == col) return (int)(4 * bkt);
+            if (kv.y == col) return (int)(4 * bkt + 1);
+            if (kv.z == col) return (int)(4 * bkt + 2);
+            if (kv.w == col) return (int)(4 * bkt + 3);
+            if (kv.x == kEmpty || kv.y == kEmpty || kv.z == kEmpty || kv.w == kEmpty) return -1;
+            bkt = (bkt + 1) & (nb - 1);
         }
         return -1;
     };
-    // A visit that does not fit on chip is appended to the log; the lanes
+    // A visit that does not fit on chip is appended to the log, with the
+    // FP32 bits of 1/d_col from the record the chain has just read; the lanes
     // that arrive together reserve their positions with one atomic.
-    auto accumulate = [&](uint32_t col, unsigned long long add) {
+    auto accumulate = [&](uint32_t col, unsigned long long add, uint32_t invd_bits) {
         if (onchip_add(col, add)) return;
-        cg::coalesced_group g = cg::coalesced_threads();
+        const uint32_t m = __activemask();
+        const uint32_t lane = (uint32_t)tid & 31u;
+        const int leader = __ffs(m) - 1;
         uint32_t base = 0;
-        if (g.thread_rank() == 0) base = atomicAdd(&s_nlog, g.size());
-        base = g.shfl(base, 0);
-        const uint32_t pos = base + g.thread_rank();
+        if ((int)lane == leader) base = atomicAdd(&s_nlog, (uint32_t)__popc(m));
+        base = __shfl_sync(m, base, leader);
+        const uint32_t pos = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
         if (pos < a.log_cap) {
-            lc[pos] = col;
+            lc[pos] = make_uint2(col, invd_bits);
             lv[pos] = add;
         } else {
             report(a.st, s_row, MCMI_ERR_CAPACITY);   // cannot happen: a row makes at most N Lb visits
@@ -385,9 +397,11 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                     // leaves head-room in the fixed-point scale up to w_limit
                     if (FIX && a.lbkt && !(fabsf(w[j]) <= a.w_limit)) report(a.st, s_row, MCMI_ERR_CAPACITY);
                     if (FIX)
-                        accumulate(st[j], (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F)));
+                        accumulate(st[j], (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F)),
+                                   s[j][2]);
                     else
-                        accumulate(st[j], (unsigned long long)__float_as_uint(__fmul_rn(w[j], __uint_as_float(s[j][2]))));
+                        accumulate(st[j], (unsigned long long)__float_as_uint(__fmul_rn(w[j], __uint_as_float(s[j][2]))),
+                                   s[j][2]);
                 }
                 const uint32_t Q = s[j][0];
                 if (t[j] == a.L || !(fabsf(w[j]) >= a.delta_f) || Q == 0u) {
@@ -425,17 +439,23 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
         }
         const uint32_t nlog = min(s_nlog, a.log_cap);
 
-        // finished values M_ij = (1/N) X_ij / d_j of the raw accumulator words
-        auto finish = [&](unsigned long long raw, uint32_t col) -> VT {
+        // finished values M_ij = (1/N) X_ij / d_j of the raw accumulator
+        // words; invd = 1/d_j (the record's FP32 copy, or FP64), unused by the
+        // Kahan accumulator, whose sums are already scaled
+        auto load_invd = [&](uint32_t col) -> VT {
+            if (!FIX) return (VT)0;
+            if (PREC == 64) return (VT)__ldg(&a.rowd[col].y);
+            return (VT)__uint_as_float(__ldg(&a.slots[4 * (size_t)col].z));
+        };
+        auto finish = [&](unsigned long long raw, VT invd) -> VT {
             if (PREC == 64) {
                 const double X = __dmul_rn(__ll2double_rn((long long)raw), a.fix_inv);   // exact scaling
-                return __dmul_rn(__ddiv_rn(X, (double)a.N), __ldg(&a.rowd[col].y));
+                return (VT)__dmul_rn(__ddiv_rn(X, (double)a.N), (double)invd);
             } else if (FIX) {
                 // fl32(|X| 2^F), then (2^-F / N) and 1/d_j: three FP32 roundings
                 const long long x = (long long)raw;
                 const float m = u64_to_f32_rn((unsigned long long)(x < 0 ? -x : x));
-                const float invd = __uint_as_float(__ldg(&a.slots[4 * (size_t)col].z));
-                const float v = __fmul_rn(__fmul_rn(m, a.fin_scale), invd);
+                const float v = __fmul_rn(__fmul_rn(m, a.fin_scale), (float)invd);
                 return (VT)(x < 0 ? -v : v);
             } else {
                 const float sum = __uint_as_float((uint32_t)raw), c = __uint_as_float((uint32_t)(raw >> 32));
@@ -459,20 +479,41 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                 if (DUMP || PREC == 64) s_aux[h] = 0u;
             }
         };
-        // finished on-chip entries appended to the entry list; the table is cleared
-        auto flush = [&]() {
-            for (int h = tid; h < H; h += B) {
-                const uint32_t key = s_keys[h];
-                if (key == kEmpty) continue;
-                const VT v = finish(s_val[h], key);
-                if (key == (uint32_t)row) s_diag = (double)v;
-                const uint32_t p = atomicAdd(&s_nent, 1u);
-                ec[p] = key;
-                ev[p] = enc(v);
-                if (DUMP) ecn[p] = s_aux[h];
-                s_keys[h] = kEmpty;
-                s_val[h] = 0ull;
-                if (DUMP || PREC == 64) s_aux[h] = 0u;
+        // The loops below take their global loads in batches (UF, UL per
+        // thread) issued before any of them is used: one L2 round trip per
+        // batch instead of one per element.
+        constexpr int UF = 8, UL = 4;
+        VT lmax = (VT)0;   // largest |M_ij| this thread has finished
+        // Finishes the on-chip entries, in place, or appended to the entry
+        // list with the table cleared.
+        auto finish_table = [&](bool to_list) {
+            for (int h0 = tid; h0 < H; h0 += UF * B) {
+                uint32_t key[UF];
+                VT invd[UF];
+#pragma unroll
+                for (int u = 0; u < UF; ++u) key[u] = h0 + u * B < H ? s_keys[h0 + u * B] : kEmpty;
+#pragma unroll
+                for (int u = 0; u < UF; ++u) invd[u] = key[u] != kEmpty ? load_invd(key[u]) : (VT)0;
+#pragma unroll
+                for (int u = 0; u < UF; ++u) {
+                    if (key[u] == kEmpty) continue;
+                    const int h = h0 + u * B;
+                    const VT v = finish(s_val[h], invd[u]);
+                    const VT av = v < (VT)0 ? -v : v;
+                    lmax = av > lmax ? av : lmax;
+                    if (key[u] == (uint32_t)row) s_diag = (double)v;
+                    if (to_list) {
+                        const uint32_t p = atomicAdd(&s_nent, 1u);
+                        ec[p] = key[u];
+                        ev[p] = enc(v);
+                        if (DUMP) ecn[p] = s_aux[h];
+                        s_keys[h] = kEmpty;
+                        s_val[h] = 0ull;
+                        if (DUMP || PREC == 64) s_aux[h] = 0u;
+                    } else {
+                        s_val[h] = enc(v);
+                    }
+                }
             }
         };
 
@@ -481,24 +522,31 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
         if (nlog) {   // block-uniform
             // entries whose column is on chip are added there; the others are
             // counted per hash-range bucket (top 8 bits of col * kPartMul)
-            for (uint32_t e = tid; e < nlog; e += B) {
-                const uint32_t key = lc[e];
-                const int h = onchip_find(key);
-                if (h >= 0) {
-                    const unsigned long long add = lv[e];
-                    if (FIX) fix_add_shared(&s_val[h], (long long)add);
-                    else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
-                    if (DUMP) atomicAdd(&s_aux[h], 1u);
-                    lc[e] = kEmpty;
-                } else {
-                    ++nrem;
-                    atomicAdd(&s_hist[(key * kPartMul) >> 24], 1u);
+            for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
+                uint32_t key[UL];
+#pragma unroll
+                for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B].x : kEmpty;
+#pragma unroll
+                for (int u = 0; u < UL; ++u) {
+                    if (key[u] == kEmpty) continue;
+                    const uint32_t e = e0 + u * B;
+                    const int h = onchip_find(key[u]);
+                    if (h >= 0) {
+                        const unsigned long long add = lv[e];
+                        if (FIX) fix_add_shared(&s_val[h], (long long)add);
+                        else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
+                        if (DUMP) atomicAdd(&s_aux[h], 1u);
+                        lc[e].x = kEmpty;
+                    } else {
+                        ++nrem;
+                        atomicAdd(&s_hist[(key[u] * kPartMul) >> 24], 1u);
+                    }
                 }
             }
             nrem = (uint32_t)block_sum(nrem, s_redu);
         }
         if (nrem) {   // block-uniform
-            flush();
+            finish_table(true);
             // bucket starts: exclusive scan of the 256 counts (warp 0, 8 per lane)
             if (tid < 32) {
                 uint32_t c8[8], tot = 0;
@@ -523,35 +571,133 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             }
             __syncthreads();
             const uint32_t n_first = s_nent;   // on-chip entries moved to the list
-            for (uint32_t e = tid; e < nlog; e += B) {
-                const uint32_t key = lc[e];
-                if (key == kEmpty) continue;
-                const uint32_t p = atomicAdd(&s_hist[(key * kPartMul) >> 24], 1u);
-                lc2[p] = key;
-                lv2[p] = lv[e];
+            for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
+                uint2 key[UL];
+                unsigned long long val[UL];
+#pragma unroll
+                for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
+#pragma unroll
+                for (int u = 0; u < UL; ++u) val[u] = key[u].x != kEmpty ? lv[e0 + u * B] : 0ull;
+#pragma unroll
+                for (int u = 0; u < UL; ++u) {
+                    if (key[u].x == kEmpty) continue;
+                    const uint32_t p = atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
+                    lc2[p] = key[u];
+                    lv2[p] = val[u];
+                }
             }
             if (tid == 0) s_fill = 0;
-            // passes over hash ranges [lo, hi) of at most per_pass log entries
-            // (so at most per_pass distinct columns); a pass that still does
-            // not fit is retried on the lower half of its range
+            __syncthreads();
+            // Buckets of at most 32 entries: one warp each.  Lanes holding the
+            // same column find each other with __match_any_sync; the group's
+            // lowest lane sums it in a per-warp scratch row (value words of the
+            // empty table, which needs B <= H slots) and appends the finished entry.
+            const bool by_warp = B <= H;
+            if (by_warp) {
+                const uint32_t lane = (uint32_t)tid & 31u;
+                unsigned long long *scratch = s_val + (tid & ~31);
+                constexpr int UB = 2;   // buckets per round: their loads are in flight together
+                const int nw = B >> 5;
+                for (int bk0 = tid >> 5; bk0 < 256; bk0 += UB * nw) {
+                    uint2 key[UB];
+                    unsigned long long val[UB];
+                    uint32_t cnt[UB];
+#pragma unroll
+                    for (int u = 0; u < UB; ++u) {
+                        const int bk = bk0 + u * nw;
+                        const uint32_t s0 = bk < 256 ? s_bstart[bk] : 0u;
+                        cnt[u] = bk < 256 ? s_bstart[bk + 1] - s0 : 0u;
+                        const bool act = cnt[u] <= 32u && lane < cnt[u];
+                        key[u] = act ? lc2[s0 + lane] : make_uint2(kEmpty, 0u);
+                        val[u] = act ? lv2[s0 + lane] : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < UB; ++u) {
+                        if (cnt[u] == 0u || cnt[u] > 32u) continue;   // warp-uniform
+                        const bool act = lane < cnt[u];
+                        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key[u].x);
+                        const uint32_t leader = (uint32_t)__ffs(grp) - 1u;
+                        scratch[lane] = 0ull;
+                        __syncwarp();
+                        if (act) {
+                            if (FIX) fix_add_shared(&scratch[leader], (long long)val[u]);
+                            else comp_add(&scratch[leader], __uint_as_float((uint32_t)val[u]));
+                        }
+                        __syncwarp();
+                        const bool lead = act && lane == leader;
+                        VT v = (VT)0;
+                        if (lead) {
+                            const VT invd = PREC == 64 ? load_invd(key[u].x) : (VT)__uint_as_float(key[u].y);
+                            v = finish(scratch[lane], invd);
+                            const VT av = v < (VT)0 ? -v : v;
+                            lmax = av > lmax ? av : lmax;
+                        }
+                        const uint32_t lm = __ballot_sync(0xFFFFFFFFu, lead);
+                        const int first = __ffs(lm) - 1;
+                        uint32_t base = 0;
+                        if ((int)lane == first) base = atomicAdd(&s_nent, (uint32_t)__popc(lm));
+                        base = __shfl_sync(0xFFFFFFFFu, base, first);
+                        if (lead) {
+                            const uint32_t p = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
+                            ec[p] = key[u].x;
+                            ev[p] = enc(v);
+                            if (DUMP) ecn[p] = (uint32_t)__popc(grp);
+                        }
+                        __syncwarp();
+                    }
+                }
+                scratch[lane] = 0ull;
+            }
+            // larger buckets stay pending: s_hist[b] = entries of pending bucket b, else 0
+            for (int bk = tid; bk < 256; bk += B) {
+                const uint32_t cnt = s_bstart[bk + 1] - s_bstart[bk];
+                s_hist[bk] = (cnt > 32u || !by_warp) ? cnt : 0u;
+            }
+            // Pending buckets: passes over hash ranges [lo, hi) holding at most
+            // per_pass of their entries (so at most per_pass distinct columns)
+            // through the on-chip table; a pass that still does not fit is
+            // retried on the lower half of its range.
             const uint32_t per_pass = fill_cap - (fill_cap >> 2);
             unsigned long long lo = 0, retry_hi = 0;
-            while (lo < (1ull << 32)) {
+            for (;;) {
                 __syncthreads();
-                unsigned long long hi = retry_hi;
-                if (!hi) {
-                    const uint32_t b0 = (uint32_t)(lo >> 24);
-                    uint32_t b1 = b0 + 1;
-                    while (b1 < 256u && s_bstart[b1 + 1] - s_bstart[b0] <= per_pass) ++b1;
-                    hi = (unsigned long long)b1 << 24;
+                if (tid == 0) {
+                    unsigned long long l = lo, h = retry_hi;
+                    if (!h) {
+                        uint32_t b0 = (uint32_t)(l >> 24);
+                        while (b0 < 256u && s_hist[b0] == 0u) ++b0;
+                        if (b0 > (uint32_t)(l >> 24)) l = (unsigned long long)b0 << 24;
+                        if (b0 < 256u) {
+                            uint32_t b1 = b0 + 1, c = s_hist[b0];
+                            while (b1 < 256u && c + s_hist[b1] <= per_pass) c += s_hist[b1++];
+                            h = (unsigned long long)b1 << 24;
+                        } else {
+                            l = h = 1ull << 32;
+                        }
+                    }
+                    s_pass_lo = l;
+                    s_pass_hi = h;
                 }
+                __syncthreads();
+                lo = s_pass_lo;
+                const unsigned long long hi = s_pass_hi;
+                if (lo >= (1ull << 32)) break;
                 const uint32_t e0 = s_bstart[lo >> 24], e1 = s_bstart[((hi - 1) >> 24) + 1];
                 bool ok = true;
-                for (uint32_t e = e0 + tid; e < e1; e += B) {
-                    const uint32_t key = lc2[e];
-                    const unsigned long long hv = key * kPartMul;
-                    if (hv < lo || hv >= hi) continue;
-                    if (!onchip_add(key, lv2[e])) { ok = false; break; }
+                for (uint32_t eb = e0 + tid; eb < e1 && ok; eb += UL * B) {
+                    uint32_t key[UL];
+                    unsigned long long val[UL];
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) key[u] = eb + u * B < e1 ? lc2[eb + u * B].x : kEmpty;
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) val[u] = key[u] != kEmpty ? lv2[eb + u * B] : 0ull;
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) {
+                        if (key[u] == kEmpty) continue;
+                        const unsigned long long hv = key[u] * kPartMul;
+                        if (hv < lo || hv >= hi || s_hist[hv >> 24] == 0u) continue;
+                        if (!onchip_add(key[u], val[u])) ok = false;
+                    }
                 }
                 if (__syncthreads_or(!ok)) {
                     clear_table();
@@ -563,7 +709,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                         lo = hi;
                     }
                 } else {
-                    flush();
+                    finish_table(true);
                     retry_hi = 0;
                     lo = hi;
                 }
@@ -573,13 +719,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             __syncthreads();
             if (tid == 0) atomicAdd(&a.st->spilled, (unsigned long long)(s_nent - n_first));
         } else {
-            for (int h = tid; h < H; h += B) {
-                const uint32_t key = s_keys[h];
-                if (key == kEmpty) continue;
-                const VT v = finish(s_val[h], key);
-                if (key == (uint32_t)row) s_diag = (double)v;
-                s_val[h] = enc(v);
-            }
+            finish_table(false);
         }
         __syncthreads();
         const uint32_t nent = s_nent;
@@ -606,11 +746,8 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             // ---- Sec. IV-B filter: diagonal kept; tau rule; top-k ----
             VT rowmax;
             if (PREC == 64) {
-                unsigned long long lm = 0;
-                for (int h = tid; h < H; h += B)
-                    if (s_keys[h] != kEmpty) lm = max(lm, (unsigned long long)__double_as_longlong(fabs((double)sval(h))));
-                for (uint32_t e = tid; e < nent; e += B)
-                    lm = max(lm, (unsigned long long)__double_as_longlong(fabs((double)dec(ev[e]))));
+                // |M_ij| >= 0: the order of the FP64 bit patterns is the order of the values
+                unsigned long long lm = (unsigned long long)__double_as_longlong((double)lmax);
                 for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
                 __syncthreads();
                 if ((tid & 31) == 0) s_redu[tid >> 5] = lm;
@@ -619,11 +756,7 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                 for (int w = 0; w < (B >> 5); ++w) lm = max(lm, s_redu[w]);
                 rowmax = (VT)__longlong_as_double((long long)lm);
             } else {
-                float lmax = 0.0f;
-                for (int h = tid; h < H; h += B)
-                    if (s_keys[h] != kEmpty) lmax = fmaxf(lmax, fabsf((float)sval(h)));
-                for (uint32_t e = tid; e < nent; e += B) lmax = fmaxf(lmax, fabsf((float)dec(ev[e])));
-                rowmax = (VT)block_max(lmax, s_redf);
+                rowmax = (VT)block_max((float)lmax, s_redf);
             }
             // threshold tau * rowmax in FP64; an FP32 build compares against the
             // smallest float >= it, which keeps exactly the same entries
@@ -642,10 +775,20 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                     if (p < list_cap) list_at(p) = (uint32_t)h;
                 }
             }
-            for (uint32_t e = tid; e < nent; e += B) {
-                if (is_cand(ec[e], dec(ev[e]))) {
-                    const uint32_t p = atomicAdd(&s_ncand, 1u);
-                    if (p < list_cap) list_at(p) = (uint32_t)H + e;
+            for (uint32_t e0 = tid; e0 < nent; e0 += UL * B) {
+                uint32_t key[UL];
+                unsigned long long raw[UL];
+#pragma unroll
+                for (int u = 0; u < UL; ++u) {
+                    key[u] = e0 + u * B < nent ? ec[e0 + u * B] : kEmpty;
+                    raw[u] = e0 + u * B < nent ? ev[e0 + u * B] : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < UL; ++u) {
+                    if (key[u] != kEmpty && is_cand(key[u], dec(raw[u]))) {
+                        const uint32_t p = atomicAdd(&s_ncand, 1u);
+                        if (p < list_cap) list_at(p) = (uint32_t)H + e0 + u * B;
+                    }
                 }
             }
             __syncthreads();

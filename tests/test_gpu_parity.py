@@ -225,9 +225,11 @@ def test_build_through_the_overflow_log():
     go to the log and are reduced in several hash-range passes."""
     m = _cases_small()["powerlaw_4k"]
     rows = np.arange(0, m.n, 41)
-    for prec in (32, 64):
+    # 2^6 slots (< 128 threads): hash-range passes only; 2^8 and 2^11 slots:
+    # per-warp bucket reduction, passes for the rare buckets above 32 entries
+    for prec, log2h in [(32, 6), (64, 6), (32, 8), (64, 8), (32, 11)]:
         for tau, k in [(5e-3, 0), (0.0, 8)]:
-            M, *_ = _check_build(m, rows, 128, 256, 1e-3, tau, k, prec=prec, extra={"hash_log2": 6},
+            M, *_ = _check_build(m, rows, 128, 256, 1e-3, tau, k, prec=prec, extra={"hash_log2": log2h},
                                  seed=17)
             assert M.stats.spilled > 0
 
