@@ -77,6 +77,30 @@ def _dist():
     return world, rank, local
 
 
+def _init_ranks(world):
+    """One process per GPU (torchrun); gloo when no GPU is present."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+
+
+def _reduce_ranks(tot_ms, steps, device):
+    """Whole-job figures: the slowest rank's timed milliseconds and the sum of
+    the ranks' steps.  Ranks build independent matrices (weak scaling), so the
+    only exchange is this reduction of their results."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(tot_ms), float(steps)
+    t = torch.tensor([float(tot_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(steps)], device=device, dtype=torch.float64)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -238,9 +262,7 @@ def run_reference(a):
 def run_ours(a):
     import torch
     world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    _init_ranks(world)
     torch.cuda.set_device(local)
     import paper_2409_03095_b300 as mc
     mc.load()
@@ -287,16 +309,7 @@ def run_ours(a):
     if world > 1:
         torch.distributed.barrier()
     ck = clocks.stop() if clocks else None
-    tot_ms = sum(times)
-    tot_steps = steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        s = torch.tensor([float(steps)], device="cuda", dtype=torch.float64)
-        dist.all_reduce(s, op=dist.ReduceOp.SUM)
-        tot_steps = s.item()
+    tot_ms, tot_steps = _reduce_ranks(sum(times), steps, "cuda")
     value = tot_steps / (tot_ms / 1e3)
 
     # e2e through the public API with host buffers: H2D of B, build, apply,
@@ -496,6 +509,7 @@ def run_batched(a):
     import torch
     import paper_2409_03095_b300 as mc
     world, rank, local = _dist()
+    _init_ranks(world)
     torch.cuda.set_device(local)
     mc.load()
     t0 = time.perf_counter()
@@ -512,6 +526,8 @@ def run_batched(a):
         Ms, st = mc.mcmi_build_batched(Bs, p)
         del Ms
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     if clocks:
         clocks.start()
     times, steps, walk_ms, launches = [], 0, [], 0
@@ -531,10 +547,13 @@ def run_batched(a):
         del Ms
     if clocks:
         clocks.end()
+    if world > 1:
+        torch.distributed.barrier()
     ck = clocks.stop() if clocks else None
-    tot_ms = sum(times)
-    value = steps / (tot_ms / 1e3)
+    tot_ms, tot_steps = _reduce_ranks(sum(times), steps, "cuda")
+    value = tot_steps / (tot_ms / 1e3)
     if rank != 0:
+        torch.distributed.destroy_process_group()
         return 0
     peaks, peak_src = _peaks()
     visits = steps + 128 * st.rows * a.steps
@@ -543,7 +562,7 @@ def run_batched(a):
             "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch_512: {WORKLOADS['batch_512']}", "matrices": len(mats),
-                       "rows": int(st.rows), "rows_per_s": st.rows * a.steps / (tot_ms / 1e3),
+                       "rows": int(st.rows), "rows_per_s": st.rows * a.steps * world / (tot_ms / 1e3),
                        "steps_per_build": int(st.steps), "generation_s": gen_s,
                        "autotuned": {"threads": st.threads, "chains_per_thread": st.chains_per_thread,
                                      "hash_log2": st.hash_log2, "table": ["cumulative", "alias"][st.table]},
@@ -554,6 +573,8 @@ def run_batched(a):
                          "bytes_per_unit": "64 B per visited state"},
             "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck}
     print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
