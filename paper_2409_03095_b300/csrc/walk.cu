@@ -184,8 +184,11 @@ __device__ __forceinline__ void load_slot(const uint4 *sp, uint32_t (&w)[16])
 
 }  // namespace
 
+// Register cap: 72 per thread lets seven 128-thread blocks (896 chains) share
+// an SM with one chain per thread without spilling; measured faster than
+// eight blocks at 64 registers, which spill.
 template <int PREC, int TABLE, int ACC, bool DUMP, int CPT>
-__global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk(WalkArgs a)
+__global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
     // finished values and the filter work in the build's precision: FP32
@@ -238,15 +241,14 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
     }
     if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; }
 
-    // Adds one visit to the on-chip table.  The addend is the fixed-point
-    // weight, or the FP32 bits of W / d_j for the Kahan accumulator.  Linear
-    // probing over 4-slot buckets, one 16-byte read per bucket; a key always
-    // takes the first empty slot in probe order, so a search that meets an
-    // empty slot before the key knows the key is absent.  Returns false when
-    // the visit was not added: the column is absent and cannot be inserted
-    // (table at its fill cap, or no free slot within the probe window), or the
-    // table is at its cap and the column was not in the buckets searched.
-    auto onchip_add = [&](uint32_t col, unsigned long long add) -> bool {
+    // Slot of col in the on-chip table, inserting it if absent; -1 when it
+    // is not added.  Linear probing over 4-slot buckets, one 16-byte read per
+    // bucket; a key always takes the first empty slot in probe order, so a
+    // search that meets an empty slot before the key knows the key is absent.
+    // -1: the column is absent and cannot be inserted (table at its fill cap,
+    // or no free slot within the probe window), or the table is at its cap
+    // and the column was not in the buckets searched.
+    auto onchip_slot = [&](uint32_t col) -> int {
         uint32_t bkt = hash_home(col, a.log2H - 2);
         const uint32_t nb = (uint32_t)(H >> 2);
 #pragma unroll 1
@@ -255,31 +257,36 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
                          : "=r"(kv.x), "=r"(kv.y), "=r"(kv.z), "=r"(kv.w)
                          : "r"((uint32_t)__cvta_generic_to_shared(s_keys + 4 * bkt)));
-            int slot = kv.x == col ? 0 : kv.y == col ? 1 : kv.z == col ? 2 : kv.w == col ? 3 : -1;
-            if (slot < 0) {
-                const int e = kv.x == kEmpty ? 0 : kv.y == kEmpty ? 1 : kv.z == kEmpty ? 2 : kv.w == kEmpty ? 3 : -1;
-                if (e >= 0) {
-                    if (*(volatile uint32_t *)&s_fill >= fill_cap) return false;
-                    const uint32_t old = atomicCAS(&s_keys[4 * bkt + e], kEmpty, col);
-                    if (old == kEmpty) atomicAdd(&s_fill, 1u);
-                    if (old == kEmpty || old == col) slot = e;
-                    else { --p; continue; }   // another key took it: read the bucket again
-                }
-            }
-            if (slot >= 0) {
-                const uint32_t h = 4 * bkt + (uint32_t)slot;
-                if (FIX) fix_add_shared(&s_val[h], (long long)add);
-                else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
-                if (DUMP) atomicAdd(&s_aux[h], 1u);
-                return true;
+            const int slot = kv.x == col ? 0 : kv.y == col ? 1 : kv.z == col ? 2 : kv.w == col ? 3 : -1;
+            if (slot >= 0) return (int)(4 * bkt) + slot;
+            const int e = kv.x == kEmpty ? 0 : kv.y == kEmpty ? 1 : kv.z == kEmpty ? 2 : kv.w == kEmpty ? 3 : -1;
+            if (e >= 0) {
+                if (*(volatile uint32_t *)&s_fill >= fill_cap) return -1;
+                const uint32_t old = atomicCAS(&s_keys[4 * bkt + e], kEmpty, col);
+                if (old == kEmpty) atomicAdd(&s_fill, 1u);
+                if (old == kEmpty || old == col) return (int)(4 * bkt) + e;
+                --p;   // another key took the slot: read the bucket again
+                continue;
             }
             // a full bucket without the key: once the table is at its cap, the
             // search stops here (the visit is logged; the merge after the walks
             // finds the key if it sits further on)
-            if (*(volatile uint32_t *)&s_fill >= fill_cap) return false;
+            if (*(volatile uint32_t *)&s_fill >= fill_cap) return -1;
             bkt = (bkt + 1) & (nb - 1);
         }
-        return false;
+        return -1;
+    };
+    // Adds one visit to the on-chip table (the addend: the fixed-point weight,
+    // or the FP32 bits of W / d_j for the Kahan accumulator); false when it
+    // was not added.  The atomics come after the probe loop, where the lanes
+    // of a warp have re-converged, so that one instruction serves them all.
+    auto onchip_add = [&](uint32_t col, unsigned long long add) -> bool {
+        const int h = onchip_slot(col);
+        if (h < 0) return false;
+        if (FIX) fix_add_shared(&s_val[h], (long long)add);
+        else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
+        if (DUMP) atomicAdd(&s_aux[h], 1u);
+        return true;
     };
     // Slot of col on chip, or -1; no insertion (used once no insertions run):
     // the bucket probe of onchip_add, ended by the first bucket with a free slot.
@@ -297,26 +304,6 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
         }
         return -1;
     };
-    // A visit that does not fit on chip is appended to the log, with the
-    // FP32 bits of 1/d_col from the record the chain has just read; the lanes
-    // that arrive together reserve their positions with one atomic.
-    auto accumulate = [&](uint32_t col, unsigned long long add, uint32_t invd_bits) {
-        if (onchip_add(col, add)) return;
-        const uint32_t m = __activemask();
-        const uint32_t lane = (uint32_t)tid & 31u;
-        const int leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if ((int)lane == leader) base = atomicAdd(&s_nlog, (uint32_t)__popc(m));
-        base = __shfl_sync(m, base, leader);
-        const uint32_t pos = base + (uint32_t)__popc(m & ((1u << lane) - 1u));
-        if (pos < a.log_cap) {
-            lc[pos] = make_uint2(col, invd_bits);
-            lv[pos] = add;
-        } else {
-            report(a.st, s_row, MCMI_ERR_CAPACITY);   // cannot happen: a row makes at most N Lb visits
-        }
-    };
-
     for (;;) {
         __syncthreads();
         if (tid == 0) {
@@ -379,8 +366,12 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             t[j] = 0;
             r4[j] = make_uint4(0, 0, 0, 0);
         }
+        // All lanes of a warp run every iteration (the loop test is a warp
+        // vote), so that the shared atomics of a step are issued by the whole
+        // warp at once; lanes without a live chain only take part in the votes.
+        const uint32_t lane = (uint32_t)tid & 31u;
 #pragma unroll 1
-        while (k[0] < a.N || (CPT > 1 && k[CPT - 1] < a.N)) {
+        while (__any_sync(0xFFFFFFFFu, k[0] < a.N || (CPT > 1 && k[CPT - 1] < a.N))) {
             uint32_t s[CPT][16];
             double2 rd[CPT];
 #pragma unroll
@@ -391,18 +382,44 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
                 }
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                if (k[j] >= a.N) continue;
-                if (t[j] > 0) {
+                const bool live = k[j] < a.N;
+                const bool acc = live && t[j] > 0;   // the visit of st[j] (t = 0 is counted at the row start)
+                unsigned long long add = 0ull;
+                int h = -1;
+                if (acc) {
                     // a learned proposal's weights are not bounded by 1: the host
                     // leaves head-room in the fixed-point scale up to w_limit
                     if (FIX && a.lbkt && !(fabsf(w[j]) <= a.w_limit)) report(a.st, s_row, MCMI_ERR_CAPACITY);
-                    if (FIX)
-                        accumulate(st[j], (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F)),
-                                   s[j][2]);
-                    else
-                        accumulate(st[j], (unsigned long long)__float_as_uint(__fmul_rn(w[j], __uint_as_float(s[j][2]))),
-                                   s[j][2]);
+                    if (FIX) add = (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F));
+                    else add = (unsigned long long)__float_as_uint(__fmul_rn(w[j], __uint_as_float(s[j][2])));
+                    h = onchip_slot(st[j]);
                 }
+                __syncwarp();
+                if (acc && h >= 0) {
+                    if (FIX) fix_add_shared(&s_val[h], (long long)add);
+                    else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
+                    if (DUMP) atomicAdd(&s_aux[h], 1u);
+                }
+                // visits that do not fit on chip go to the log with the FP32 bits
+                // of 1/d_col from the record just read; one atomic per warp
+                const bool to_log = acc && h < 0;
+                const uint32_t lm = __ballot_sync(0xFFFFFFFFu, to_log);
+                if (lm) {
+                    const int first = __ffs(lm) - 1;
+                    uint32_t base = 0;
+                    if ((int)lane == first) base = atomicAdd(&s_nlog, (uint32_t)__popc(lm));
+                    base = __shfl_sync(0xFFFFFFFFu, base, first);
+                    if (to_log) {
+                        const uint32_t pos = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
+                        if (pos < a.log_cap) {
+                            lc[pos] = make_uint2(st[j], s[j][2]);
+                            lv[pos] = add;
+                        } else {
+                            report(a.st, s_row, MCMI_ERR_CAPACITY);   // cannot happen: a row makes at most N Lb visits
+                        }
+                    }
+                }
+                if (!live) continue;
                 const uint32_t Q = s[j][0];
                 if (t[j] == a.L || !(fabsf(w[j]) >= a.delta_f) || Q == 0u) {
                     my_steps += (unsigned long long)t[j];
@@ -594,7 +611,6 @@ __global__ void __launch_bounds__(CPT == 2 ? 128 : 256, CPT == 2 ? 6 : 4) k_walk
             // empty table, which needs B <= H slots) and appends the finished entry.
             const bool by_warp = B <= H;
             if (by_warp) {
-                const uint32_t lane = (uint32_t)tid & 31u;
                 unsigned long long *scratch = s_val + (tid & ~31);
                 constexpr int UB = 2;   // buckets per round: their loads are in flight together
                 const int nw = B >> 5;
