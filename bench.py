@@ -62,6 +62,7 @@ def _args():
     ap.add_argument("--workload", default="stencil3d_64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-quality", action="store_true", help="skip the (untimed) estimator-error check")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--learned", action="store_true",
                     help="learned vs |c| proposal on the anisotropic 1024^2 problem (one JSON line)")
@@ -384,6 +385,17 @@ def run_ours(a):
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = _cpu_baseline(m, w, a.cpu_seconds, last.table)
+    # quality of the timed builds (untimed): estimator error on sample rows
+    quality = None
+    if not a.no_quality:
+        try:
+            qrows = np.random.default_rng(5).choice(m.n, 16, replace=False)
+            eps_hat, _ = _estimator_error(mc, B, m, p, qrows, _exact_rows(mc, m, p.alpha, qrows))
+            quality = {"eps_hat": eps_hat, "sample_rows": len(qrows),
+                       "definition": "mean relative L2 error of unfiltered rows against exact rows of B^-1 "
+                                     "(FP64 BiCGstab on B^T to 1e-11)"}
+        except Exception as exc:  # measurement only
+            quality = {"error": str(exc)}
     rows_per_s = (last.rows * a.steps * world) / (tot_ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -393,12 +405,48 @@ def run_ours(a):
                        "nnz_M": last.nnz, "steps_per_build": last.steps, "max_len_bound": last.max_len_bound,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"rows on one GPU; {world} independent builds (one per GPU)",
-                       "stage_ms": {"prepare": last.ms_prepare, "walk": last.ms_walk, "assemble": last.ms_assemble}},
+                       "stage_ms": {"prepare": last.ms_prepare, "walk": last.ms_walk, "assemble": last.ms_assemble},
+                       "quality": quality},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _exact_rows(mc, m, alpha, rows):
+    """Exact rows of Bhat^-1 (Bhat = B with the Eq. 1 diagonal augmentation):
+    row i = (Bhat^-T e_i)^T, by the library's FP64 BiCGstab on Bhat^T
+    (assembled on the host) to a relative residual of 1e-11."""
+    import torch
+    from synth import Csr
+    Bh = m.to_scipy().tolil()
+    dd = m.to_scipy().diagonal()
+    bn = float(np.abs(m.to_scipy()).sum(axis=1).max())
+    Bh.setdiag(dd + alpha * bn * np.where(dd < 0, -1.0, 1.0))
+    BhT = Bh.tocsr().T.tocsr()
+    BhT.sort_indices()
+    BT = mc.DeviceCsr.from_host(Csr(m.n, BhT.indptr.astype(np.int64), BhT.indices.astype(np.int32), BhT.data))
+    exact = []
+    for r in rows:
+        e = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+        e[int(r)] = 1.0
+        x = torch.zeros_like(e)
+        mc.mcmi_solve(BT, None, e, x, mc.SOLVE_BICGSTAB, rtol=1e-11, maxit=20000)
+        exact.append(x.cpu().numpy())
+    return exact
+
+
+def _estimator_error(mc, B, m, p, rows, exact):
+    """eps_hat: mean over sample rows of ||X_i - x_i*||_2 / ||x_i*||_2 for the
+    unfiltered estimate X_i (the parity dump of the same walks)."""
+    dump = mc.mcmi_walk_dump(B, p, rows, 400000)
+    errs = []
+    for g, xe in zip(dump, exact):
+        est = np.zeros(m.n)
+        est[g["col"]] = g["val"]
+        errs.append(np.linalg.norm(est - xe) / np.linalg.norm(xe))
+    return float(np.mean(errs)), sum(g["steps"] for g in dump)
 
 
 def _pick_alpha(mc, B):
@@ -420,7 +468,6 @@ def run_learned(a):
     estimator error against exact rows (FP64 BiCGstab on Bhat^T), walk steps
     at equal error, and BiCGstab iterations to 1e-8 with each M."""
     import torch
-    import scipy.sparse as sp
     import paper_2409_03095_b300 as mc
     torch.cuda.set_device(0)
     mc.load()
@@ -447,35 +494,13 @@ def run_learned(a):
     alpha = _pick_alpha(mc, B)
     out["alpha"] = alpha
     N, L, delta, tau = 128, 256, 1e-3, 1e-2
-    # exact rows of Bhat^-1 for sample rows: row i = (Bhat^-T e_i)^T, by the
-    # FP64 BiCGstab of the library on Bhat^T (assembled on the host)
-    Bh = m.to_scipy().tolil()
-    dd = m.to_scipy().diagonal()
-    bn = float(np.abs(m.to_scipy()).sum(axis=1).max())
-    Bh.setdiag(dd + alpha * bn * np.where(dd < 0, -1.0, 1.0))
-    BhT = Bh.tocsr().T.tocsr()
-    BhT.sort_indices()
-    from synth import Csr
-    BT = mc.DeviceCsr.from_host(Csr(m.n, BhT.indptr.astype(np.int64), BhT.indices.astype(np.int32), BhT.data))
     rows = np.random.default_rng(1).choice(m.n, 32, replace=False)
-    exact = []
-    for r in rows:
-        e = torch.zeros(m.n, dtype=torch.float64, device="cuda")
-        e[r] = 1.0
-        x = torch.zeros_like(e)
-        it, rr = mc.mcmi_solve(BT, None, e, x, mc.SOLVE_BICGSTAB, rtol=1e-11, maxit=20000)
-        exact.append(x.cpu().numpy())
+    exact = _exact_rows(mc, m, alpha, rows)
     res = {}
     for name, prop in (("plain", None), ("learned", P)):
         p = mc.params(chains=N, max_len=L, delta=delta, seed=11, alpha=alpha, filter_tau=tau,
                       table=mc.TABLE_ALIAS, proposal=prop)
-        dump = mc.mcmi_walk_dump(B, p, rows, 200000)
-        errs = []
-        for g, xe in zip(dump, exact):
-            est = np.zeros(m.n)
-            est[g["col"]] = g["val"]
-            errs.append(np.linalg.norm(est - xe) / np.linalg.norm(xe))
-        steps_sample = sum(g["steps"] for g in dump)
+        eps_hat, steps_sample = _estimator_error(mc, B, m, p, rows, exact)
         # timed builds of the whole matrix
         for _ in range(2):
             M = mc.mcmi_build_ex(B, p)
@@ -487,7 +512,7 @@ def run_learned(a):
         bvec = torch.from_numpy(np.random.default_rng(2).standard_normal(m.n)).cuda()
         x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
         its, relres = mc.mcmi_solve(B, M, bvec, x, mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
-        res[name] = {"eps_hat": float(np.mean(errs)), "steps_per_row": steps_sample / len(rows),
+        res[name] = {"eps_hat": eps_hat, "steps_per_row": steps_sample / len(rows),
                      "build_ms": float(np.median(ts)), "steps": int(st.steps),
                      "steps_per_s": st.steps / (np.median(ts) / 1e3), "nnz_M": int(st.nnz),
                      "bicgstab_iters": int(its), "relres": float(relres)}
