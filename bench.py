@@ -512,17 +512,25 @@ def run_learned(a):
         bvec = torch.from_numpy(np.random.default_rng(2).standard_normal(m.n)).cuda()
         x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
         its, relres = mc.mcmi_solve(B, M, bvec, x, mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
+        # GMRES(50): monotone residuals, a steadier comparison than BiCGstab's
+        xg = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+        its_g, relres_g = mc.mcmi_solve(B, M, bvec, xg, mc.SOLVE_GMRES, rtol=1e-8, maxit=20000, restart=50)
         res[name] = {"eps_hat": eps_hat, "steps_per_row": steps_sample / len(rows),
                      "build_ms": float(np.median(ts)), "steps": int(st.steps),
                      "steps_per_s": st.steps / (np.median(ts) / 1e3), "nnz_M": int(st.nnz),
-                     "bicgstab_iters": int(its), "relres": float(relres)}
+                     "bicgstab_iters": int(its), "relres": float(relres),
+                     "gmres50_iters": int(its_g), "gmres50_relres": float(relres_g)}
     its0, _ = mc.mcmi_solve(B, None, bvec, torch.zeros_like(bvec), mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
+    its0_g, _ = mc.mcmi_solve(B, None, bvec, torch.zeros_like(bvec), mc.SOLVE_GMRES, rtol=1e-8, maxit=20000,
+                              restart=50)
     pl, le = res["plain"], res["learned"]
     # steps needed for the plain proposal's error (error ~ N^-1/2 at fixed walk lengths)
     eq = (le["eps_hat"] / pl["eps_hat"]) ** 2
     out.update({"plain": pl, "learned": le, "bicgstab_iters_unpreconditioned": int(its0),
+                "gmres50_iters_unpreconditioned": int(its0_g),
                 "learned_steps_at_equal_error_over_plain": eq * le["steps_per_row"] / pl["steps_per_row"],
                 "learned_iters_over_plain": le["bicgstab_iters"] / max(1, pl["bicgstab_iters"]),
+                "learned_gmres_iters_over_plain": le["gmres50_iters"] / max(1, pl["gmres50_iters"]),
                 "chains": N, "max_len": L, "delta": delta, "tau": tau})
     print(json.dumps(out), flush=True)
     return 0
