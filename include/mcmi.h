@@ -86,7 +86,7 @@ typedef struct {
     int32_t top_k;       /* keep at most top_k off-diagonals per row; 0 disables */
     int32_t precision;   /* 32: FP32 weights, Kahan FP32 sums; 64: FP64 weights and sums */
     int32_t table;       /* MCMI_TABLE_* */
-    int32_t threads;     /* threads per block of the walk kernel (0 = auto; 128 or 256) */
+    int32_t threads;     /* threads per block of the walk kernel (0 = auto; 64, 128 or 256) */
     int32_t hash_log2;   /* log2 of the on-chip accumulator slots per block (0 = auto) */
     int32_t accumulator; /* MCMI_ACC_*: row sums exact in 64-bit fixed point (default) or FP32 Kahan */
     int64_t row_begin;   /* build rows [row_begin, row_end) only; both 0 = all rows */
