@@ -62,6 +62,8 @@ def _args():
     ap.add_argument("--workload", default="stencil3d_64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64],
+                    help="walk weights and accumulator precision of the build")
     ap.add_argument("--no-quality", action="store_true", help="skip the (untimed) estimator-error check")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--learned", action="store_true",
@@ -181,10 +183,10 @@ class Clocks:
                 "reasons": reasons, "samples": len(inside)}
 
 
-def _params_for(mc, name, seed):
+def _params_for(mc, name, seed, precision=32):
     m, w = synth.workload(name)
     p = mc.params(chains=w["chains"], max_len=w["max_len"], delta=w["delta"], filter_tau=w["tau"],
-                  top_k=w["top_k"], seed=seed)
+                  top_k=w["top_k"], seed=seed, precision=precision)
     return m, w, p
 
 
@@ -267,7 +269,7 @@ def run_ours(a):
     torch.cuda.set_device(local)
     import paper_2409_03095_b300 as mc
     mc.load()
-    m, w, p = _params_for(mc, a.workload, seed=1000 + rank)
+    m, w, p = _params_for(mc, a.workload, seed=1000 + rank, precision=a.precision)
     B = mc.DeviceCsr.from_host(m)
     x = torch.ones(m.n, device="cuda", dtype=torch.float32)
     y = torch.empty(m.n, device="cuda", dtype=torch.float32)
@@ -399,7 +401,7 @@ def run_ours(a):
     rows_per_s = (last.rows * a.steps * world) / (tot_ms / 1e3)
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if a.precision == 64 else "f32", "data": "synthetic",
             "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "rows": last.rows,
                        "rows_per_s": rows_per_s, "chains": last.chains, "table": ["cumulative", "alias"][last.table],
                        "nnz_M": last.nnz, "steps_per_build": last.steps, "max_len_bound": last.max_len_bound,
