@@ -633,18 +633,23 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
                         const bool act = lane < cnt[u];
                         const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key[u].x);
                         const uint32_t leader = (uint32_t)__ffs(grp) - 1u;
-                        scratch[lane] = 0ull;
-                        __syncwarp();
-                        if (act) {
-                            if (FIX) fix_add_shared(&scratch[leader], (long long)val[u]);
-                            else comp_add(&scratch[leader], __uint_as_float((uint32_t)val[u]));
+                        // a column seen once is its own sum; groups of several
+                        // lanes add up in the warp's scratch row
+                        const bool single = (grp & (grp - 1u)) == 0u;
+                        if (!__all_sync(0xFFFFFFFFu, single || !act)) {
+                            scratch[lane] = 0ull;
+                            __syncwarp();
+                            if (act && !single) {
+                                if (FIX) fix_add_shared(&scratch[leader], (long long)val[u]);
+                                else comp_add(&scratch[leader], __uint_as_float((uint32_t)val[u]));
+                            }
+                            __syncwarp();
                         }
-                        __syncwarp();
                         const bool lead = act && lane == leader;
                         VT v = (VT)0;
                         if (lead) {
                             const VT invd = PREC == 64 ? load_invd(key[u].x) : (VT)__uint_as_float(key[u].y);
-                            v = finish(scratch[lane], invd);
+                            v = finish(single ? val[u] : scratch[lane], invd);
                             const VT av = v < (VT)0 ? -v : v;
                             lmax = av > lmax ? av : lmax;
                         }
