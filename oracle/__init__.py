@@ -75,6 +75,8 @@ def _L():
         lib.orc_filter_row.argtypes = [i64, P, P, i64, f64, i64, P, P]
         lib.orc_filter_row.restype = i64
         lib.orc_spmv.argtypes = [i64, P, P, P, P, P]
+        lib.orc_reduce_mask.argtypes = [i64, P, P, P, f64, i32, P]
+        lib.orc_reduce_mask.restype = i64
         _lib = lib
     return _lib
 
@@ -347,3 +349,25 @@ def train_edges(m, alpha=0.0):
     row = np.zeros(max(E, 1), dtype=np.int64)
     _L().orc_train_edges(m.n, _p(rp), _p(col), _p(val), _p(d), _p(s), _p(feat), _p(p), _p(tgt), _p(row))
     return feat[:E], p[:E], tgt[:E], row[:E]
+
+
+REDUCE_ENTRIES, REDUCE_RANGE = 0, 1
+
+
+def reduce(m, fraction, mode=REDUCE_ENTRIES):
+    """Matrix reduction (Algorithm 1 step 2; Sec. III "Matrix Reduction"):
+    drop a share of the smallest off-diagonal entries before the split.
+    mode 0: floor(fraction * nnz_off) smallest |b_ij|, ties by CSR position;
+    mode 1: |b_ij| < lo + fraction (hi - lo) over the off-diagonal range.
+    Returns (reduced Csr, keep mask over the stored entries, dropped count)."""
+    from synth import Csr
+    rp, col, val = _csr(m)
+    keep = np.ones(max(len(col), 1), dtype=np.uint8)
+    d = _L().orc_reduce_mask(m.n, _p(rp), _p(col), _p(val), float(fraction), int(mode), _p(keep))
+    if d < 0:
+        raise ValueError("bad reduction arguments")
+    keep = keep[:len(col)].astype(bool)
+    counts = np.array([keep[rp[i]:rp[i + 1]].sum() for i in range(m.n)], dtype=np.int64)
+    nrp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    return Csr(m.n, nrp, col[keep].astype(np.int32), val[keep].astype(np.float64)), keep, int(d)
+

@@ -780,3 +780,77 @@ void orc_spmv(int64_t n, const int64_t *rp, const int32_t *col, const double *va
         y[i] = acc;
     }
 }
+
+/* ------------------------------------------------------------------------
+ * Matrix reduction (Algorithm 1, step 2; Sec. III, "Matrix Reduction"):
+ * before the split, drop a set share of the smallest (in magnitude) entries
+ * of B.  Only off-diagonal entries are dropped (the split needs b_ii).
+ *   mode 0, share of the entries: the k = floor(fraction * nnz_off)
+ *     off-diagonal entries smallest in |b_ij|, ties broken by position in
+ *     CSR order (the earlier entry is dropped first);
+ *   mode 1, share of the value range (the experiments' "% of the value
+ *     range of the entries removed"): the off-diagonal entries with
+ *     |b_ij| < lo + fraction (hi - lo), lo and hi the smallest and largest
+ *     off-diagonal |b_ij|, evaluated in FP64 in that order.
+ * keep[k] is set to 1 for kept stored entries and 0 for dropped ones; the
+ * return value is the number dropped (-1 on a bad argument).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double a;
+    int64_t k;
+} orc_absidx;
+
+static int cmp_absidx(const void *x, const void *y)
+{
+    const orc_absidx *p = (const orc_absidx *)x, *q = (const orc_absidx *)y;
+    if (p->a < q->a) return -1;
+    if (p->a > q->a) return 1;
+    return (p->k > q->k) - (p->k < q->k);
+}
+
+int64_t orc_reduce_mask(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double fraction,
+                        int mode, uint8_t *keep)
+{
+    if (!(fraction >= 0.0 && fraction <= 1.0) || (mode != 0 && mode != 1)) return -1;
+    const int64_t nnz = rp[n];
+    int64_t noff = 0;
+    for (int64_t k = 0; k < nnz; ++k) keep[k] = 1;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (col[k] != i) ++noff;
+    if (noff == 0) return 0;
+    int64_t dropped = 0;
+    if (mode == 1) {
+        double lo = INFINITY, hi = 0.0;
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+                if (col[k] != i) {
+                    const double a = fabs(val[k]);
+                    if (a < lo) lo = a;
+                    if (a > hi) hi = a;
+                }
+        const double thr = lo + fraction * (hi - lo);
+        for (int64_t i = 0; i < n; ++i)
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+                if (col[k] != i && fabs(val[k]) < thr) {
+                    keep[k] = 0;
+                    ++dropped;
+                }
+        return dropped;
+    }
+    const int64_t kdrop = (int64_t)floor(fraction * (double)noff);
+    orc_absidx *e = (orc_absidx *)malloc((size_t)noff * sizeof(orc_absidx));
+    if (!e) return -1;
+    int64_t m = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (col[k] != i) {
+                e[m].a = fabs(val[k]);
+                e[m].k = k;
+                ++m;
+            }
+    qsort(e, (size_t)noff, sizeof(orc_absidx), cmp_absidx);
+    for (int64_t t = 0; t < kdrop; ++t) keep[e[t].k] = 0;
+    free(e);
+    return kdrop;
+}

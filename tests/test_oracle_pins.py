@@ -462,3 +462,75 @@ def test_spmv_matches_scipy(orc):
     m = synth.random_dd(300, 9, seed=2)
     x = np.random.default_rng(0).standard_normal(m.n)
     assert np.allclose(orc.spmv(m.row_ptr, m.col, m.val, x), m.to_scipy() @ x, rtol=1e-13)
+
+
+# ---------------------------------------------------------------- matrix reduction (Algorithm 1, step 2)
+
+
+def _offdiag(m):
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    return m.col != rows
+
+
+@pytest.mark.parametrize("fraction", [0.0, 0.1, 0.37, 0.5, 0.93, 1.0])
+def test_reduce_entries_drops_the_smallest_ties_by_position(fraction):
+    import oracle
+    m = synth.random_dd(300, 7, seed=11, diag_sign="mixed")
+    off = _offdiag(m)
+    # many equal magnitudes, both signs: ties at the cut
+    m.val[off] = np.round(m.val[off], 1)
+    r, keep, d = oracle.reduce(m, fraction, oracle.REDUCE_ENTRIES)
+    noff = int(off.sum())
+    a = np.abs(m.val)
+    assert d == int(np.floor(fraction * noff)) and int((~keep).sum()) == d
+    assert keep[~off].all()                                    # the diagonal stays
+    if 0 < d < noff:
+        assert a[off & ~keep].max() <= a[off & keep].min()     # every dropped entry <= every kept one
+        b = a[off & ~keep].max()
+        tie = np.flatnonzero(off & (a == b))
+        assert np.all(np.diff(keep[tie].astype(int)) >= 0)     # equal magnitudes: earlier entries dropped first
+    # the same set from numpy's lexsort on (|b|, position)
+    pos = np.flatnonzero(off)
+    first = pos[np.lexsort((pos, a[off]))][:d]
+    assert set(first.tolist()) == set(np.flatnonzero(~keep).tolist())
+    # the reduced CSR keeps the remaining entries in order
+    assert np.array_equal(r.col, m.col[keep]) and np.array_equal(r.val, m.val[keep])
+    assert np.array_equal(np.diff(r.row_ptr), [keep[m.row_ptr[i]:m.row_ptr[i + 1]].sum() for i in range(m.n)])
+
+
+def test_reduce_range_closed_form():
+    """Off-diagonal magnitudes 1..100 (alternating signs): the cut at
+    lo + f (hi - lo) = 1 + 99 f drops exactly the values below it."""
+    import oracle
+    n = 101
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        rows.append(i); cols.append(i); vals.append(1000.0)
+        if i < 100:
+            rows.append(i); cols.append((i + 7) % n); vals.append((i + 1.0) * (-1) ** i)
+    m = synth._from_coo(n, np.array(rows), np.array(cols), np.array(vals))
+    for f, expect in [(0.0, 0), (0.5, 50), (0.25, 25), (1.0, 99), (0.004, 1), (0.011, 2)]:
+        r, keep, d = oracle.reduce(m, f, oracle.REDUCE_RANGE)
+        assert d == expect, (f, d)
+        kept = np.abs(r.val[_offdiag(r)])
+        assert kept.min(initial=np.inf) >= 1 + 99 * f - 1e-12
+    # the 0.5 cut: values 1..50 go, 51..100 stay
+    r, keep, d = oracle.reduce(m, 0.5, oracle.REDUCE_RANGE)
+    assert sorted(np.abs(r.val[_offdiag(r)]).tolist()) == [float(v) for v in range(51, 101)]
+
+
+def test_reduce_keeps_the_diagonal_and_handles_diagonal_matrices():
+    import oracle
+
+    def csr(n, r, c, v):
+        return synth._from_coo(n, np.array(r), np.array(c), np.array(v, dtype=np.float64))
+    m = csr(4, [0, 1, 2, 3, 0], [0, 1, 2, 3, 3], [2.0, 3.0, -4.0, 5.0, 0.5])
+    r, keep, d = oracle.reduce(m, 1.0, oracle.REDUCE_ENTRIES)      # every off-diagonal entry goes
+    assert d == 1 and r.nnz == 4 and np.array_equal(r.col, [0, 1, 2, 3])
+    r, keep, d = oracle.reduce(m, 1.0, oracle.REDUCE_RANGE)        # the largest off-diagonal |b| stays
+    assert d == 0 and r.nnz == 5
+    d0 = csr(3, [0, 1, 2], [0, 1, 2], [1.0, 2.0, 3.0])
+    r, keep, d = oracle.reduce(d0, 0.5, oracle.REDUCE_ENTRIES)
+    assert d == 0 and r.nnz == 3
+    with pytest.raises(ValueError):
+        oracle.reduce(d0, 1.5, oracle.REDUCE_ENTRIES)
