@@ -269,6 +269,40 @@ mcmi_status mcmi_solve(const mcmi_csr *B, mcmi_matrix M, const double *b, double
 /* Release a handle (stream-ordered on the stream it was built on).  NULL ok. */
 void mcmi_free(mcmi_matrix M);
 
+/* ---------------------------------------------------------------------
+ * Matrix reduction (Algorithm 1, step 2; Sec. III, "Matrix Reduction"):
+ * before the split, drop a set share of the off-diagonal entries of B that
+ * are smallest in magnitude (diagonal entries are always kept; the others
+ * keep their order).  mode:
+ *   MCMI_REDUCE_ENTRIES: the floor(fraction * nnz_off) smallest |b_ij|,
+ *     ties broken by position in CSR order (the earlier entry goes first);
+ *   MCMI_REDUCE_RANGE: every |b_ij| < lo + fraction (hi - lo), lo and hi
+ *     the smallest and largest off-diagonal |b_ij|, in FP64 in that order
+ *     (the "% of the value range of the entries removed" of Sec. V).
+ * B: device CSR (read only; columns need not be sorted); fraction in
+ * [0, 1].  *R receives a library-owned device CSR (FP64 values) of the same
+ * size n, viewed with mcmi_reduced_csr and released with
+ * mcmi_reduced_free; *dropped (host, optional) the number of entries
+ * removed.  Synchronises `stream`.  Errors: MCMI_ERR_ARG (bad pointers,
+ * fraction or mode), MCMI_ERR_OOM, MCMI_ERR_CUDA; on error *R = NULL.     */
+#define MCMI_REDUCE_ENTRIES 0
+#define MCMI_REDUCE_RANGE 1
+typedef struct mcmi_reduced_s *mcmi_reduced;
+mcmi_status mcmi_reduce(const mcmi_csr *B, double fraction, int32_t mode, void *stream, mcmi_reduced *R,
+                        int64_t *dropped);
+
+/* View of a reduced matrix (device pointers owned by R, valid until
+ * mcmi_reduced_free): pass *view to the builds as their B.               */
+mcmi_status mcmi_reduced_csr(mcmi_reduced R, mcmi_csr *view);
+
+/* Copy a reduced matrix into caller-owned device buffers: row_ptr
+ * int64[n+1], col int32[nnz], val double[nnz] (sizes from
+ * mcmi_reduced_csr).  Asynchronous on `stream`.                          */
+mcmi_status mcmi_reduced_copy(mcmi_reduced R, int64_t *row_ptr, int32_t *col, double *val, void *stream);
+
+/* Release a reduced matrix (stream-ordered on its stream).  NULL ok.      */
+void mcmi_reduced_free(mcmi_reduced R);
+
 /* Description of the last error on the calling host thread.               */
 const char *mcmi_last_error(void);
 

@@ -115,6 +115,14 @@ def load():
     for f in ("mcmi_proposal_create", "mcmi_proposal_get", "mcmi_row_moments", "mcmi_proposal_loss_grad",
               "mcmi_proposal_train"):
         getattr(lib, f).restype = C.c_int
+    lib.mcmi_reduce.argtypes = [C.POINTER(mcmi_csr), f64, i32, P, C.POINTER(P), C.POINTER(i64)]
+    lib.mcmi_reduce.restype = C.c_int
+    lib.mcmi_reduced_csr.argtypes = [P, C.POINTER(mcmi_csr)]
+    lib.mcmi_reduced_csr.restype = C.c_int
+    lib.mcmi_reduced_copy.argtypes = [P, P, P, P, P]
+    lib.mcmi_reduced_copy.restype = C.c_int
+    lib.mcmi_reduced_free.argtypes = [P]
+    lib.mcmi_reduced_free.restype = None
     for f in ("mcmi_build", "mcmi_build_ex", "mcmi_matrix_csr", "mcmi_matrix_copy", "mcmi_apply",
               "mcmi_walk_dump", "mcmi_debug_tables", "mcmi_exclusive_scan_noalloc"):
         getattr(lib, f).restype = C.c_int
@@ -200,6 +208,53 @@ class Matrix:
         val = torch.empty(max(nnz, 1), dtype=torch.float32, device="cuda")
         _check(load().mcmi_matrix_copy(self.h, _ptr(rp), _ptr(col), _ptr(val), _stream(stream)))
         return rp, col[:nnz], val[:nnz]
+
+
+REDUCE_ENTRIES, REDUCE_RANGE = 0, 1
+
+
+class Reduced:
+    """Library-owned reduced input matrix (FP64 CSR, device); ``.c`` is its
+    mcmi_csr view, so it can be passed to the builds as B."""
+
+    def __init__(self, handle, dropped):
+        self.h = handle
+        self.dropped = dropped
+        self.c = mcmi_csr()
+        _check(load().mcmi_reduced_csr(self.h, C.byref(self.c)))
+        self.n = int(self.c.n)
+
+    @property
+    def nnz(self):
+        return int(self.c.nnz)
+
+    def to_torch(self, stream=None):
+        """Copy as (row_ptr int64, col int32, val float64) CUDA tensors."""
+        import torch
+        rp = torch.empty(self.n + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(self.nnz, 1), dtype=torch.int32, device="cuda")
+        val = torch.empty(max(self.nnz, 1), dtype=torch.float64, device="cuda")
+        _check(load().mcmi_reduced_copy(self.h, _ptr(rp), _ptr(col), _ptr(val), _stream(stream)))
+        return rp, col[:self.nnz], val[:self.nnz]
+
+    def close(self):
+        if self.h:
+            load().mcmi_reduced_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mcmi_reduce(B: DeviceCsr, fraction, mode=REDUCE_ENTRIES, stream=None) -> Reduced:
+    """Matrix reduction of Algorithm 1 step 2 (drop the smallest off-diagonal
+    entries: a share of the entries, or of the value range)."""
+    h, d = C.c_void_p(), C.c_int64()
+    _check(load().mcmi_reduce(C.byref(B.c), float(fraction), int(mode), _stream(stream), C.byref(h), C.byref(d)))
+    return Reduced(h, d.value)
 
 
 def mcmi_build(B: DeviceCsr, eps, delta, chains, filter_tau, seed, stream=None) -> Matrix:

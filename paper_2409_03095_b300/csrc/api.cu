@@ -23,6 +23,15 @@ struct mcmi_matrix_s {
     int device = 0;
 };
 
+// A reduced input matrix (FP64 CSR, device, library-owned).
+struct mcmi_reduced_s {
+    int64_t n = 0, nnz = 0;
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr;
+    double *val = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
 namespace {
 
 thread_local std::string g_err;
@@ -1260,6 +1269,139 @@ mcmi_status mcmi_proposal_train(const mcmi_csr *Bs, int32_t count, const mcmi_tr
     if (e == cudaSuccess) e = cudaMemcpy(P->h_params, P->d_params, kMlpParams * 4, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "training");
     return MCMI_OK;
+}
+
+mcmi_status mcmi_reduce(const mcmi_csr *B, double fraction, int32_t mode, void *stream, mcmi_reduced *R_out,
+                        int64_t *dropped)
+{
+    if (!R_out) return fail(MCMI_ERR_ARG, "R is NULL");
+    *R_out = nullptr;
+    mcmi_status r = check_csr(B);
+    if (r != MCMI_OK) return r;
+    if (!(fraction >= 0.0 && fraction <= 1.0)) return fail(MCMI_ERR_ARG, "fraction must be in [0, 1]");
+    if (mode != MCMI_REDUCE_ENTRIES && mode != MCMI_REDUCE_RANGE) return fail(MCMI_ERR_ARG, "unknown reduction mode");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    const int64_t n = B->n;
+    unsigned long long *stats = S.get<unsigned long long>(3);
+    unsigned int *hist = S.get<unsigned int>(256);
+    int32_t *kc = S.get<int32_t>(n);
+    int64_t *rp2 = S.get<int64_t>(n + 1);
+    int64_t *tmp = S.get<int64_t>(scan_tmp_elems(n));
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (reduction)");
+    // off-diagonal count and |b| range
+    unsigned long long hs[3] = {0ull, ~0ull, 0ull};
+    cudaMemcpyAsync(stats, hs, sizeof(hs), cudaMemcpyHostToDevice, s);
+    cudaError_t e = launch_offstats(n, B->row_ptr, B->col, B->val, stats, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs, stats, sizeof(hs), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reduction statistics");
+    const int64_t noff = (int64_t)hs[0];
+    const int rmode = mode;
+    double thr = 0.0;
+    unsigned long long T = 0ull;
+    long long need = 0;
+    int64_t *eq_off = nullptr;
+    if (mode == MCMI_REDUCE_RANGE) {
+        double lo = 0.0, hi = 0.0;
+        const unsigned long long lob = hs[1], hib = hs[2];
+        memcpy(&lo, &lob, 8);
+        memcpy(&hi, &hib, 8);
+        thr = noff > 0 ? lo + fraction * (hi - lo) : 0.0;   // FP64, this order (no contraction)
+    } else {
+        const int64_t kdrop = (int64_t)std::floor(fraction * (double)noff);
+        if (kdrop > 0) {   // (kdrop == 0: T = 0 and need = 0 drop nothing)
+            // radix select of the kdrop-th smallest key (8 bits per pass, from the top)
+            unsigned long long prefix = 0ull, mask = 0ull;
+            long long rank = kdrop;   // 1-based rank inside the current prefix group
+            unsigned int h[256];
+            for (int shift = 56; shift >= 0; shift -= 8) {
+                cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned int), s);
+                e = launch_abs_hist(n, B->row_ptr, B->col, B->val, prefix, mask, shift, hist, s);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(h, hist, sizeof(h), cudaMemcpyDeviceToHost, s);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                if (e != cudaSuccess) return cuda_fail(e, "reduction select");
+                long long cum = 0;
+                int digit = 255;
+                for (int d = 0; d < 256; ++d) {
+                    if (cum + (long long)h[d] >= rank) {
+                        digit = d;
+                        break;
+                    }
+                    cum += h[d];
+                }
+                rank -= cum;
+                prefix |= (unsigned long long)digit << shift;
+                mask |= 255ull << shift;
+            }
+            T = prefix;     // key of the kdrop-th smallest entry
+            need = rank;    // entries equal to T that are dropped (the first ones in CSR order)
+            int32_t *eqc = S.get<int32_t>(n);
+            eq_off = S.get<int64_t>(n + 1);
+            if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (reduction ranks)");
+            e = launch_eq_count(n, B->row_ptr, B->col, B->val, T, eqc, s);
+            if (e == cudaSuccess) e = scan_counts(eqc, n, eq_off, tmp, s);
+            if (e != cudaSuccess) return cuda_fail(e, "reduction ranks");
+        }
+    }
+    e = launch_keep(n, B->row_ptr, B->col, B->val, rmode, thr, T, need, eq_off, kc, nullptr, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = scan_counts(kc, n, rp2, tmp, s);
+    int64_t nnz2 = 0;
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(&nnz2, rp2 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reduction counts");
+    int32_t *col2 = S.get<int32_t>(nnz2);
+    double *val2 = S.get<double>(nnz2);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (reduced matrix)");
+    e = launch_keep(n, B->row_ptr, B->col, B->val, rmode, thr, T, need, eq_off, nullptr, rp2, col2, val2, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "reduction compaction");
+    mcmi_reduced R = new mcmi_reduced_s();
+    R->n = n;
+    R->nnz = nnz2;
+    R->rp = rp2;
+    R->col = col2;
+    R->val = val2;
+    R->stream = s;
+    S.keep(rp2);
+    S.keep(col2);
+    S.keep(val2);
+    if (n == 0) cudaMemsetAsync(rp2, 0, sizeof(int64_t), s);
+    if (dropped) *dropped = B->nnz - nnz2;
+    *R_out = R;
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_reduced_csr(mcmi_reduced R, mcmi_csr *view)
+{
+    if (!R || !view) return fail(MCMI_ERR_ARG, "NULL argument");
+    view->n = R->n;
+    view->nnz = R->nnz;
+    view->row_ptr = R->rp;
+    view->col = R->col;
+    view->val = R->val;
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_reduced_copy(mcmi_reduced R, int64_t *row_ptr, int32_t *col, double *val, void *stream)
+{
+    if (!R || !row_ptr || ((!col || !val) && R->nnz > 0)) return fail(MCMI_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(row_ptr, R->rp, (R->n + 1) * sizeof(int64_t), cudaMemcpyDefault, s);
+    if (e == cudaSuccess && R->nnz > 0) e = cudaMemcpyAsync(col, R->col, R->nnz * sizeof(int32_t), cudaMemcpyDefault, s);
+    if (e == cudaSuccess && R->nnz > 0) e = cudaMemcpyAsync(val, R->val, R->nnz * sizeof(double), cudaMemcpyDefault, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the reduced matrix");
+    return MCMI_OK;
+}
+
+void mcmi_reduced_free(mcmi_reduced R)
+{
+    if (!R) return;
+    if (R->rp) cudaFreeAsync(R->rp, R->stream);
+    if (R->col) cudaFreeAsync(R->col, R->stream);
+    if (R->val) cudaFreeAsync(R->val, R->stream);
+    delete R;
 }
 
 }  // extern "C"

@@ -72,4 +72,16 @@ cudaError_t launch_split(const BatchOut *out, int count, const int64_t *row_base
 cudaError_t launch_spmv(int64_t rows, const int64_t *rp, const int32_t *col, const float *val, const float *x,
                         float *y, cudaStream_t s);
 
+// matrix reduction
+cudaError_t launch_offstats(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                            unsigned long long *out, cudaStream_t s);
+cudaError_t launch_abs_hist(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                            unsigned long long prefix, unsigned long long mask, int shift, unsigned int *hist,
+                            cudaStream_t s);
+cudaError_t launch_eq_count(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                            unsigned long long T, int32_t *eqc, cudaStream_t s);
+cudaError_t launch_keep(int64_t n, const int64_t *rp, const int32_t *col, const double *val, int mode, double thr,
+                        unsigned long long T, long long need, const int64_t *eq_off, int32_t *kc,
+                        const int64_t *out_rp, int32_t *out_col, double *out_val, cudaStream_t s);
+
 }  // namespace mcmi
