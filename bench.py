@@ -45,6 +45,8 @@ WORKLOADS = {
     "powerlaw_1m": "random sparse nonsymmetric n=1048576, power-law rows (alpha 2.5, 4..256), N(0,1) values, "
                    "dominance 0.85; 128 chains/row, cutoff 1e-3, max length 256, tau 5e-3",
     "powerlaw_128k": "power-law random as powerlaw_1m with n=131072: profiling-size case",
+    "aniso2d_1024": "2D 9-point rotated anisotropy (ratio 1e-3, angle per 32x32 block), 1024^2 (n=1048576), "
+                    "alpha 0.25; 128 chains/row, cutoff 1e-3, max length 256, tau 1e-2",
     "batch_512": "512 matrices, n log-uniform in [1e3, 2e5], cycling 2D 5-point / 3D 7-point / power-law random, "
                  "dominance U[0.8, 0.95]; 128 chains/row, cutoff 1e-3, max length 128, top-16; one batched build "
                  "(graph-captured persistent walk, autotuned shape)",
@@ -69,6 +71,8 @@ def _args():
     ap.add_argument("--learned", action="store_true",
                     help="learned vs |c| proposal on the anisotropic 1024^2 problem (one JSON line)")
     ap.add_argument("--train-count", type=int, default=2000)
+    ap.add_argument("--reduce", action="store_true",
+                    help="matrix reduction sweep judged by BiCGstab/GMRES on --workload (one JSON line)")
     ap.add_argument("--train-steps", type=int, default=100)
     return ap.parse_args()
 
@@ -142,7 +146,8 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         self.t0 = self.t1 = None
         try:
-            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits",
                                        "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -186,7 +191,7 @@ class Clocks:
 def _params_for(mc, name, seed, precision=32):
     m, w = synth.workload(name)
     p = mc.params(chains=w["chains"], max_len=w["max_len"], delta=w["delta"], filter_tau=w["tau"],
-                  top_k=w["top_k"], seed=seed, precision=precision)
+                  top_k=w["top_k"], seed=seed, precision=precision, alpha=w.get("alpha", 0.0))
     return m, w, p
 
 
@@ -200,7 +205,7 @@ def _cpu_baseline(m, w, seconds, table):
         rows = np.linspace(0, m.n - 1, nr).astype(np.int64)
         t0 = time.perf_counter()
         oracle.build(m, rows=rows, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
-                     tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+                     alpha=w.get("alpha", 0.0), tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
         return time.perf_counter() - t0
     # per-row cost from two probe sizes (each call also builds the tables of
     # the whole matrix, a fixed cost)
@@ -211,7 +216,8 @@ def _cpu_baseline(m, w, seconds, table):
     rows = np.linspace(0, m.n - 1, nrows).astype(np.int64)
     t0 = time.perf_counter()
     _, _, _, steps = oracle.build(m, rows=rows, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
-                                  tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+                                  alpha=w.get("alpha", 0.0), tau=w["tau"], top_k=w["top_k"], table=table,
+                                  threads=cores)
     dt = time.perf_counter() - t0
     return {"value": float(steps.sum()) / dt, "unit": "steps/s", "cores": cores, "kind": "oracle",
             "sample": f"{nrows} of {m.n} rows (evenly spaced), {int(steps.sum())} transitions in {dt:.1f} s",
@@ -232,7 +238,7 @@ def run_reference(a):
         rr = np.linspace(0, m.n - 1, nr).astype(np.int64)
         t0 = time.perf_counter()
         oracle.build(m, rows=rr, chains=w["chains"], max_len=w["max_len"], delta=w["delta"], seed=1,
-                     tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
+                     alpha=w.get("alpha", 0.0), tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
         return time.perf_counter() - t0
     n1, n2 = min(m.n, 128), min(m.n, 1024)
     t1, t2 = run(n1), run(n2)
@@ -243,6 +249,7 @@ def run_reference(a):
     for it in range(a.warmup + a.steps):
         t0 = time.perf_counter()
         _, _, _, steps = oracle.build(m, rows=rows, chains=w["chains"], max_len=w["max_len"], delta=w["delta"],
+                                      alpha=w.get("alpha", 0.0),
                                       seed=1 + it, tau=w["tau"], top_k=w["top_k"], table=table, threads=cores)
         dt = time.perf_counter() - t0
         if it >= a.warmup:
@@ -613,12 +620,65 @@ def run_batched(a):
     return 0
 
 
+def run_reduce(a):
+    """Matrix reduction (Algorithm 1 step 2) judged by the Krylov solver:
+    for each dropped share of the value range (and of the entries), the
+    reduction and build times on the reduced matrix, walk steps, nnz(M), and
+    BiCGstab / GMRES(50) iterations and time on the ORIGINAL system with the
+    preconditioner built from the reduced one (one JSON line)."""
+    import torch
+    import paper_2409_03095_b300 as mc
+    torch.cuda.set_device(0)
+    mc.load()
+    m, w, p = _params_for(mc, a.workload, seed=1000)
+    B = mc.DeviceCsr.from_host(m)
+    bvec = torch.from_numpy(np.random.default_rng(2).standard_normal(m.n)).cuda()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    rows = []
+    its0, ms0 = timed(lambda: mc.mcmi_solve(B, None, bvec, torch.zeros_like(bvec), mc.SOLVE_BICGSTAB, rtol=1e-8,
+                                              maxit=20000))
+    for mode, name in ((mc.REDUCE_RANGE, "range"), (mc.REDUCE_ENTRIES, "entries")):
+        for f in (0.0, 0.02, 0.04, 0.06, 0.075, 0.1, 0.2):
+            R, red_ms = timed(lambda: mc.mcmi_reduce(B, f, mode))
+            for _ in range(2):
+                mc.mcmi_build_ex(R, p)
+            M, build_ms = timed(lambda: mc.mcmi_build_ex(R, p))
+            (it_b, rr_b), solve_b = timed(lambda: mc.mcmi_solve(B, M, bvec, torch.zeros_like(bvec), mc.SOLVE_BICGSTAB,
+                                                                rtol=1e-8, maxit=20000))
+            (it_g, rr_g), solve_g = timed(lambda: mc.mcmi_solve(B, M, bvec, torch.zeros_like(bvec), mc.SOLVE_GMRES,
+                                                                rtol=1e-8, maxit=20000, restart=50))
+            rows.append({"mode": name, "fraction": f, "nnz_B": R.nnz, "dropped": R.dropped,
+                         "reduce_ms": red_ms, "build_ms": build_ms, "steps": int(M.stats.steps),
+                         "nnz_M": int(M.stats.nnz),
+                         "bicgstab_iters": it_b, "bicgstab_ms": solve_b, "bicgstab_relres": rr_b,
+                         "gmres50_iters": it_g, "gmres50_ms": solve_g, "gmres50_relres": rr_g,
+                         "total_bicgstab_ms": red_ms + build_ms + solve_b})
+            R.close()
+    base = rows[0]
+    out = {"metric": METRIC, "unit": "steps/s", "mode": "matrix reduction (Algorithm 1 step 2) judged by Krylov",
+           "value": base["steps"] / (base["build_ms"] / 1e3), "workload": f"{a.workload}: {WORKLOADS[a.workload]}",
+           "data": "synthetic", "bicgstab_unpreconditioned": {"iters": its0[0], "ms": ms0}, "sweep": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
     if a.learned:
         return run_learned(a)
+    if a.reduce:
+        return run_reduce(a)
     if a.workload == "batch_512":
         return run_batched(a)
     return run_ours(a)

@@ -308,6 +308,8 @@ WORKLOADS = {
                         delta=1e-3, max_len=256, tau=5e-3, top_k=0),
     "powerlaw_128k": dict(gen=lambda: powerlaw_random(1 << 17, seed=1003), chains=128,
                           delta=1e-3, max_len=256, tau=5e-3, top_k=0),
+    "aniso2d_1024": dict(gen=lambda: aniso2d_9pt(1024, seed=1005), chains=128,
+                         delta=1e-3, max_len=256, tau=1e-2, top_k=0, alpha=0.25),
 }
 
 
