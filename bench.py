@@ -45,6 +45,8 @@ WORKLOADS = {
     "powerlaw_1m": "random sparse nonsymmetric n=1048576, power-law rows (alpha 2.5, 4..256), N(0,1) values, "
                    "dominance 0.85; 128 chains/row, cutoff 1e-3, max length 256, tau 5e-3",
     "powerlaw_128k": "power-law random as powerlaw_1m with n=131072: profiling-size case",
+    "general_128k": "random sparse, n=131072, 9 off-diagonals N(0,1) per row, |b_ii| = abs-sum/1.4 with random "
+                    "sign (not diagonally dominant), alpha 0.5; 128 chains/row, cutoff 1e-3, max length 256, tau 5e-3",
     "aniso2d_1024": "2D 9-point rotated anisotropy (ratio 1e-3, angle per 32x32 block), 1024^2 (n=1048576), "
                     "alpha 0.25; 128 chains/row, cutoff 1e-3, max length 256, tau 1e-2",
     "batch_512": "512 matrices, n log-uniform in [1e3, 2e5], cycling 2D 5-point / 3D 7-point / power-law random, "
@@ -71,6 +73,8 @@ def _args():
     ap.add_argument("--learned", action="store_true",
                     help="learned vs |c| proposal on the anisotropic 1024^2 problem (one JSON line)")
     ap.add_argument("--train-count", type=int, default=2000)
+    ap.add_argument("--alpha-sweep", action="store_true",
+                    help="Eq. 1 augmentation sweep judged by BiCGstab/GMRES on --workload (one JSON line)")
     ap.add_argument("--reduce", action="store_true",
                     help="matrix reduction sweep judged by BiCGstab/GMRES on --workload (one JSON line)")
     ap.add_argument("--train-steps", type=int, default=100)
@@ -671,6 +675,44 @@ def run_reduce(a):
     return 0
 
 
+def run_alpha_sweep(a):
+    """Eq. 1 augmentation on a general matrix: for each alpha, walk steps,
+    build time and nnz(M), and BiCGstab / GMRES(50) iterations on the
+    ORIGINAL system B with M built from Bhat (one JSON line).  The paper
+    reports about 20% longer runs at alpha = 4 than at alpha = 5."""
+    import torch
+    import paper_2409_03095_b300 as mc
+    torch.cuda.set_device(0)
+    mc.load()
+    m, w, p = _params_for(mc, a.workload, seed=1000)
+    B = mc.DeviceCsr.from_host(m)
+    bvec = torch.from_numpy(np.random.default_rng(2).standard_normal(m.n)).cuda()
+    its0, _ = mc.mcmi_solve(B, None, bvec, torch.zeros_like(bvec), mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
+    rows = []
+    for alpha in (0.3, 0.5, 1.0, 2.0, 4.0, 5.0):
+        p.alpha = alpha
+        for _ in range(2):
+            mc.mcmi_build_ex(B, p)
+        ts = []
+        for _ in range(3):
+            M = mc.mcmi_build_ex(B, p)
+            ts.append(M.stats.ms_prepare + M.stats.ms_walk + M.stats.ms_assemble)
+        it_b, rr_b = mc.mcmi_solve(B, M, bvec, torch.zeros_like(bvec), mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
+        it_g, rr_g = mc.mcmi_solve(B, M, bvec, torch.zeros_like(bvec), mc.SOLVE_GMRES, rtol=1e-8, maxit=20000,
+                                   restart=50)
+        rows.append({"alpha": alpha, "max_s": M.stats.max_s, "steps": int(M.stats.steps),
+                     "build_ms": float(np.median(ts)), "nnz_M": int(M.stats.nnz), "bicgstab_iters": it_b,
+                     "bicgstab_relres": rr_b, "gmres50_iters": it_g, "gmres50_relres": rr_g})
+    s4 = next(r for r in rows if r["alpha"] == 4.0)
+    s5 = next(r for r in rows if r["alpha"] == 5.0)
+    out = {"metric": METRIC, "unit": "steps/s", "mode": "alpha sweep (Eq. 1 augmentation) judged by Krylov",
+           "workload": f"{a.workload}: {WORKLOADS[a.workload]}", "data": "synthetic",
+           "bicgstab_unpreconditioned": its0, "alpha4_over_alpha5_steps": s4["steps"] / s5["steps"],
+           "alpha4_over_alpha5_build_ms": s4["build_ms"] / s5["build_ms"], "sweep": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -679,6 +721,8 @@ def main():
         return run_learned(a)
     if a.reduce:
         return run_reduce(a)
+    if a.alpha_sweep:
+        return run_alpha_sweep(a)
     if a.workload == "batch_512":
         return run_batched(a)
     return run_ours(a)

@@ -233,6 +233,25 @@ def random_dd(n, deg, seed, dominance=0.8, signs="mixed", diag_sign="positive",
     return out
 
 
+def equal_rows(n, deg, seed, diag=0.2):
+    """General (not diagonally dominant) random matrix whose rows all have the
+    same norms: ``deg`` off-diagonals of magnitude 1/deg with random signs
+    (columns uniform without replacement) and a diagonal of magnitude
+    ``diag`` with a random sign.  With the Eq. 1 augmentation every row then
+    has the same s_i = 1 / (diag + alpha (1 + diag))."""
+    rng = np.random.default_rng(seed)
+    d = min(deg, n - 1)
+    row_of = np.repeat(np.arange(n, dtype=np.int64), d)
+    cols = _unique_cols(rng, n, row_of, n * d)
+    order = np.lexsort((cols, row_of))
+    cols = cols[order]
+    v = np.where(rng.random(cols.size) < 0.5, -1.0, 1.0) / d
+    m = _from_coo(n, row_of, cols, v)
+    out = _add_diagonal(m, diag * np.where(rng.random(n) < 0.5, -1.0, 1.0))
+    out.meta = dict(family="equal_rows", n=n, deg=deg, seed=seed)
+    return out
+
+
 def aniso2d_9pt(nx=1024, eps=1e-3, block=32, seed=1005):
     """2D anisotropic diffusion, 9-point finite differences of div(K grad u).
 
@@ -308,6 +327,8 @@ WORKLOADS = {
                         delta=1e-3, max_len=256, tau=5e-3, top_k=0),
     "powerlaw_128k": dict(gen=lambda: powerlaw_random(1 << 17, seed=1003), chains=128,
                           delta=1e-3, max_len=256, tau=5e-3, top_k=0),
+    "general_128k": dict(gen=lambda: random_dd(1 << 17, 9, seed=1006, dominance=1.4, diag_sign="mixed"),
+                         chains=128, delta=1e-3, max_len=256, tau=5e-3, top_k=0, alpha=0.5),
     "aniso2d_1024": dict(gen=lambda: aniso2d_9pt(1024, seed=1005), chains=128,
                          delta=1e-3, max_len=256, tau=1e-2, top_k=0, alpha=0.25),
 }
