@@ -77,6 +77,8 @@ def _L():
         lib.orc_spmv.argtypes = [i64, P, P, P, P, P]
         lib.orc_reduce_mask.argtypes = [i64, P, P, P, f64, i32, P]
         lib.orc_reduce_mask.restype = i64
+        lib.orc_recover_dense.argtypes = [i64, P, P]
+        lib.orc_recover_dense.restype = i32
         _lib = lib
     return _lib
 
@@ -370,4 +372,21 @@ def reduce(m, fraction, mode=REDUCE_ENTRIES):
     counts = np.array([keep[rp[i]:rp[i + 1]].sum() for i in range(m.n)], dtype=np.int64)
     nrp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
     return Csr(m.n, nrp, col[keep].astype(np.int32), val[keep].astype(np.float64)), keep, int(d)
+
+
+def augmentation(m, alpha):
+    """Diagonal of S = Bhat - B for the Eq. 1 augmentation: alpha ||B||_inf sgn(b_ii)."""
+    d0, _ = split(m, 0.0)
+    d1, _ = split(m, alpha)
+    return d1 - d0
+
+
+def recover_dense(X, s):
+    """Eq. 3 (Algorithm 1 step 5): B^-1 from a dense Bhat^-1 (or an
+    approximation) by n Sherman-Morrison rank-one updates, k = n-1 .. 0."""
+    X = np.ascontiguousarray(np.array(X, dtype=np.float64))
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    if _L().orc_recover_dense(X.shape[0], _p(s), _p(X)) != 0:
+        raise ValueError("zero denominator in the recovery")
+    return X
 

@@ -854,3 +854,43 @@ int64_t orc_reduce_mask(int64_t n, const int64_t *rp, const int32_t *col, const 
     free(e);
     return kdrop;
 }
+
+/* ------------------------------------------------------------------------
+ * Recovery of B^-1 from Bhat^-1 (Eq. 3; Algorithm 1, step 5): with
+ * S = Bhat - B, which is zero except on the diagonal, s_i = alpha ||B||_inf
+ * sgn(b_ii), apply for k = n-1, ..., 0 (the paper's S_{k+1}, row i = k here)
+ *   X <- X + s_i X e_i e_i^T X / (1 - s_i X_ii),
+ * a rank-one update by column i and row i of the current X.  X is the dense
+ * n x n row-major Bhat^-1 (or an approximation of it) and is overwritten by
+ * the recovered B^-1.  s: the n diagonal entries of S.  Returns 0, or -1 if
+ * a denominator is zero.  O(n^3): a diagnostic for small n.
+ * ------------------------------------------------------------------------ */
+int orc_recover_dense(int64_t n, const double *s, double *X)
+{
+    double *c = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    double *r = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+    if (!c || !r) {
+        free(c);
+        free(r);
+        return -1;
+    }
+    int status = 0;
+    for (int64_t i = n - 1; i >= 0 && status == 0; --i) {
+        if (s[i] == 0.0) continue;
+        const double den = 1.0 - s[i] * X[i * n + i];
+        if (den == 0.0) {
+            status = -1;
+            break;
+        }
+        const double g = s[i] / den;
+        for (int64_t a = 0; a < n; ++a) {
+            c[a] = X[a * n + i];
+            r[a] = X[i * n + a];
+        }
+        for (int64_t a = 0; a < n; ++a)
+            for (int64_t b = 0; b < n; ++b) X[a * n + b] += g * c[a] * r[b];
+    }
+    free(c);
+    free(r);
+    return status;
+}

@@ -534,3 +534,43 @@ def test_reduce_keeps_the_diagonal_and_handles_diagonal_matrices():
     assert d == 0 and r.nnz == 3
     with pytest.raises(ValueError):
         oracle.reduce(d0, 1.5, oracle.REDUCE_ENTRIES)
+
+
+# ---------------------------------------------------------------- recovery of B^-1 (Eq. 3, Algorithm 1 step 5)
+
+
+@pytest.mark.parametrize("alpha", [0.3, 1.0, 4.0])
+def test_recovery_of_the_exact_inverse_is_the_inverse(alpha):
+    """Sherman-Morrison is exact: from Bhat^-1 (numpy) the n rank-one
+    updates of Eq. 3 give B^-1 (numpy) up to rounding."""
+    import oracle
+    m = synth.random_dd(80, 6, seed=5, dominance=1.3, diag_sign="mixed")
+    s = oracle.augmentation(m, alpha)
+    B = m.to_scipy().toarray()
+    d1, _ = oracle.split(m, alpha)
+    Bh = B.copy()
+    Bh[np.diag_indices(m.n)] = d1
+    assert np.array_equal(np.diag(Bh) - np.diag(B), s)
+    X = oracle.recover_dense(np.linalg.inv(Bh), s)
+    ref = np.linalg.inv(B)
+    assert np.abs(X - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_recovery_without_augmentation_changes_nothing():
+    import oracle
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((30, 30))
+    Y = oracle.recover_dense(X, np.zeros(30))
+    assert np.array_equal(X, Y)
+
+
+def test_recovery_of_one_diagonal_change():
+    """One nonzero s_i: the recovery inverts Bhat - s_i e_i e_i^T (numpy)."""
+    import oracle
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((25, 25)) + 25 * np.eye(25)
+    s = np.zeros(25)
+    s[7] = 3.5
+    X = oracle.recover_dense(np.linalg.inv(A), s)
+    ref = np.linalg.inv(A - np.diag(s))
+    assert np.abs(X - ref).max() <= 1e-12 * np.abs(ref).max()
