@@ -270,6 +270,24 @@ mcmi_status mcmi_solve(const mcmi_csr *B, mcmi_matrix M, const double *b, double
 void mcmi_free(mcmi_matrix M);
 
 /* ---------------------------------------------------------------------
+ * Recovery of B^-1 from Bhat^-1 (Eq. 3; Algorithm 1, step 5), a dense
+ * O(n^3) diagnostic of the gap between Bhat^-1 and B^-1 for small n.
+ * S = Bhat - B is diagonal: s_i = d_i - b_ii, d_i the Eq. 1 diagonal for
+ * `alpha`.  For i = n-1, ..., 0 with s_i != 0,
+ *     X <- X + g X e_i e_i^T X,  g = s_i / (1 - s_i X_ii)
+ * (each step reads column i, row i and X_ii before updating; FP64, the
+ * product taken as (g x_col) x_row).  B: device CSR; X: device dense
+ * double[n * n], row-major, holding Bhat^-1 or an approximation of it on
+ * entry and the recovered matrix on return.  n <= 16384.  Synchronises
+ * `stream`.  Errors: MCMI_ERR_ARG (bad pointers or n, alpha < 0, a zero
+ * denominator), MCMI_ERR_BAD_CSR, MCMI_ERR_ZERO_DIAG, MCMI_ERR_CUDA.     */
+mcmi_status mcmi_recover_dense(const mcmi_csr *B, double alpha, double *X, void *stream);
+
+/* Dense copy of M: X device double[rows * n_cols], row-major (rows, n_cols
+ * from mcmi_matrix_csr; M's rows start at row_begin).  Asynchronous.      */
+mcmi_status mcmi_matrix_dense(mcmi_matrix M, double *X, void *stream);
+
+/* ---------------------------------------------------------------------
  * Matrix reduction (Algorithm 1, step 2; Sec. III, "Matrix Reduction"):
  * before the split, drop a set share of the off-diagonal entries of B that
  * are smallest in magnitude (diagonal entries are always kept; the others

@@ -115,6 +115,10 @@ def load():
     for f in ("mcmi_proposal_create", "mcmi_proposal_get", "mcmi_row_moments", "mcmi_proposal_loss_grad",
               "mcmi_proposal_train"):
         getattr(lib, f).restype = C.c_int
+    lib.mcmi_recover_dense.argtypes = [C.POINTER(mcmi_csr), f64, P, P]
+    lib.mcmi_recover_dense.restype = C.c_int
+    lib.mcmi_matrix_dense.argtypes = [P, P, P]
+    lib.mcmi_matrix_dense.restype = C.c_int
     lib.mcmi_reduce.argtypes = [C.POINTER(mcmi_csr), f64, i32, P, C.POINTER(P), C.POINTER(i64)]
     lib.mcmi_reduce.restype = C.c_int
     lib.mcmi_reduced_csr.argtypes = [P, C.POINTER(mcmi_csr)]
@@ -208,6 +212,24 @@ class Matrix:
         val = torch.empty(max(nnz, 1), dtype=torch.float32, device="cuda")
         _check(load().mcmi_matrix_copy(self.h, _ptr(rp), _ptr(col), _ptr(val), _stream(stream)))
         return rp, col[:nnz], val[:nnz]
+
+
+def mcmi_recover_dense(B: DeviceCsr, alpha, X, stream=None):
+    """Eq. 3 recovery (Algorithm 1 step 5) in place on the dense row-major
+    FP64 CUDA tensor X (n x n) holding Bhat^-1 or an approximation of it."""
+    assert X.dtype.is_floating_point and X.element_size() == 8 and X.is_contiguous()
+    _check(load().mcmi_recover_dense(C.byref(B.c), float(alpha), _ptr(X), _stream(stream)))
+    return X
+
+
+def mcmi_matrix_dense(M, n, stream=None):
+    """Dense FP64 copy of M (its rows x the n columns of the matrix it was
+    built from) as a CUDA tensor."""
+    import torch
+    rows, rb, nnz = M.shape()
+    X = torch.empty((rows, n), dtype=torch.float64, device="cuda")
+    _check(load().mcmi_matrix_dense(M.h, _ptr(X), _stream(stream)))
+    return X
 
 
 REDUCE_ENTRIES, REDUCE_RANGE = 0, 1

@@ -1271,6 +1271,63 @@ mcmi_status mcmi_proposal_train(const mcmi_csr *Bs, int32_t count, const mcmi_tr
     return MCMI_OK;
 }
 
+mcmi_status mcmi_recover_dense(const mcmi_csr *B, double alpha, double *X, void *stream)
+{
+    mcmi_status r = check_csr(B);
+    if (r != MCMI_OK) return r;
+    if (!X && B->n > 0) return fail(MCMI_ERR_ARG, "X is NULL");
+    if (!(alpha >= 0.0)) return fail(MCMI_ERR_ARG, "alpha must be >= 0");
+    if (B->n > 16384) return fail(MCMI_ERR_ARG, "the dense recovery is a diagnostic for n <= 16384");
+    const int64_t n = B->n;
+    if (n == 0) return MCMI_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+    DevState *st = S.get<DevState>(1);
+    double *d = S.get<double>(n), *sv = S.get<double>(n), *sd = S.get<double>(n);
+    double *c = S.get<double>(n), *rr = S.get<double>(n), *gs = S.get<double>(1);
+    int *flag = S.get<int>(1);
+    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (recovery)");
+    cudaMemsetAsync(st, 0, sizeof(DevState), s);
+    cudaMemsetAsync(&st->err, 0xFF, sizeof(unsigned long long), s);
+    cudaMemsetAsync(&st->smin_bits, 0xFF, sizeof(unsigned long long), s);
+    cudaMemsetAsync(flag, 0, sizeof(int), s);
+    launch_validate(n, B->nnz, B->row_ptr, B->col, B->val, st, s);
+    DevState h;
+    r = read_state(st, &h, s);
+    if (r != MCMI_OK) return r;
+    if (alpha > 0.0) launch_rownorm(n, B->row_ptr, B->val, st, s);
+    launch_split(n, B->row_ptr, B->col, B->val, alpha, d, sv, st, s);
+    cudaError_t e = cudaMemcpyAsync(&h, st, sizeof(DevState), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "device state read");
+    // the recovery needs Bhat, not a contractive split: only other errors count
+    if (h.err != ~0ull && (int)(h.err & 0xFF) != MCMI_ERR_NOT_CONTRACTIVE) return read_state(st, &h, s);
+    e = launch_aug_diag(n, B->row_ptr, B->col, B->val, d, sd, s);
+    std::vector<double> sh((size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sh.data(), sd, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "recovery set-up");
+    for (int64_t i = n - 1; i >= 0 && e == cudaSuccess; --i)
+        if (sh[(size_t)i] != 0.0) e = launch_sm_step(n, X, i, sd, c, rr, gs, flag, s);
+    int hf = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hf, flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "recovery");
+    if (hf) return fail(MCMI_ERR_ARG, "zero denominator 1 - s_i X_ii in the recovery (Eq. 3)");
+    return MCMI_OK;
+}
+
+mcmi_status mcmi_matrix_dense(mcmi_matrix M, double *X, void *stream)
+{
+    if (!M || (!X && M->rows > 0)) return fail(MCMI_ERR_ARG, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(X, 0, (size_t)M->rows * (size_t)M->n_cols * sizeof(double), s);
+    if (e == cudaSuccess) e = launch_csr_dense(M->rows, M->n_cols, M->rp, M->col, M->val, X, s);
+    if (e != cudaSuccess) return cuda_fail(e, "dense copy of M");
+    return MCMI_OK;
+}
+
 mcmi_status mcmi_reduce(const mcmi_csr *B, double fraction, int32_t mode, void *stream, mcmi_reduced *R_out,
                         int64_t *dropped)
 {

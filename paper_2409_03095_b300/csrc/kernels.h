@@ -72,6 +72,14 @@ cudaError_t launch_split(const BatchOut *out, int count, const int64_t *row_base
 cudaError_t launch_spmv(int64_t rows, const int64_t *rp, const int32_t *col, const float *val, const float *x,
                         float *y, cudaStream_t s);
 
+// recovery of B^-1 (Eq. 3) and dense copies
+cudaError_t launch_aug_diag(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
+                            double *s, cudaStream_t st);
+cudaError_t launch_sm_step(int64_t n, double *X, int64_t i, const double *s, double *c, double *r, double *gs,
+                           int *flag, cudaStream_t st);
+cudaError_t launch_csr_dense(int64_t rows, int64_t ncols, const int64_t *rp, const int32_t *col, const float *val,
+                             double *X, cudaStream_t st);
+
 // matrix reduction
 cudaError_t launch_offstats(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
                             unsigned long long *out, cudaStream_t s);
