@@ -328,7 +328,7 @@ def test_edge_bad_parameters():
         assert e.value.status == 1, kw
 
 
-def test_north_star_signature_and_eps_rule():
+def test_mcmi_build_signature_and_eps_rule():
     m = synth.random_dd(64, 4, seed=6, dominance=0.5)
     B = mc.DeviceCsr.from_host(m)
     M = mc.mcmi_build(B, 0.05, 1e-3, 64, 1e-2, 5)
