@@ -23,6 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 TABLE_CUMULATIVE = 0
 TABLE_ALIAS = 1
+TABLE_HYBRID = 2   # per row: cumulative for at most 6 transitions, alias for longer rows
 
 
 def compile_lib(force: bool = False) -> str:

@@ -45,7 +45,17 @@
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_BAD_CSR = 2, ORC_ERR_ZERO_DIAG = 3,
        ORC_ERR_NOT_CONTRACTIVE = 4, ORC_ERR_CAPACITY = 5 };
-enum { ORC_TABLE_CUMULATIVE = 0, ORC_TABLE_ALIAS = 1 };
+enum { ORC_TABLE_CUMULATIVE = 0, ORC_TABLE_ALIAS = 1, ORC_TABLE_HYBRID = 2 };
+
+/* The hybrid table chooses per row: rows with at most ORC_HYBRID_CUM_MAX
+ * transitions sample from the cumulative table, longer rows from the alias
+ * table (both sample the same integer weights q, with different paths).  */
+#define ORC_HYBRID_CUM_MAX 6
+
+static int uses_alias(int table, int64_t deg)
+{
+    return table == ORC_TABLE_ALIAS || (table == ORC_TABLE_HYBRID && deg > ORC_HYBRID_CUM_MAX);
+}
 
 /* ---------------------------------------------------------------------- */
 /* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as  */
@@ -448,8 +458,8 @@ static int mat_prepare(orc_mat *M, int table)
     M->q = (uint32_t *)malloc(sizeof(uint32_t) * sz);
     M->ocol = (int32_t *)malloc(sizeof(int32_t) * sz);
     M->neg = (uint8_t *)malloc(sz);
-    M->prob = table == ORC_TABLE_ALIAS ? (uint32_t *)malloc(sizeof(uint32_t) * sz) : NULL;
-    M->alias = table == ORC_TABLE_ALIAS ? (int32_t *)malloc(sizeof(int32_t) * sz) : NULL;
+    M->prob = table != ORC_TABLE_CUMULATIVE ? (uint32_t *)malloc(sizeof(uint32_t) * sz) : NULL;
+    M->alias = table != ORC_TABLE_CUMULATIVE ? (int32_t *)malloc(sizeof(int32_t) * sz) : NULL;
     M->fac = M->theta ? (double *)malloc(sizeof(double) * sz) : NULL;
     int64_t *degs = NULL;
     if (M->theta) {
@@ -464,7 +474,7 @@ static int mat_prepare(orc_mat *M, int table)
                                                 M->ocol + o, M->neg + o, M->fac + o, NULL, &M->Q[i])
                           : row_weights(i, M->rp, M->col, M->val, M->d, M->s, M->q + o, M->ocol + o, M->neg + o,
                                         &M->Q[i]);
-        if (table == ORC_TABLE_ALIAS && deg > 0)
+        if (uses_alias(table, deg) && deg > 0)
             orc_alias_build(M->q + o, deg, M->Q[i], M->prob + o, M->alias + o);
         o += deg;
     }
@@ -523,7 +533,7 @@ static uint64_t walk_row(const orc_mat *M, int table, int64_t i, int64_t N, int6
             }
             uint32_t r = r4[t % 4];
             int64_t o = M->off[state], deg = M->off[state + 1] - o;
-            int64_t m = table == ORC_TABLE_ALIAS
+            int64_t m = uses_alias(table, deg)
                             ? pick_alias(r, deg, M->Q[state], M->prob + o, M->alias + o)
                             : pick_cumulative(r, M->q + o, deg, M->Q[state]);
             if (M->fac) {
@@ -605,7 +615,7 @@ int orc_row_moments(int64_t n, const int64_t *rp, const int32_t *col, const doub
                     orc_philox4x32_10(ctr, key, r4);
                 }
                 const int64_t o = M.off[state], deg = M.off[state + 1] - o;
-                const int64_t m = table == ORC_TABLE_ALIAS
+                const int64_t m = uses_alias(table, deg)
                                       ? pick_alias(r4[t % 4], deg, M.Q[state], M.prob + o, M.alias + o)
                                       : pick_cumulative(r4[t % 4], M.q + o, deg, M.Q[state]);
                 double f;
