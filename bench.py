@@ -425,7 +425,8 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if a.precision == 64 else "f32", "data": "synthetic",
             "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "rows": last.rows,
-                       "rows_per_s": rows_per_s, "chains": last.chains, "table": ["cumulative", "alias"][last.table],
+                       "rows_per_s": rows_per_s, "chains": last.chains,
+                       "table": ["cumulative", "alias", "hybrid"][last.table],
                        "nnz_M": last.nnz, "steps_per_build": last.steps, "max_len_bound": last.max_len_bound,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"rows on one GPU; {world} independent builds (one per GPU)",
@@ -622,7 +623,7 @@ def run_batched(a):
                        "rows": int(st.rows), "rows_per_s": st.rows * a.steps * world / (tot_ms / 1e3),
                        "steps_per_build": int(st.steps), "generation_s": gen_s,
                        "autotuned": {"threads": st.threads, "chains_per_thread": st.chains_per_thread,
-                                     "hash_log2": st.hash_log2, "table": ["cumulative", "alias"][st.table]},
+                                     "hash_log2": st.hash_log2, "table": ["cumulative", "alias", "hybrid"][st.table]},
                        "walk_ms": float(np.median(walk_ms)), "l2": "flushed between timed steps (256 MiB write)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_walk (batched)",

@@ -57,7 +57,8 @@ typedef enum {
 enum {
     MCMI_TABLE_AUTO = -1,       /* pick from the degree distribution */
     MCMI_TABLE_CUMULATIVE = 0,  /* integer cumulative thresholds */
-    MCMI_TABLE_ALIAS = 1        /* integer Walker/Vose alias buckets */
+    MCMI_TABLE_ALIAS = 1,       /* integer Walker/Vose alias buckets */
+    MCMI_TABLE_HYBRID = 2       /* per row: cumulative for at most 6 transitions (inline), alias otherwise */
 };
 
 /* Row accumulator of the walk kernel.                                    */

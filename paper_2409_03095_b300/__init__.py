@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libmcmi.so")
 MCMI_OK = 0
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_BAD_CSR", 3: "ERR_ZERO_DIAG", 4: "ERR_NOT_CONTRACTIVE",
           5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_CAPACITY"}
-TABLE_AUTO, TABLE_CUMULATIVE, TABLE_ALIAS = -1, 0, 1
+TABLE_AUTO, TABLE_CUMULATIVE, TABLE_ALIAS, TABLE_HYBRID = -1, 0, 1, 2
 ACC_FIXED64, ACC_KAHAN32 = 0, 1
 
 

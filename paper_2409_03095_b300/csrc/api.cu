@@ -200,7 +200,7 @@ mcmi_status check_params(const mcmi_params *p)
     if (p->chains < 0 || p->max_len < 0 || p->top_k < 0) return fail(MCMI_ERR_ARG, "negative count");
     if (p->chains == 0 && !(p->eps > 0.0)) return fail(MCMI_ERR_ARG, "chains == 0 needs eps > 0");
     if (p->precision != 32 && p->precision != 64) return fail(MCMI_ERR_ARG, "precision must be 32 or 64");
-    if (p->table < -1 || p->table > 1) return fail(MCMI_ERR_ARG, "unknown table type");
+    if (p->table < -1 || p->table > 2) return fail(MCMI_ERR_ARG, "unknown table type");
     if (p->chains_per_thread < 0 || p->chains_per_thread > 2)
         return fail(MCMI_ERR_ARG, "chains_per_thread must be 0, 1 or 2");
     if (p->threads != 0 && p->threads != 64 && p->threads != 128 && p->threads != 256)
@@ -256,10 +256,11 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     memcpy(&smax, &h.smax_bits, sizeof(double));
     P.smax = smax;
     if (h.smin_bits != ~0ull) memcpy(&P.smin, &h.smin_bits, sizeof(double));
-    // table type: short rows favour the inline cumulative table (one 64-byte
-    // load per step); long rows the alias table (two loads, no search)
     int table = p->table;
-    if (table == MCMI_TABLE_AUTO) table = (nnz - (int64_t)h.ndiag) <= 6 * n ? MCMI_TABLE_CUMULATIVE : MCMI_TABLE_ALIAS;
+    // automatic choice: short rows on average favour the inline cumulative
+    // table (one 64-byte load per step); otherwise the hybrid table keeps
+    // rows of at most 6 transitions inline and gives longer rows alias buckets
+    if (table == MCMI_TABLE_AUTO) table = (nnz - (int64_t)h.ndiag) <= 6 * n ? MCMI_TABLE_CUMULATIVE : MCMI_TABLE_HYBRID;
     if (p->proposal) table = MCMI_TABLE_ALIAS;   // learned proposals use 32-byte alias buckets
     P.table = table;
     P.learned = p->proposal != nullptr;
@@ -277,8 +278,8 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     P.b = S.get<uint32_t>(nnz);
     unsigned long long *wscr = nullptr;
     uint32_t *sstk = nullptr, *lstk = nullptr;
-    if (table == MCMI_TABLE_ALIAS || keep_debug) P.c = S.get<uint32_t>(nnz);
-    if (table == MCMI_TABLE_ALIAS) {
+    if (table != MCMI_TABLE_CUMULATIVE || keep_debug) P.c = S.get<uint32_t>(nnz);
+    if (table != MCMI_TABLE_CUMULATIVE) {
         P.bkt = S.get<uint4>(nnz);
         wscr = S.get<unsigned long long>(nnz);
         sstk = S.get<uint32_t>(nnz);
@@ -483,8 +484,8 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
     const int64_t sb = rb0 + (re0 - rb0 - ns) / 2, se = sb + ns;
     struct Shape { int threads, cpt; } shapes[] = {{128, 1}, {256, 1}, {128, 2}, {64, 2}};
     const int hashes[] = {10, 11, 12, 13};
-    int tables[2] = {MCMI_TABLE_CUMULATIVE, MCMI_TABLE_ALIAS};
-    const int ntab = p->table == MCMI_TABLE_AUTO ? 2 : 1;
+    int tables[3] = {MCMI_TABLE_CUMULATIVE, MCMI_TABLE_ALIAS, MCMI_TABLE_HYBRID};
+    const int ntab = p->table == MCMI_TABLE_AUTO ? 3 : 1;
     if (p->table != MCMI_TABLE_AUTO) tables[0] = p->table;
     float best = 1e30f, dflt = -1.0f;
     mcmi_params bestp = *p;

@@ -424,7 +424,7 @@ int grid_of(int64_t work, int bs, int cap)
 cudaError_t launch_row_moments(const WalkArgs &a, int table, int64_t n, float *m, cudaStream_t s)
 {
     const int g = grid_of(n * (int64_t)a.N, 256, 148 * 16);
-    if (table == MCMI_TABLE_ALIAS)
+    if (table != MCMI_TABLE_CUMULATIVE)   // alias and hybrid tables
         k_row_moments<MCMI_TABLE_ALIAS><<<g, 256, 0, s>>>(a, n, m);
     else
         k_row_moments<MCMI_TABLE_CUMULATIVE><<<g, 256, 0, s>>>(a, n, m);

@@ -17,6 +17,7 @@ namespace mcmi {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;      // empty accumulator key
 constexpr uint32_t kOolFlag = 0x80000000u;    // slot word 3: table stored out of line
+constexpr uint32_t kCumFlag = 0x40000000u;    // slot word 3: hybrid table, this row is cumulative (inline)
 constexpr uint32_t kNegBit = 0x80000000u;     // record: sign of c_ij
 constexpr int kInlineCum = 6;                 // cumulative pairs that fit a 64-byte slot
 constexpr int kInlineAlias = 4;               // alias triples that fit a 64-byte slot
@@ -118,15 +119,17 @@ struct WalkArgs {
 //   cumulative: x = floor(r Q / 2^32), the smallest m with x < T_m (inline
 //               pairs, or a binary search out of line);
 //   alias:      bucket b = floor(r deg / 2^32), the low 32 bits of r deg
-//               scaled to [0, Q) against the bucket's threshold.
+//               scaled to [0, Q) against the bucket's threshold;
+//   hybrid:     the alias kernels; rows flagged kCumFlag (at most 6
+//               transitions) hold an inline cumulative record.
 template <int TABLE>
 __device__ __forceinline__ uint32_t pick_transition(const uint32_t (&s)[16], uint32_t r, const WalkArgs &a,
                                                     float *f)
 {
     const uint32_t Q = s[0];
-    const uint32_t deg = s[3] & ~kOolFlag;
+    const uint32_t deg = s[3] & ~(kOolFlag | kCumFlag);
     uint32_t cs;
-    if (TABLE == MCMI_TABLE_CUMULATIVE) {
+    if (TABLE == MCMI_TABLE_CUMULATIVE || (s[3] & kCumFlag)) {
         const uint32_t x = __umulhi(r, Q);
         if (!(s[3] & kOolFlag)) {
             const uint32_t m = (s[4] <= x) + (s[6] <= x) + (s[8] <= x) + (s[10] <= x) + (s[12] <= x) + (s[14] <= x);

@@ -126,9 +126,12 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
         w[2] = __float_as_uint(__double2float_rn(__ddiv_rn(1.0, di)));
         if (rowd) rowd[i] = make_double2(si, __ddiv_rn(1.0, di));
         const uint32_t begin = (uint32_t)a;
-        if (table == MCMI_TABLE_CUMULATIVE) {
+        // the hybrid table takes the cumulative layout for rows of at most
+        // kInlineCum transitions (always inline) and the alias layout otherwise
+        const bool cum_row = table == MCMI_TABLE_CUMULATIVE || (table == MCMI_TABLE_HYBRID && deg <= (uint32_t)kInlineCum);
+        if (cum_row) {
             const bool inl = deg <= (uint32_t)kInlineCum;
-            w[3] = deg | (inl ? 0u : kOolFlag);
+            w[3] = deg | (inl ? 0u : kOolFlag) | (table == MCMI_TABLE_HYBRID ? kCumFlag : 0u);
             if (inl) {
 #pragma unroll
                 for (int m = 0; m < kInlineCum; ++m) { w[4 + 2 * m] = 0xFFFFFFFFu; w[5 + 2 * m] = 0u; }

@@ -29,7 +29,7 @@ def _csr(M):
     return out
 
 
-@pytest.mark.parametrize("table", [0, 1])
+@pytest.mark.parametrize("table", [0, 1, 2])
 def test_batched_equals_individual_builds(table):
     mats = _mats()
     Bs = [mc.DeviceCsr.from_host(m) for m in mats]

@@ -39,15 +39,19 @@ def _cases_small():
 
 
 @pytest.mark.parametrize("name", list(_cases_small()))
-@pytest.mark.parametrize("table", [0, 1])
+@pytest.mark.parametrize("table", [0, 1, 2])
 def test_tables_bit_exact(name, table):
+    """Table 2 (hybrid): rows of at most 6 transitions hold the inline
+    cumulative record (flag bit 30), longer rows the alias buckets."""
     orc = _orc()
     m = _cases_small()[name]
     B = mc.DeviceCsr.from_host(m)
     g = mc.mcmi_debug_tables(B, mc.params(table=table))
     d, s = orc.split(m)
     assert np.array_equal(g["d"], d) and np.array_equal(g["s"], s)
-    tb = orc.tables(m, d, s, alias=table == 1)
+    tbc = orc.tables(m, d, s, alias=False)
+    tba = orc.tables(m, d, s, alias=True)
+    tb = tba if table == 1 else tbc
     slot = g["slot"]
     assert np.array_equal(slot[:, 0], tb["Q"].astype(np.uint32))
     assert np.array_equal(slot[:, 1], s.astype(np.float32).view(np.uint32))
@@ -58,9 +62,11 @@ def test_tables_bit_exact(name, table):
         cols = np.array([c for c in m.col[m.row_ptr[i]:m.row_ptr[i + 1]] if c != i], dtype=np.int64)
         vals = np.array([v for c, v in zip(m.col[m.row_ptr[i]:m.row_ptr[i + 1]], m.val[m.row_ptr[i]:m.row_ptr[i + 1]]) if c != i])
         cs = (cols | np.where(-vals / d[i] < 0, 1 << 31, 0)).astype(np.uint32)
-        inline = deg <= (6 if table == 0 else 4)
-        assert slot[i, 3] == (deg | (0 if inline else 1 << 31))
-        if table == 0:
+        kind = table if table != 2 else (0 if deg <= 6 else 1)
+        tb = tbc if kind == 0 else tba
+        inline = deg <= (6 if kind == 0 else 4)
+        assert slot[i, 3] == (deg | (0 if inline else 1 << 31) | (1 << 30 if table == 2 and kind == 0 else 0))
+        if kind == 0:
             T = np.cumsum(tb["q"][a:b].astype(np.uint64)).astype(np.uint32)
             if inline:
                 assert np.array_equal(slot[i, 4:4 + 2 * deg:2], T) and np.array_equal(slot[i, 5:5 + 2 * deg:2], cs)
@@ -96,6 +102,11 @@ WALK_CASES = [
     ("stencil2d", 64, 1, 1000, 64, 1e-3, {"threads": 128, "chains_per_thread": 2}),
     ("powerlaw_4k", 32, 1, 128, 256, 1e-3, {}),
     ("powerlaw_4k", 32, 0, 128, 256, 1e-3, {"hash_log2": 6}),      # forces the overflow log
+    # hybrid table: inline cumulative rows (<= 6 transitions) and alias rows in one walk
+    ("powerlaw_4k", 32, 2, 128, 256, 1e-3, {}),
+    ("powerlaw_4k", 64, 2, 128, 256, 1e-3, {"hash_log2": 6}),
+    ("rand_mixed", 32, 2, 300, 80, 1e-4, {"threads": 64, "chains_per_thread": 2}),
+    ("rand_long", 32, 2, 128, 256, 1e-3, {"accumulator": 1}),
     ("powerlaw_4k", 64, 1, 128, 256, 1e-3, {"hash_log2": 6}),
     ("rand_long", 32, 1, 300, 256, 1e-3, {"hash_log2": 8, "threads": 64, "chains_per_thread": 2}),
     ("stencil2d", 32, 0, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 64}),
