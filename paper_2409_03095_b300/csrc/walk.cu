@@ -210,7 +210,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
 
     __shared__ long long s_row, s_pos, s_key_row;
     __shared__ int s_next_chain;
-    __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent;
+    __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent, s_nred;
     __shared__ long long s_off;
     __shared__ double s_diag;
     __shared__ unsigned long long s_pass_lo, s_pass_hi;
@@ -239,7 +239,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
         s_val[h] = 0ull;
         if (DUMP) s_aux[h] = 0u;
     }
-    if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; }
+    if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; }
 
     // Slot of col in the on-chip table, inserting it if absent; -1 when it
     // is not added.  Linear probing over 4-slot buckets, one 16-byte read per
@@ -501,9 +501,14 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
         // batch instead of one per element.
         constexpr int UF = 8, UL = 4;
         VT lmax = (VT)0;   // largest |M_ij| this thread has finished
+        // Entries of the log below lowthr can never pass the tau rule: lowthr
+        // is tau times a lower bound of the row maximum, rounded down, so the
+        // entry list keeps only possible candidates (0: keep everything).
+        VT lowthr = (VT)0;
+        uint32_t nred = 0;   // distinct log columns this thread reduced (statistics)
         // Finishes the on-chip entries, in place, or appended to the entry
-        // list with the table cleared.
-        auto finish_table = [&](bool to_list) {
+        // list with the table cleared (from_log: entries reduced from the log).
+        auto finish_table = [&](bool to_list, bool from_log) {
             for (int h0 = tid; h0 < H; h0 += UF * B) {
                 uint32_t key[UF];
                 VT invd[UF];
@@ -520,10 +525,13 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
                     lmax = av > lmax ? av : lmax;
                     if (key[u] == (uint32_t)row) s_diag = (double)v;
                     if (to_list) {
-                        const uint32_t p = atomicAdd(&s_nent, 1u);
-                        ec[p] = key[u];
-                        ev[p] = enc(v);
-                        if (DUMP) ecn[p] = s_aux[h];
+                        nred += from_log;
+                        if (!(from_log && av < lowthr)) {
+                            const uint32_t p = atomicAdd(&s_nent, 1u);
+                            ec[p] = key[u];
+                            ev[p] = enc(v);
+                            if (DUMP) ecn[p] = s_aux[h];
+                        }
                         s_keys[h] = kEmpty;
                         s_val[h] = 0ull;
                         if (DUMP || PREC == 64) s_aux[h] = 0u;
@@ -563,7 +571,25 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
             nrem = (uint32_t)block_sum(nrem, s_redu);
         }
         if (nrem) {   // block-uniform
-            finish_table(true);
+            finish_table(true, false);
+            if (!DUMP && use_tau) {
+                // the on-chip entries (the diagonal among them) bound the row maximum from below
+                VT rm;
+                if (PREC == 64) {
+                    unsigned long long lm = (unsigned long long)__double_as_longlong((double)lmax);
+                    for (int o = 16; o > 0; o >>= 1) lm = max(lm, __shfl_xor_sync(0xFFFFFFFFu, lm, o));
+                    __syncthreads();
+                    if ((tid & 31) == 0) s_redu[tid >> 5] = lm;
+                    __syncthreads();
+                    lm = 0;
+                    for (int w = 0; w < (B >> 5); ++w) lm = max(lm, s_redu[w]);
+                    rm = (VT)__longlong_as_double((long long)lm);
+                    lowthr = (VT)__dmul_rd(a.tau, (double)rm);
+                } else {
+                    rm = (VT)block_max((float)lmax, s_redf);
+                    lowthr = (VT)__fmul_rd(__double2float_rd(a.tau), (float)rm);
+                }
+            }
             // bucket starts: exclusive scan of the 256 counts (warp 0, 8 per lane)
             if (tid < 32) {
                 uint32_t c8[8], tot = 0;
@@ -587,7 +613,6 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
                 if (tid == 31) s_bstart[256] = run;
             }
             __syncthreads();
-            const uint32_t n_first = s_nent;   // on-chip entries moved to the list
             for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
                 uint2 key[UL];
                 unsigned long long val[UL];
@@ -647,18 +672,21 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
                         }
                         const bool lead = act && lane == leader;
                         VT v = (VT)0;
+                        bool keep = false;
                         if (lead) {
                             const VT invd = PREC == 64 ? load_invd(key[u].x) : (VT)__uint_as_float(key[u].y);
                             v = finish(single ? val[u] : scratch[lane], invd);
                             const VT av = v < (VT)0 ? -v : v;
                             lmax = av > lmax ? av : lmax;
+                            keep = !(av < lowthr);
+                            ++nred;
                         }
-                        const uint32_t lm = __ballot_sync(0xFFFFFFFFu, lead);
+                        const uint32_t lm = __ballot_sync(0xFFFFFFFFu, keep);
                         const int first = __ffs(lm) - 1;
                         uint32_t base = 0;
-                        if ((int)lane == first) base = atomicAdd(&s_nent, (uint32_t)__popc(lm));
-                        base = __shfl_sync(0xFFFFFFFFu, base, first);
-                        if (lead) {
+                        if (lm && (int)lane == first) base = atomicAdd(&s_nent, (uint32_t)__popc(lm));
+                        if (lm) base = __shfl_sync(0xFFFFFFFFu, base, first);
+                        if (keep) {
                             const uint32_t p = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
                             ec[p] = key[u].x;
                             ev[p] = enc(v);
@@ -730,7 +758,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
                         lo = hi;
                     }
                 } else {
-                    finish_table(true);
+                    finish_table(true, true);
                     retry_hi = 0;
                     lo = hi;
                 }
@@ -738,9 +766,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
                 if (tid == 0) s_fill = 0;
             }
             __syncthreads();
-            if (tid == 0) atomicAdd(&a.st->spilled, (unsigned long long)(s_nent - n_first));
+            if (nred) atomicAdd(&s_nred, nred);
+            __syncthreads();
+            if (tid == 0) atomicAdd(&a.st->spilled, (unsigned long long)s_nred);
         } else {
-            finish_table(false);
+            finish_table(false, false);
         }
         __syncthreads();
         const uint32_t nent = s_nent;
@@ -915,7 +945,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
         __syncthreads();
         // ---- reset the accumulator for the next row ----
         clear_table();
-        if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; }
+        if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; }
     }
 }
 
