@@ -368,19 +368,29 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     a.key1 = (uint32_t)(p->seed >> 32);
     a.log2H = W.log2H;
     a.tau = p->filter_tau;
-    // fixed-point scale: N (L_bound + 1) weights of magnitude <= 1 stay below 2^62
-    // Fixed-point scale 2^F: the largest F for which N (L_bound + 1) weights
-    // of magnitude <= 1 stay below 2^62, lowered to what keeps the rounding
-    // of every accumulated weight below 2^-25 relative: weights are >= delta
-    // until the last step of a chain, which is >= delta * min_i s_i.  A small
-    // F keeps most weights below 2^32, so the high-word atomic is rare.
-    // A learned proposal's weights may exceed 1: 10 more bits of head-room,
-    // and the kernel reports MCMI_ERR_CAPACITY if |W| ever passes 1024.
+    // Fixed-point scale 2^F: at most the F for which N (L_bound + 1) weights
+    // of magnitude <= 1 stay below 2^62.  A small F keeps most weights below
+    // 2^32, so the high-word atomic is rare.
+    //  - FP32 walks with the |c| proposal: every accumulated weight is at
+    //    least w_min = fl32(delta_f fl32(min_i s_i)) (the first weight below the
+    //    cutoff, |W| >= delta_f times |f| >= fl32(s_min), rounded to nearest),
+    //    so F = 23 - floor(log2 w_min) makes every FP32 weight an exact
+    //    integer multiple of 2^-F: the sums are exact.
+    //  - FP64 walks: F keeps the rounding of every weight below 2^-25 relative.
+    //  - A learned proposal's weights may exceed 1: 10 more bits of head-room,
+    //    and the kernel reports MCMI_ERR_CAPACITY if |W| ever passes 1024.
     const double visits = (double)P.N * (double)(P.Lb + 1) + 1.0;
     const int Fmax = 62 - (int)std::ceil(std::log2(visits)) - (P.learned ? 10 : 0);
     int F = Fmax;
     const double wmin = p->delta * (double)(float)P.smin;
-    if (wmin > 0.0) {
+    if (p->precision == 32 && !P.learned && a.delta_f > 0.0f && P.smin > 0.0) {
+        const float wmin32 = a.delta_f * (float)P.smin;   // IEEE single product, no contraction
+        int e = 0;
+        std::frexp(wmin32, &e);                             // wmin32 = m 2^e, m in [0.5, 1)
+        const int Fexact = 23 - (e - 1);
+        F = Fexact < 31 ? 31 : Fexact;
+        if (F > Fmax) F = Fmax;
+    } else if (wmin > 0.0) {
         const int Fneed = 25 + (int)std::ceil(-std::log2(wmin));
         F = Fneed < 31 ? 31 : Fneed;
         if (F > Fmax) F = Fmax;
