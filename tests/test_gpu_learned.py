@@ -153,3 +153,38 @@ def test_training_lowers_the_loss_and_keeps_unbiasedness():
             est = np.zeros(m.n)
             est[g["col"]] = g["val"]
             assert np.linalg.norm(est - inv[r]) / np.linalg.norm(inv[r]) < 0.03
+
+
+def test_trained_proposal_needs_fewer_steps_on_heterogeneous_rows():
+    """Where the rows' own walk lengths differ a lot (s_i from 0.1 to 0.97),
+    |c| is far from the best proposal: after training, the learned proposal
+    reaches the |c| proposal's estimator error with measurably fewer walk
+    steps (errors against the exact inverse, same chains and cutoff)."""
+    rng = np.random.default_rng(0)
+    train = [synth.random_dd(int(n), 6, seed=3000 + k, dominance=0.97, dominance_jitter=0.9, diag_sign="mixed")
+             for k, n in enumerate(rng.integers(1000, 4000, 40))]
+    P = mc.Proposal()
+    tp = mc.mcmi_train_params(steps=150, lr=3e-3, chains=64, max_len=300, delta=1e-4, alpha=0.0, seed=7,
+                              round_bf16=1)
+    hist = mc.mcmi_proposal_train([mc.DeviceCsr.from_host(m) for m in train], tp, P)
+    assert hist[-1] < hist[0]
+    m = synth.random_dd(3000, 6, seed=3999, dominance=0.97, dominance_jitter=0.9, diag_sign="mixed")
+    B = mc.DeviceCsr.from_host(m)
+    inv = np.linalg.inv(m.to_scipy().toarray())
+    rows = np.arange(0, m.n, 29)
+    res = {}
+    for name, prop in (("plain", None), ("learned", P)):
+        p = mc.params(chains=128, max_len=300, delta=1e-4, seed=5, table=mc.TABLE_ALIAS, proposal=prop)
+        errs, steps = [], 0
+        for k in range(6):
+            p.seed = 100 + k
+            for r, g in zip(rows, mc.mcmi_walk_dump(B, p, rows, m.n + 1)):
+                est = np.zeros(m.n)
+                est[g["col"]] = g["val"]
+                errs.append(np.linalg.norm(est - inv[r]) / np.linalg.norm(inv[r]))
+                steps += g["steps"]
+        res[name] = (float(np.mean(errs)), steps)
+    (ep, sp), (el, sl) = res["plain"], res["learned"]
+    ratio = (el / ep) ** 2 * sl / sp    # steps the learned proposal needs at the plain one's error (error ~ N^-1/2)
+    print(f"loss {hist[0]:.4f} -> {hist[-1]:.4f}; eps plain {ep:.4f} learned {el:.4f}; steps at equal error {ratio:.3f}")
+    assert ratio < 0.97
