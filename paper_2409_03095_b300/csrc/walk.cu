@@ -184,11 +184,13 @@ __device__ __forceinline__ void load_slot(const uint4 *sp, uint32_t (&w)[16])
 
 }  // namespace
 
-// Register cap: 72 per thread lets seven 128-thread blocks (896 chains) share
-// an SM with one chain per thread without spilling; measured faster than
-// eight blocks at 64 registers, which spill.
+// Register cap: 64 per thread lets eight 128-thread blocks (1024 chains) share
+// an SM with one chain per thread.  The post-walk loops batch their loads
+// 4 (UF) and 2 (UL) deep so that the kernel stays below the cap without
+// spilling (deeper batches need 72 registers: seven blocks, 2.6% slower on
+// a stencil).  FP64 walks keep 72 (seven blocks) rather than spill.
 template <int PREC, int TABLE, int ACC, bool DUMP, int CPT>
-__global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
+__global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkArgs a)
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
     // finished values and the filter work in the build's precision: FP32
@@ -499,7 +501,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : 72) k_walk(WalkArgs a)
         // The loops below take their global loads in batches (UF, UL per
         // thread) issued before any of them is used: one L2 round trip per
         // batch instead of one per element.
-        constexpr int UF = 8, UL = 4;
+        constexpr int UF = 4, UL = 2;
         VT lmax = (VT)0;   // largest |M_ij| this thread has finished
         // Entries of the log below lowthr can never pass the tau rule: lowthr
         // is tau times a lower bound of the row maximum, rounded down, so the
