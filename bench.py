@@ -398,7 +398,7 @@ def run_ours(a):
     # the walk's launch shape and at full occupancy (outside the timed region)
     foot = SLOT_BYTES * m.n
     try:
-        g_walk = mc.mcmi_gather_roofline(foot, 128, 7, 64)   # the walk's 7 blocks of 128 threads per SM
+        g_walk = mc.mcmi_gather_roofline(foot, 128, 8, 64)   # the walk's 8 blocks of 128 threads per SM
         g_full = mc.mcmi_gather_roofline(foot, 256, 8, 64)
         visits_per_s = visits / (walk_total_ms / 1e3)
         roof["gather"] = {"footprint_bytes": foot, "records_per_s_walk_shape": g_walk,

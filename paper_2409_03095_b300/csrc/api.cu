@@ -321,9 +321,9 @@ struct WalkPlan {
 
 mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, bool dump, WalkPlan &W)
 {
-    // default: 128 threads with one chain each (7 blocks = 7 rows in flight
-    // per SM, register-limited, with a 2^11-slot table); the autotuner may
-    // pick 2 chains per thread or other block sizes
+    // default: 128 threads with one chain each (8 blocks = 8 rows in flight
+    // per SM with a 2^11-slot table); the autotuner may pick 2 chains per
+    // thread or other block sizes
     W.cpt = p->chains_per_thread ? p->chains_per_thread : 1;
     W.threads = p->threads ? p->threads : 128;
     // distinct columns a row can reach: at most N (Lb + 1) visits, at most n columns
@@ -333,7 +333,7 @@ mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, boo
         W.log2H = p->hash_log2;
     } else {
         // on-chip table at most ~75% full for the reachable columns, capped at
-        // 2^11 slots (24 KB) so that seven blocks share an SM; rows that reach
+        // 2^11 slots (24 KB) so that eight blocks share an SM; rows that reach
         // more columns log the excess visits and reduce them after the walks
         int l = ceil_log2((distinct * 4) / 3 + 1);
         W.log2H = l < 8 ? 8 : (l > 11 ? 11 : l);
