@@ -96,24 +96,34 @@ __device__ __forceinline__ float u64_to_f32_rn(unsigned long long u)
 }
 
 // Exact 64-bit add into a shared word from two native 32-bit atomics.
+__device__ __forceinline__ void fix_add_shared(uint32_t *lo_w, uint32_t *hi_w, long long v)
+{
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)((unsigned long long)v >> 32);
+    const uint32_t old = atomicAdd(lo_w, lo);
+    const uint32_t carry = (uint32_t)(old + lo < old);
+    if (hi + carry) atomicAdd(hi_w, hi + carry);
+}
+
 __device__ __forceinline__ void fix_add_shared(unsigned long long *p, long long v)
 {
     uint32_t *w = reinterpret_cast<uint32_t *>(p);
-    const uint32_t lo = (uint32_t)v, hi = (uint32_t)((unsigned long long)v >> 32);
-    const uint32_t old = atomicAdd(w, lo);
-    const uint32_t carry = (uint32_t)(old + lo < old);
-    if (hi + carry) atomicAdd(w + 1, hi + carry);
+    fix_add_shared(w, w + 1, v);
 }
 
-// Compensated FP32 add of v into the {sum, comp} pair at p.
-__device__ __forceinline__ void comp_add(unsigned long long *p, float v)
+// Compensated FP32 add of v into the {sum, comp} pair.
+__device__ __forceinline__ void comp_add(float *sum, float *comp, float v)
 {
-    float *sum = reinterpret_cast<float *>(p);
     const float a = atomicAdd(sum, v);
     const float s = __fadd_rn(a, v);
     const float bp = __fsub_rn(s, a);
     const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(v, bp));
-    if (err != 0.0f) atomicAdd(sum + 1, err);
+    if (err != 0.0f) atomicAdd(comp, err);
+}
+
+__device__ __forceinline__ void comp_add(unsigned long long *p, float v)
+{
+    float *w = reinterpret_cast<float *>(p);
+    comp_add(w, w + 1, v);
 }
 
 __device__ __forceinline__ float block_max(float v, float *red)
@@ -199,15 +209,30 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
     using VT = typename std::conditional<PREC == 64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const int H = 1 << a.log2H;
-    // per slot: an 8-byte value word (fixed-point sum, or FP32 {sum, comp};
-    // after the walks the finished value of M_ij), the key, and an auxiliary
-    // word (visit counts in the parity build, candidate list for FP64 values)
-    unsigned long long *s_val = reinterpret_cast<unsigned long long *>(smem);
-    uint32_t *s_keys = reinterpret_cast<uint32_t *>(smem + (size_t)8 * H);
+    // per slot: a 64-bit value (fixed-point sum, or FP32 {sum, comp}; after
+    // the walks the finished value of M_ij) as a low and a high 32-bit word in
+    // two arrays, so that the low words of neighbouring slots fall in
+    // neighbouring banks; the key; and an auxiliary word (visit counts in the
+    // parity build, candidate list for FP64 values)
+    uint32_t *s_lo = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *s_hi = s_lo + H;
+    uint32_t *s_keys = s_hi + H;
     uint32_t *s_aux = s_keys + H;
-    // FP32 values leave the high half of each value word free for the list
+    auto vword = [&](uint32_t h) -> unsigned long long {
+        return (unsigned long long)s_lo[h] | ((unsigned long long)s_hi[h] << 32);
+    };
+    auto set_vword = [&](uint32_t h, unsigned long long v) {
+        s_lo[h] = (uint32_t)v;
+        s_hi[h] = (uint32_t)(v >> 32);
+    };
+    auto val_add = [&](uint32_t h, unsigned long long add) {
+        if (FIX) fix_add_shared(&s_lo[h], &s_hi[h], (long long)add);
+        else comp_add(reinterpret_cast<float *>(&s_lo[h]), reinterpret_cast<float *>(&s_hi[h]),
+                      __uint_as_float((uint32_t)add));
+    };
+    // FP32 values leave the high words free for the candidate list
     auto list_at = [&](uint32_t p) -> uint32_t & {
-        return PREC == 64 ? s_aux[p] : reinterpret_cast<uint32_t *>(s_val + p)[1];
+        return PREC == 64 ? s_aux[p] : s_hi[p];
     };
 
     __shared__ long long s_row, s_pos, s_key_row;
@@ -238,7 +263,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
 
     for (int h = tid; h < H; h += B) {
         s_keys[h] = kEmpty;
-        s_val[h] = 0ull;
+        s_lo[h] = 0u;
+        s_hi[h] = 0u;
         if (DUMP) s_aux[h] = 0u;
     }
     if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; }
@@ -285,8 +311,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
     auto onchip_add = [&](uint32_t col, unsigned long long add) -> bool {
         const int h = onchip_slot(col);
         if (h < 0) return false;
-        if (FIX) fix_add_shared(&s_val[h], (long long)add);
-        else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
+        val_add((uint32_t)h, add);
         if (DUMP) atomicAdd(&s_aux[h], 1u);
         return true;
     };
@@ -331,15 +356,15 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
                 s_keys[h] = r;
                 s_fill = 1;
                 if (FIX) {
-                    s_val[h] = (unsigned long long)((long long)a.N << F);
+                    set_vword(h, (unsigned long long)((long long)a.N << F));
                 } else {
                     const float invd = __uint_as_float(__ldg(&a.slots[4 * (size_t)r].z));
                     const float s0 = __fmul_rn((float)a.N, invd);
                     const float c0 = __fmaf_rn((float)a.N, invd, -s0);   // exact residual of the product
                     // the pair holds sum + comp == value; the compensation is
                     // stored as an addend, the TwoSum errors are added to it
-                    s_val[h] = (unsigned long long)__float_as_uint(s0) |
-                               ((unsigned long long)__float_as_uint(c0) << 32);
+                    set_vword(h, (unsigned long long)__float_as_uint(s0) |
+                                     ((unsigned long long)__float_as_uint(c0) << 32));
                 }
                 if (DUMP) s_aux[h] = (uint32_t)a.N;
             }
@@ -398,8 +423,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
                 }
                 __syncwarp();
                 if (acc && h >= 0) {
-                    if (FIX) fix_add_shared(&s_val[h], (long long)add);
-                    else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
+                    val_add((uint32_t)h, add);
                     if (DUMP) atomicAdd(&s_aux[h], 1u);
                 }
                 // visits that do not fit on chip go to the log with the FP32 bits
@@ -490,11 +514,12 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
             if (PREC == 64) return (VT)__longlong_as_double((long long)b);
             return (VT)__uint_as_float((uint32_t)b);
         };
-        auto sval = [&](uint32_t h) -> VT { return dec(s_val[h]); };
+        auto sval = [&](uint32_t h) -> VT { return dec(vword(h)); };
         auto clear_table = [&]() {
             for (int h = tid; h < H; h += B) {
                 s_keys[h] = kEmpty;
-                s_val[h] = 0ull;
+                s_lo[h] = 0u;
+        s_hi[h] = 0u;
                 if (DUMP || PREC == 64) s_aux[h] = 0u;
             }
         };
@@ -522,7 +547,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
                 for (int u = 0; u < UF; ++u) {
                     if (key[u] == kEmpty) continue;
                     const int h = h0 + u * B;
-                    const VT v = finish(s_val[h], invd[u]);
+                    const VT v = finish(vword(h), invd[u]);
                     const VT av = v < (VT)0 ? -v : v;
                     lmax = av > lmax ? av : lmax;
                     if (key[u] == (uint32_t)row) s_diag = (double)v;
@@ -535,10 +560,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
                             if (DUMP) ecn[p] = s_aux[h];
                         }
                         s_keys[h] = kEmpty;
-                        s_val[h] = 0ull;
+                        s_lo[h] = 0u;
+        s_hi[h] = 0u;
                         if (DUMP || PREC == 64) s_aux[h] = 0u;
                     } else {
-                        s_val[h] = enc(v);
+                        set_vword(h, enc(v));
                     }
                 }
             }
@@ -560,8 +586,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
                     const int h = onchip_find(key[u]);
                     if (h >= 0) {
                         const unsigned long long add = lv[e];
-                        if (FIX) fix_add_shared(&s_val[h], (long long)add);
-                        else comp_add(&s_val[h], __uint_as_float((uint32_t)add));
+                        val_add((uint32_t)h, add);
                         if (DUMP) atomicAdd(&s_aux[h], 1u);
                         lc[e].x = kEmpty;
                     } else {
@@ -634,11 +659,12 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
             __syncthreads();
             // Buckets of at most 32 entries: one warp each.  Lanes holding the
             // same column find each other with __match_any_sync; the group's
-            // lowest lane sums it in a per-warp scratch row (value words of the
-            // empty table, which needs B <= H slots) and appends the finished entry.
-            const bool by_warp = B <= H;
+            // lowest lane sums it in a per-warp scratch row of 64-bit words
+            // (over the empty table's low words, which needs 2B <= H slots) and
+            // appends the finished entry.
+            const bool by_warp = 2 * B <= H;
             if (by_warp) {
-                unsigned long long *scratch = s_val + (tid & ~31);
+                unsigned long long *scratch = reinterpret_cast<unsigned long long *>(s_lo) + (tid & ~31);
                 constexpr int UB = 2;   // buckets per round: their loads are in flight together
                 const int nw = B >> 5;
                 for (int bk0 = tid >> 5; bk0 < 256; bk0 += UB * nw) {
