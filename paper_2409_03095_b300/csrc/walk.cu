@@ -237,7 +237,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
 
     __shared__ long long s_row, s_pos, s_key_row;
     __shared__ int s_next_chain;
-    __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent, s_nred;
+    __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent, s_nred, s_nsub;
     __shared__ long long s_off;
     __shared__ double s_diag;
     __shared__ unsigned long long s_pass_lo, s_pass_hi;
@@ -898,12 +898,33 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
             };
             uint32_t vstar = 0, cstar_inv = 0;
             if (select) {
+                // magnitude bits of compact candidate i
+                auto cand_mag = [&](uint32_t i) -> uint32_t {
+                    const uint32_t c = list_at(i);
+                    const VT v = c < (uint32_t)H ? sval(c) : dec(ev[c - H]);
+                    return __float_as_uint(fabsf((float)v));
+                };
+                // After the first pass the candidates of the chosen bin (usually
+                // few) are listed in s_bstart, and later passes visit only them.
+                bool narrow = false;
+                uint32_t nsub = 0;
+                auto for_bin = [&](auto fn) {   // fn(magnitude bits, column) over the bin's candidates
+                    if (narrow) {
+                        for (uint32_t t = tid; t < nsub; t += B) {
+                            const uint32_t i = s_bstart[t];
+                            const uint32_t c = list_at(i);
+                            fn(cand_mag(i), c < (uint32_t)H ? s_keys[c] : ec[c - H]);
+                        }
+                    } else {
+                        for_cands([&](uint32_t mag, uint32_t col, VT) { fn(mag, col); });
+                    }
+                };
                 // radix select of the top_k-th largest magnitude (FP32 bits), 8 bits per pass
                 uint32_t pre = 0, mask = 0, kk = (uint32_t)a.top_k;
                 for (int shift = 24; shift >= 0; shift -= 8) {
                     for (int b = tid; b < 256; b += B) s_hist[b] = 0;
                     __syncthreads();
-                    for_cands([&](uint32_t mag, uint32_t, VT) {
+                    for_bin([&](uint32_t mag, uint32_t) {
                         if ((mag & mask) == pre) atomicAdd(&s_hist[(mag >> shift) & 255u], 1u);
                     });
                     __syncthreads();
@@ -912,12 +933,21 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
                     pre |= s_digit << shift;
                     kk = s_rank;
                     mask |= 255u << shift;
+                    if (shift == 24 && compact && s_hist[s_digit] <= 256u) {
+                        if (tid == 0) s_nsub = 0;
+                        __syncthreads();
+                        for (uint32_t i = tid; i < nc; i += B)
+                            if ((cand_mag(i) & mask) == pre) s_bstart[atomicAdd(&s_nsub, 1u)] = i;
+                        __syncthreads();
+                        nsub = s_nsub;
+                        narrow = true;
+                    }
                     __syncthreads();
                 }
                 vstar = pre;               // magnitude bits of the top_k-th largest
                 const uint32_t keep_ties = kk;
                 unsigned long long eq_l = 0;
-                for_cands([&](uint32_t mag, uint32_t, VT) { eq_l += (mag == vstar); });
+                for_bin([&](uint32_t mag, uint32_t) { eq_l += (mag == vstar); });
                 const unsigned long long neq = block_sum(eq_l, s_redu);
                 if (neq > keep_ties) {
                     // equal magnitudes: keep the keep_ties smallest columns (radix select on ~col)
@@ -925,7 +955,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
                     for (int shift = 24; shift >= 0; shift -= 8) {
                         for (int b = tid; b < 256; b += B) s_hist[b] = 0;
                         __syncthreads();
-                        for_cands([&](uint32_t mag, uint32_t col, VT) {
+                        for_bin([&](uint32_t mag, uint32_t col) {
                             const uint32_t inv = ~col;
                             if (mag == vstar && (inv & cmask) == cpre) atomicAdd(&s_hist[(inv >> shift) & 255u], 1u);
                         });
