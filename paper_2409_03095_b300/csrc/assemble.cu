@@ -97,20 +97,75 @@ cudaError_t scan_counts(const int32_t *counts, int64_t n, int64_t *out, int64_t 
     return cudaGetLastError();
 }
 
-// One warp per row: entries of the staging buffer placed at their rank by
-// column (columns are unique inside a row).
-__global__ void k_assemble(int64_t rows, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ st_off,
-                           const int32_t *__restrict__ st_cnt, const uint32_t *__restrict__ st_col,
-                           const float *__restrict__ st_val, int32_t *__restrict__ out_col,
-                           float *__restrict__ out_val)
+// Rows are copied from the staging buffer sorted by column (columns are
+// distinct inside a row).  Entries travel as one 64-bit key, column in the
+// high word and the value's bits in the low word, sorted by a bitonic network
+// in the form whose comparators all put the smaller key at the lower index:
+// merging blocks of k starts with the mirror step (i, i ^ (k - 1)) and goes on
+// with the half-cleaners (i, i + j), j = k/4, ..., 1.  Padding a row to a
+// power of two with +inf keys therefore never moves an entry, and a comparator
+// whose upper index lies past the row's end can simply be skipped.
+constexpr int kAsmWarps = 4;            // warps per block of k_assemble
+constexpr int kAsmWarpMax = 1024;       // rows up to this length: one warp, shared memory
+constexpr int kAsmLongThreads = 256;    // threads per block of k_assemble_long
+constexpr int kAsmTile = 4096;          // shared-memory tile of k_assemble_long
+constexpr unsigned long long kKeyInf = ~0ull;
+
+__device__ __forceinline__ unsigned long long pack_entry(uint32_t c, float v)
 {
+    return ((unsigned long long)c << 32) | __float_as_uint(v);
+}
+
+__device__ __forceinline__ void cmp_swap(unsigned long long *a, int i, int l)
+{
+    const unsigned long long x = a[i], y = a[l];
+    if (x > y) {
+        a[i] = y;
+        a[l] = x;
+    }
+}
+
+// pair q of a step whose comparators span distance h: lower index
+__device__ __forceinline__ int64_t pair_lo(int64_t q, int64_t h) { return ((q & ~(h - 1)) << 1) | (q & (h - 1)); }
+
+// sorts a[0, P) (P a power of two) in shared memory with NT cooperating
+// threads t = 0..NT-1 (one warp, or the whole block)
+template <int NT, bool WARP>
+__device__ __forceinline__ void bitonic_shared(unsigned long long *a, int P, int t)
+{
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int q = t; q < (P >> 1); q += NT) {
+            const int i = (int)pair_lo(q, k >> 1);
+            cmp_swap(a, i, i ^ (k - 1));
+        }
+        if (WARP) __syncwarp(); else __syncthreads();
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            for (int q = t; q < (P >> 1); q += NT) {
+                const int i = (int)pair_lo(q, j);
+                cmp_swap(a, i, i + j);
+            }
+            if (WARP) __syncwarp(); else __syncthreads();
+        }
+    }
+}
+
+// rows of at most kAsmWarpMax entries, one warp per row; longer rows are left
+// to k_assemble_long
+__global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(
+    int64_t rows, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ st_off,
+    const int32_t *__restrict__ st_cnt, const uint32_t *__restrict__ st_col, const float *__restrict__ st_val,
+    int32_t *__restrict__ out_col, float *__restrict__ out_val)
+{
+    __shared__ unsigned long long sk[kAsmWarps][kAsmWarpMax];
     const int lane = threadIdx.x & 31;
+    unsigned long long *key = sk[threadIdx.x >> 5];
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < rows; r += nwarps) {
         const int cnt = st_cnt[r];
         const int64_t off = st_off[r], dst = row_ptr[r];
         if (cnt <= 32) {
+            // rank by shuffles
             const uint32_t c = lane < cnt ? st_col[off + lane] : 0xFFFFFFFFu;
             const float v = lane < cnt ? st_val[off + lane] : 0.0f;
             int rank = 0;
@@ -122,27 +177,136 @@ __global__ void k_assemble(int64_t rows, const int64_t *__restrict__ row_ptr, co
                 out_col[dst + rank] = (int32_t)c;
                 out_val[dst + rank] = v;
             }
-        } else {
-            for (int e = lane; e < cnt; e += 32) {
-                const uint32_t c = st_col[off + e];
-                int rank = 0;
-                for (int j = 0; j < cnt; ++j) rank += st_col[off + j] < c;
-                out_col[dst + rank] = (int32_t)c;
-                out_val[dst + rank] = st_val[off + e];
+        } else if (cnt <= kAsmWarpMax) {
+            int P = 64;
+            while (P < cnt) P <<= 1;
+            for (int i = lane; i < P; i += 32) key[i] = i < cnt ? pack_entry(st_col[off + i], st_val[off + i]) : kKeyInf;
+            __syncwarp();
+            bitonic_shared<32, true>(key, P, lane);
+            for (int i = lane; i < cnt; i += 32) {
+                const unsigned long long x = key[i];
+                out_col[dst + i] = (int32_t)(x >> 32);
+                out_val[dst + i] = __uint_as_float((uint32_t)x);
             }
+            __syncwarp();
         }
     }
+}
+
+// one global comparator of the long-row sort on the output arrays
+__device__ __forceinline__ void cmp_swap_global(int32_t *col, float *val, int64_t i, int64_t l)
+{
+    const int32_t x = col[i], y = col[l];
+    if (x > y) {
+        col[i] = y;
+        col[l] = x;
+        const float t = val[i];
+        val[i] = val[l];
+        val[l] = t;
+    }
+}
+
+// rows longer than kAsmWarpMax, one block per row: tiles of kAsmTile entries
+// are sorted in shared memory and written out; merges of larger blocks run
+// their steps of distance >= kAsmTile on the output arrays in global memory
+// and the shorter half-cleaners tile by tile in shared memory
+__global__ void __launch_bounds__(kAsmLongThreads) k_assemble_long(
+    int64_t rows, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ st_off,
+    const int32_t *__restrict__ st_cnt, const uint32_t *__restrict__ st_col, const float *__restrict__ st_val,
+    int32_t *out_col, float *out_val)
+{
+    __shared__ unsigned long long tile[kAsmTile];
+    __shared__ int64_t list[kAsmLongThreads];
+    __shared__ int nlist;
+    const int t = threadIdx.x;
+    for (int64_t base = (int64_t)blockIdx.x * kAsmLongThreads; base < rows;
+         base += (int64_t)gridDim.x * kAsmLongThreads) {
+        if (t == 0) nlist = 0;
+        __syncthreads();
+        if (base + t < rows && st_cnt[base + t] > kAsmWarpMax) list[atomicAdd(&nlist, 1)] = base + t;
+        __syncthreads();
+        const int nl = nlist;
+        for (int li = 0; li < nl; ++li) {
+            const int64_t r = list[li];
+            const int64_t cnt = st_cnt[r], off = st_off[r];
+            int32_t *oc = out_col + row_ptr[r];
+            float *ov = out_val + row_ptr[r];
+            int64_t P = 1;
+            while (P < cnt) P <<= 1;
+            const int tp = P < kAsmTile ? (int)P : kAsmTile;
+            // tiles sorted in shared memory
+            for (int64_t c0 = 0; c0 < cnt; c0 += kAsmTile) {
+                for (int i = t; i < tp; i += kAsmLongThreads)
+                    tile[i] = c0 + i < cnt ? pack_entry(st_col[off + c0 + i], st_val[off + c0 + i]) : kKeyInf;
+                __syncthreads();
+                bitonic_shared<kAsmLongThreads, false>(tile, tp, t);
+                for (int i = t; i < kAsmTile && c0 + i < cnt; i += kAsmLongThreads) {
+                    const unsigned long long x = tile[i];
+                    oc[c0 + i] = (int32_t)(x >> 32);
+                    ov[c0 + i] = __uint_as_float((uint32_t)x);
+                }
+                __syncthreads();
+            }
+            // merges of blocks larger than a tile
+            for (int64_t k = 2 * (int64_t)kAsmTile; k <= P; k <<= 1) {
+                for (int64_t q = t; q < (P >> 1); q += kAsmLongThreads) {
+                    const int64_t i = pair_lo(q, k >> 1), l = i ^ (k - 1);
+                    if (l < cnt) cmp_swap_global(oc, ov, i, l);
+                }
+                __syncthreads();
+                for (int64_t j = k >> 2; j >= kAsmTile; j >>= 1) {
+                    for (int64_t q = t; q < (P >> 1); q += kAsmLongThreads) {
+                        const int64_t i = pair_lo(q, j), l = i + j;
+                        if (l < cnt) cmp_swap_global(oc, ov, i, l);
+                    }
+                    __syncthreads();
+                }
+                for (int64_t c0 = 0; c0 < cnt; c0 += kAsmTile) {
+                    for (int i = t; i < kAsmTile; i += kAsmLongThreads)
+                        tile[i] = c0 + i < cnt ? pack_entry((uint32_t)oc[c0 + i], ov[c0 + i]) : kKeyInf;
+                    __syncthreads();
+                    for (int j = kAsmTile >> 1; j > 0; j >>= 1) {
+                        for (int q = t; q < (kAsmTile >> 1); q += kAsmLongThreads) {
+                            const int i = (int)pair_lo(q, j);
+                            cmp_swap(tile, i, i + j);
+                        }
+                        __syncthreads();
+                    }
+                    for (int i = t; i < kAsmTile && c0 + i < cnt; i += kAsmLongThreads) {
+                        const unsigned long long x = tile[i];
+                        oc[c0 + i] = (int32_t)(x >> 32);
+                        ov[c0 + i] = __uint_as_float((uint32_t)x);
+                    }
+                    __syncthreads();
+                }
+            }
+        }
+        __syncthreads();   // list and nlist are rewritten by the next round
+    }
+}
+
+static int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
 }
 
 cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t *st_off, const int32_t *st_cnt,
                             const uint32_t *st_col, const float *st_val, int32_t *out_col, float *out_val,
                             cudaStream_t s)
 {
-    const int bs = 256;
+    if (rows <= 0) return cudaGetLastError();
+    const int sms = sm_count();
+    const int bs = 32 * kAsmWarps;
     int64_t g = (rows * 32 + bs - 1) / bs;
-    if (g > 148 * 16) g = 148 * 16;
-    if (g < 1) g = 1;
+    if (g > (int64_t)sms * 32) g = (int64_t)sms * 32;
     k_assemble<<<(unsigned)g, bs, 0, s>>>(rows, row_ptr, st_off, st_cnt, st_col, st_val, out_col, out_val);
+    int64_t gl = (rows + kAsmLongThreads - 1) / kAsmLongThreads;
+    if (gl > (int64_t)sms * 6) gl = (int64_t)sms * 6;
+    k_assemble_long<<<(unsigned)gl, kAsmLongThreads, 0, s>>>(rows, row_ptr, st_off, st_cnt, st_col, st_val, out_col,
+                                                             out_val);
     return cudaGetLastError();
 }
 

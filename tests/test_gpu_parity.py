@@ -231,6 +231,32 @@ def test_build_staging_regrowth_reruns_rows():
     assert M.stats.steps == sum(r["steps"] for r in orows)
 
 
+def test_build_rows_of_every_length_class():
+    """The CSR assembly orders a row by column in ways that depend on its
+    length (up to a warp, up to 1024 entries, one 4096-entry tile, several
+    tiles): rows of each class against the oracle."""
+    m = synth.powerlaw_random(4096, seed=9)
+    B = mc.DeviceCsr.from_host(m)
+    p = mc.params(chains=256, max_len=64, delta=1e-4, seed=11, filter_tau=3e-3)
+    rp = mc.mcmi_build_ex(B, p).to_torch()[0].cpu().numpy()
+    ln = np.diff(rp)
+    picks = []
+    for lo, hi in ((0, 32), (33, 1024), (1025, 1 << 30)):
+        idx = np.flatnonzero((ln >= lo) & (ln <= hi))
+        assert idx.size > 0, (lo, hi, ln.min(), ln.max())
+        picks += [idx[0], idx[-1], idx[idx.size // 2]]
+    picks.append(int(np.argmax(ln)))
+    _check_build(m, np.unique(picks), 256, 64, 1e-4, 3e-3, 0)
+    # rows beyond one 4096-entry shared-memory tile: merged in global memory
+    m = synth.powerlaw_random(1 << 15, seed=9)
+    p = mc.params(chains=512, max_len=64, delta=1e-4, seed=11, filter_tau=1e-4)
+    ln = np.diff(mc.mcmi_build_ex(mc.DeviceCsr.from_host(m), p).to_torch()[0].cpu().numpy())
+    assert ln.max() > 8192
+    big = np.flatnonzero(ln > 4096)
+    picks = [big[0], big[-1], int(np.argmax(ln)), int(np.argmin(ln))]
+    _check_build(m, np.unique(picks), 512, 64, 1e-4, 1e-4, 0)
+
+
 def test_build_through_the_overflow_log():
     """Rows that reach far more columns than a 64-slot on-chip table: visits
     go to the log and are reduced in several hash-range passes."""
