@@ -93,7 +93,11 @@ typedef struct {
     int64_t row_begin;   /* build rows [row_begin, row_end) only; both 0 = all rows */
     int64_t row_end;
     int32_t chains_per_thread; /* chains each walk thread advances in turn: 1 or 2 (0 = auto) */
-    int32_t reserved2;
+    int32_t load_depth;  /* global loads each walk thread keeps in flight in the loops after the
+                          * walks: 4 (FP32: 64 registers, eight 128-thread blocks per SM) or 8
+                          * (72 registers, seven blocks; fewer L2 round trips through the overflow
+                          * log); 0 = auto: 8 for FP32 walks on matrices of more than six
+                          * off-diagonals per row on average, else 4 */
     const struct mcmi_proposal_s *proposal; /* learned proposal (mcmi_proposal_*), NULL = p_ij = |c_ij|/s_i */
 } mcmi_params;
 
@@ -116,7 +120,7 @@ typedef struct {
     int32_t launches;       /* kernels this build launched */
     int32_t threads;        /* walk threads per block used */
     int32_t chains_per_thread; /* chains each walk thread advanced */
-    int32_t reserved;
+    int32_t load_depth;     /* load depth used */
 } mcmi_stats;
 
 typedef struct mcmi_matrix_s *mcmi_matrix;
@@ -147,7 +151,7 @@ typedef struct {
     int32_t trials;             /* configurations timed */
     float best_ms;              /* walk time of the sample rows, best configuration */
     float default_ms;           /* same with the defaults (128 threads, 1 chain, 2^11, cumulative) */
-    int32_t reserved;
+    int32_t load_depth;         /* load depth chosen (4 or 8) */
     int64_t sample_rows;        /* rows in the timed sample */
 } mcmi_tune_result;
 
@@ -155,9 +159,10 @@ typedef struct {
  * about 1/32 of the rows (2048 to 65536 rows, from the middle of the build's
  * row range) for every launch shape (threads per block 64/128/256, 1 or 2
  * chains per thread), on-chip accumulator size (2^10 .. 2^13 slots) and --
- * when p->table is MCMI_TABLE_AUTO -- both table types, with p's other
- * parameters, and writes the fastest choice into p->threads,
- * p->chains_per_thread, p->hash_log2 and p->table.  p: in/out (host);
+ * when p->table is MCMI_TABLE_AUTO -- the three table types, then the best
+ * of those at the other load depth, with p's other parameters, and writes
+ * the fastest choice into p->threads, p->chains_per_thread, p->hash_log2,
+ * p->table and p->load_depth.  p: in/out (host);
  * res: optional (host).  Synchronises `stream`; allocates stream-ordered
  * scratch.  Errors as mcmi_build_ex.                                      */
 mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_tune_result *res);

@@ -39,7 +39,7 @@ class mcmi_params(C.Structure):
                 ("seed", C.c_uint64), ("chains", C.c_int32), ("max_len", C.c_int32), ("top_k", C.c_int32),
                 ("precision", C.c_int32), ("table", C.c_int32), ("threads", C.c_int32), ("hash_log2", C.c_int32),
                 ("accumulator", C.c_int32), ("row_begin", C.c_int64), ("row_end", C.c_int64),
-                ("chains_per_thread", C.c_int32), ("reserved2", C.c_int32), ("proposal", C.c_void_p)]
+                ("chains_per_thread", C.c_int32), ("load_depth", C.c_int32), ("proposal", C.c_void_p)]
 
 
 class mcmi_train_params(C.Structure):
@@ -54,7 +54,7 @@ class mcmi_stats(C.Structure):
                 ("spilled", C.c_int64), ("deferred_rows", C.c_int64), ("ms_prepare", C.c_float),
                 ("ms_walk", C.c_float), ("ms_assemble", C.c_float), ("ms_walk_kernel", C.c_float),
                 ("launches", C.c_int32), ("threads", C.c_int32), ("chains_per_thread", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("load_depth", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -63,7 +63,7 @@ class mcmi_stats(C.Structure):
 class mcmi_tune_result(C.Structure):
     _fields_ = [("threads", C.c_int32), ("chains_per_thread", C.c_int32), ("hash_log2", C.c_int32),
                 ("table", C.c_int32), ("trials", C.c_int32), ("best_ms", C.c_float), ("default_ms", C.c_float),
-                ("reserved", C.c_int32), ("sample_rows", C.c_int64)]
+                ("load_depth", C.c_int32), ("sample_rows", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

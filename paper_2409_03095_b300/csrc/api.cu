@@ -205,6 +205,8 @@ mcmi_status check_params(const mcmi_params *p)
         return fail(MCMI_ERR_ARG, "chains_per_thread must be 0, 1 or 2");
     if (p->threads != 0 && p->threads != 64 && p->threads != 128 && p->threads != 256)
         return fail(MCMI_ERR_ARG, "threads must be 0, 64, 128 or 256");
+    if (p->load_depth != 0 && p->load_depth != 4 && p->load_depth != 8)
+        return fail(MCMI_ERR_ARG, "load_depth must be 0, 4 or 8");
     if (p->threads == 256 && p->chains_per_thread == 2)
         return fail(MCMI_ERR_ARG, "256 threads per block need chains_per_thread 1");
     if (p->hash_log2 != 0 && (p->hash_log2 < 6 || p->hash_log2 > 13)) return fail(MCMI_ERR_ARG, "hash_log2 out of [6, 13]");
@@ -316,7 +318,7 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
 }
 
 struct WalkPlan {
-    int threads = 128, cpt = 2, log2H = 11, grid = 1;
+    int threads = 128, cpt = 2, depth = 4, log2H = 11, grid = 1;
 };
 
 mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, bool dump, WalkPlan &W)
@@ -326,6 +328,11 @@ mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, boo
     // thread or other block sizes
     W.cpt = p->chains_per_thread ? p->chains_per_thread : 1;
     W.threads = p->threads ? p->threads : 128;
+    // load depth 8 for FP32 walks on matrices of more than six off-diagonals
+    // per row on average: their walks spread over many more columns than the
+    // on-chip table holds, and the loops over the overflow log dominate; 4
+    // (eight blocks per SM) otherwise.  FP64 walks spill at depth 8.
+    W.depth = p->load_depth ? p->load_depth : ((p->precision == 32 && (P.nnz - P.n) > 6 * P.n) ? 8 : 4);
     // distinct columns a row can reach: at most N (Lb + 1) visits, at most n columns
     const uint64_t reach = (uint64_t)P.N * (uint64_t)(P.Lb + 2);
     const uint64_t distinct = reach < (uint64_t)P.n ? reach : (uint64_t)P.n;
@@ -339,7 +346,8 @@ mcmi_status plan_walk(const mcmi_params *p, const Prepared &P, int64_t rows, boo
         W.log2H = l < 8 ? 8 : (l > 11 ? 11 : l);
     }
     int bps = 0;
-    cudaError_t e = walk_occupancy(p->precision, P.table, p->accumulator, dump, W.cpt, W.threads, W.log2H, &bps);
+    cudaError_t e = walk_occupancy(p->precision, P.table, p->accumulator, dump, W.cpt, W.depth, W.threads, W.log2H,
+                                   &bps);
     if (e != cudaSuccess) return cuda_fail(e, "walk occupancy");
     if (bps < 1) return fail(MCMI_ERR_ARG, "walk kernel does not fit (threads %d, hash 2^%d)", W.threads, W.log2H);
     int dev = 0, sms = 0;
@@ -463,7 +471,7 @@ mcmi_status time_walk(const mcmi_params *p, const Prepared &P, WalkPlan W, int64
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, s);
-    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.cpt, W.grid, W.threads, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.cpt, W.depth, W.grid, W.threads, s);
     cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     cudaEventElapsedTime(ms, e0, e1);
@@ -526,15 +534,41 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
                 }
             }
     }
+    // the best shape at the other load depth
+    {
+        mcmi_params q = bestp;
+        Scratch S(s);
+        if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+        Prepared P;
+        r = prepare(B, &q, s, S, P, false);
+        if (r != MCMI_OK) return r;
+        WalkPlan W;
+        if (plan_walk(&q, P, ns, false, W) == MCMI_OK) {
+            bestp.load_depth = W.depth;
+            q.load_depth = W.depth == 8 ? 4 : 8;
+            if (plan_walk(&q, P, ns, false, W) == MCMI_OK) {
+                float ms = 0.0f;
+                r = time_walk(&q, P, W, sb, se, s, &ms);
+                if (r != MCMI_OK) return r;
+                ++trials;
+                if (ms < best) {
+                    best = ms;
+                    bestp = q;
+                }
+            }
+        }
+    }
     p->threads = bestp.threads;
     p->chains_per_thread = bestp.chains_per_thread;
     p->hash_log2 = bestp.hash_log2;
     p->table = bestp.table;
+    p->load_depth = bestp.load_depth;
     if (res) {
         res->threads = bestp.threads;
         res->chains_per_thread = bestp.chains_per_thread;
         res->hash_log2 = bestp.hash_log2;
         res->table = bestp.table;
+        res->load_depth = bestp.load_depth;
         res->trials = trials;
         res->best_ms = best;
         res->default_ms = dflt;
@@ -648,7 +682,7 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
     if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (staging)"));
     reset_queue(P.st, s);
     cudaEventRecord(ev[4], s);
-    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.cpt, W.grid, W.threads, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, false, W.cpt, W.depth, W.grid, W.threads, s);
     if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch"));
     cudaEventRecord(ev[5], s);
     ++launches;
@@ -680,7 +714,7 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
         reset_queue(P.st, s);
         WalkPlan W2 = W;
         W2.grid = (int)(deferred < W.grid ? deferred : W.grid);
-        e = launch_walk(a, p->precision, P.table, p->accumulator, false, W2.cpt, W2.grid, W2.threads, s);
+        e = launch_walk(a, p->precision, P.table, p->accumulator, false, W2.cpt, W2.depth, W2.grid, W2.threads, s);
         if (e != cudaSuccess) return give_up(cuda_fail(e, "walk kernel launch (deferred rows)"));
         ++launches;
         r = read_state(P.st, &h, s);
@@ -729,6 +763,7 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
         stats->launches = launches;
         stats->threads = W.threads;
         stats->chains_per_thread = W.cpt;
+        stats->load_depth = W.depth;
     }
     *M_out = M;
     return MCMI_OK;
@@ -849,7 +884,7 @@ mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_par
         cudaMemsetAsync(&P.st->cursor, 0, 8, cs);
         cudaMemsetAsync(&P.st->deferred, 0, 8, cs);
         cudaEventRecord(ev[4], cs);
-        cudaError_t e1 = launch_walk(a, q.precision, P.table, q.accumulator, false, W.cpt, W.grid, W.threads, cs);
+        cudaError_t e1 = launch_walk(a, q.precision, P.table, q.accumulator, false, W.cpt, W.depth, W.grid, W.threads, cs);
         cudaEventRecord(ev[5], cs);
         cudaError_t e2 = scan_counts(a.row_cnt, tn, rpM, tmp, cs);
         e = cudaStreamEndCapture(cs, &graph);
@@ -891,7 +926,7 @@ mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_par
         cudaMemsetAsync(&P.st->deferred, 0, 8, s);
         reset_queue(P.st, s);
         const int g2 = (int)(deferred < W.grid ? deferred : W.grid);
-        e = launch_walk(a, q.precision, P.table, q.accumulator, false, W.cpt, g2, W.threads, s);
+        e = launch_walk(a, q.precision, P.table, q.accumulator, false, W.cpt, W.depth, g2, W.threads, s);
         if (e == cudaSuccess) e = scan_counts(a.row_cnt, tn, rpM, tmp, s);
         if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch (deferred rows)");
         launches += 4;
@@ -967,6 +1002,7 @@ mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_par
         stats->launches = launches;
         stats->threads = W.threads;
         stats->chains_per_thread = W.cpt;
+        stats->load_depth = W.depth;
     }
     return MCMI_OK;
 }
@@ -1054,7 +1090,7 @@ mcmi_status mcmi_walk_dump(const mcmi_csr *B, const mcmi_params *p, const int64_
     a.d_cap = cap;
     a.row_steps = out_steps;
     reset_queue(P.st, s);
-    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, true, W.cpt, W.grid, W.threads, s);
+    cudaError_t e = launch_walk(a, p->precision, P.table, p->accumulator, true, W.cpt, W.depth, W.grid, W.threads, s);
     if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     DevState h;
     return read_state(P.st, &h, s);

@@ -19,10 +19,11 @@ void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const doubl
                    cudaStream_t s);
 
 size_t walk_smem_bytes(int precision, int log2H, bool dump);
-cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int cpt, int threads, int log2H,
+// depth: loads per thread in flight after the walks (4 or 8)
+cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int cpt, int depth, int threads, int log2H,
                            int *blocks_per_sm);
-cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int cpt, int grid,
-                        int threads, cudaStream_t s);
+cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int cpt, int depth,
+                        int grid, int threads, cudaStream_t s);
 
 // exclusive scan of int32 counts into int64 offsets (out has n+1 entries)
 cudaError_t scan_counts(const int32_t *counts, int64_t n, int64_t *out, int64_t *block_tmp, cudaStream_t s);

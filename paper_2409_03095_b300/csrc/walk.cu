@@ -194,13 +194,15 @@ __device__ __forceinline__ void load_slot(const uint4 *sp, uint32_t (&w)[16])
 
 }  // namespace
 
-// Register cap: 64 per thread lets eight 128-thread blocks (1024 chains) share
-// an SM with one chain per thread.  The post-walk loops batch their loads
-// 4 (UF) and 2 (UL) deep so that the kernel stays below the cap without
-// spilling (deeper batches need 72 registers: seven blocks, 2.6% slower on
-// a stencil).  FP64 walks keep 72 (seven blocks) rather than spill.
-template <int PREC, int TABLE, int ACC, bool DUMP, int CPT>
-__global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkArgs a)
+// Register cap and load depth.  The loops after the walks take their global
+// loads in batches of DEPTH (UF) and DEPTH/2 (UL) per thread.  DEPTH 4 keeps
+// an FP32 walk with one chain per thread at 64 registers, so eight 128-thread
+// blocks (1024 chains) share an SM; DEPTH 8 needs 72 (seven blocks) but
+// halves the L2 round trips of those loops, which pays for rows that send
+// most of their visits through the overflow log.  FP64 walks take 72
+// registers at either depth rather than spill.
+template <int PREC, int TABLE, int ACC, bool DUMP, int CPT, int DEPTH>
+__global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 64)) k_walk(WalkArgs a)
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
     // finished values and the filter work in the build's precision: FP32
@@ -526,7 +528,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : (PREC == 64 ? 72 : 64)) k_walk(WalkA
         // The loops below take their global loads in batches (UF, UL per
         // thread) issued before any of them is used: one L2 round trip per
         // batch instead of one per element.
-        constexpr int UF = 4, UL = 2;
+        constexpr int UF = DEPTH, UL = DEPTH / 2;
         VT lmax = (VT)0;   // largest |M_ij| this thread has finished
         // Entries of the log below lowthr can never pass the tau rule: lowthr
         // is tau times a lower bound of the row maximum, rounded down, so the
@@ -1016,36 +1018,45 @@ size_t walk_smem_bytes(int precision, int log2H, bool dump)
 namespace {
 using WalkFn = void (*)(WalkArgs);
 
-template <bool D, int C>
+template <bool D, int C, int U>
 WalkFn pick_walk(int precision, int table, int acc)
 {
-    if (precision == 64) return table ? k_walk<64, 1, MCMI_ACC_FIXED64, D, C> : k_walk<64, 0, MCMI_ACC_FIXED64, D, C>;
-    if (acc == MCMI_ACC_KAHAN32) return table ? k_walk<32, 1, MCMI_ACC_KAHAN32, D, C> : k_walk<32, 0, MCMI_ACC_KAHAN32, D, C>;
-    return table ? k_walk<32, 1, MCMI_ACC_FIXED64, D, C> : k_walk<32, 0, MCMI_ACC_FIXED64, D, C>;
+    if (precision == 64)
+        return table ? k_walk<64, 1, MCMI_ACC_FIXED64, D, C, U> : k_walk<64, 0, MCMI_ACC_FIXED64, D, C, U>;
+    if (acc == MCMI_ACC_KAHAN32)
+        return table ? k_walk<32, 1, MCMI_ACC_KAHAN32, D, C, U> : k_walk<32, 0, MCMI_ACC_KAHAN32, D, C, U>;
+    return table ? k_walk<32, 1, MCMI_ACC_FIXED64, D, C, U> : k_walk<32, 0, MCMI_ACC_FIXED64, D, C, U>;
 }
 
-WalkFn walk_kernel(int precision, int table, int acc, bool dump, int cpt)
+template <int U>
+WalkFn walk_kernel_d(int precision, int table, int acc, bool dump, int cpt)
 {
-    if (cpt == 1) return dump ? pick_walk<true, 1>(precision, table, acc) : pick_walk<false, 1>(precision, table, acc);
-    return dump ? pick_walk<true, 2>(precision, table, acc) : pick_walk<false, 2>(precision, table, acc);
+    if (cpt == 1) return dump ? pick_walk<true, 1, U>(precision, table, acc) : pick_walk<false, 1, U>(precision, table, acc);
+    return dump ? pick_walk<true, 2, U>(precision, table, acc) : pick_walk<false, 2, U>(precision, table, acc);
+}
+
+WalkFn walk_kernel(int precision, int table, int acc, bool dump, int cpt, int depth)
+{
+    return depth == 8 ? walk_kernel_d<8>(precision, table, acc, dump, cpt)
+                      : walk_kernel_d<4>(precision, table, acc, dump, cpt);
 }
 }  // namespace
 
-cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int cpt, int threads, int log2H,
+cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int cpt, int depth, int threads, int log2H,
                            int *blocks_per_sm)
 {
     const size_t smem = walk_smem_bytes(precision, log2H, dump);
-    const WalkFn fn = walk_kernel(precision, table, acc, dump, cpt);
+    const WalkFn fn = walk_kernel(precision, table, acc, dump, cpt, depth);
     cudaError_t e = cudaFuncSetAttribute((const void *)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void *)fn, threads, smem);
 }
 
-cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int cpt, int grid,
-                        int threads, cudaStream_t s)
+cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bool dump, int cpt, int depth,
+                        int grid, int threads, cudaStream_t s)
 {
     const size_t smem = walk_smem_bytes(precision, a.log2H, dump);
-    const WalkFn fn = walk_kernel(precision, table, acc, dump, cpt);
+    const WalkFn fn = walk_kernel(precision, table, acc, dump, cpt, depth);
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(s, &cap);
     if (cap == cudaStreamCaptureStatusNone) {   // during graph capture it was set by walk_occupancy
