@@ -521,7 +521,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             for (int h = tid; h < H; h += B) {
                 s_keys[h] = kEmpty;
                 s_lo[h] = 0u;
-        s_hi[h] = 0u;
+                s_hi[h] = 0u;
                 if (DUMP || PREC == 64) s_aux[h] = 0u;
             }
         };
@@ -563,7 +563,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         }
                         s_keys[h] = kEmpty;
                         s_lo[h] = 0u;
-        s_hi[h] = 0u;
+                        s_hi[h] = 0u;
                         if (DUMP || PREC == 64) s_aux[h] = 0u;
                     } else {
                         set_vword(h, enc(v));
