@@ -739,7 +739,8 @@ mcmi_status mcmi_build_ex(const mcmi_csr *B, const mcmi_params *p, void *stream,
     if (S.err != cudaSuccess) return give_up(cuda_fail(S.err, "allocation (M)"));
     S.keep(M->col);
     S.keep(M->val);
-    e = launch_assemble(rows, M->rp, a.row_off, a.row_cnt, a.st_col, a.st_val, M->col, M->val, s);
+    e = launch_assemble(rows, M->rp, a.row_off, a.row_cnt, a.st_col, a.st_val, M->col, M->val,
+                        p->top_k > 0 ? (int64_t)p->top_k + 1 : 0, s);
     if (e != cudaSuccess) return give_up(cuda_fail(e, "assembly"));
     launches += 4;   // three scan kernels + assembly
     cudaEventRecord(ev[3], s);
@@ -946,7 +947,8 @@ mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_par
     BatchOut *d_out = S.get<BatchOut>(count);
     int64_t *d_nnzM_base = S.get<int64_t>(count + 1);
     if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (batched M)");
-    e = launch_assemble(tn, rpM, a.row_off, a.row_cnt, a.st_col, a.st_val, colM, valM, s);
+    e = launch_assemble(tn, rpM, a.row_off, a.row_cnt, a.st_col, a.st_val, colM, valM,
+                        q.top_k > 0 ? (int64_t)q.top_k + 1 : 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "assembly");
     std::vector<BatchOut> out(count);
     std::vector<mcmi_matrix> made;

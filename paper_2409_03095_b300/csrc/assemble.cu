@@ -149,16 +149,17 @@ __device__ __forceinline__ void bitonic_shared(unsigned long long *a, int P, int
     }
 }
 
-// rows of at most kAsmWarpMax entries, one warp per row; longer rows are left
-// to k_assemble_long
+// rows of at most wmax entries (32, or kAsmWarpMax with kAsmWarpMax keys of
+// dynamic shared memory per warp), one warp per row; longer rows are left to
+// k_assemble_long
 __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(
     int64_t rows, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ st_off,
     const int32_t *__restrict__ st_cnt, const uint32_t *__restrict__ st_col, const float *__restrict__ st_val,
-    int32_t *__restrict__ out_col, float *__restrict__ out_val)
+    int32_t *__restrict__ out_col, float *__restrict__ out_val, int wmax)
 {
-    __shared__ unsigned long long sk[kAsmWarps][kAsmWarpMax];
+    extern __shared__ unsigned long long sk[];
     const int lane = threadIdx.x & 31;
-    unsigned long long *key = sk[threadIdx.x >> 5];
+    unsigned long long *key = sk + (threadIdx.x >> 5) * kAsmWarpMax;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < rows; r += nwarps) {
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(
                 out_col[dst + rank] = (int32_t)c;
                 out_val[dst + rank] = v;
             }
-        } else if (cnt <= kAsmWarpMax) {
+        } else if (cnt <= wmax) {
             int P = 64;
             while (P < cnt) P <<= 1;
             for (int i = lane; i < P; i += 32) key[i] = i < cnt ? pack_entry(st_col[off + i], st_val[off + i]) : kKeyInf;
@@ -206,14 +207,14 @@ __device__ __forceinline__ void cmp_swap_global(int32_t *col, float *val, int64_
     }
 }
 
-// rows longer than kAsmWarpMax, one block per row: tiles of kAsmTile entries
+// rows longer than wmax, one block per row: tiles of kAsmTile entries
 // are sorted in shared memory and written out; merges of larger blocks run
 // their steps of distance >= kAsmTile on the output arrays in global memory
 // and the shorter half-cleaners tile by tile in shared memory
 __global__ void __launch_bounds__(kAsmLongThreads) k_assemble_long(
     int64_t rows, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ st_off,
     const int32_t *__restrict__ st_cnt, const uint32_t *__restrict__ st_col, const float *__restrict__ st_val,
-    int32_t *out_col, float *out_val)
+    int32_t *out_col, float *out_val, int wmax)
 {
     __shared__ unsigned long long tile[kAsmTile];
     __shared__ int64_t list[kAsmLongThreads];
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kAsmLongThreads) k_assemble_long(
          base += (int64_t)gridDim.x * kAsmLongThreads) {
         if (t == 0) nlist = 0;
         __syncthreads();
-        if (base + t < rows && st_cnt[base + t] > kAsmWarpMax) list[atomicAdd(&nlist, 1)] = base + t;
+        if (base + t < rows && st_cnt[base + t] > wmax) list[atomicAdd(&nlist, 1)] = base + t;
         __syncthreads();
         const int nl = nlist;
         for (int li = 0; li < nl; ++li) {
@@ -295,18 +296,23 @@ static int sm_count()
 
 cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t *st_off, const int32_t *st_cnt,
                             const uint32_t *st_col, const float *st_val, int32_t *out_col, float *out_val,
-                            cudaStream_t s)
+                            int64_t max_cnt, cudaStream_t s)
 {
     if (rows <= 0) return cudaGetLastError();
     const int sms = sm_count();
     const int bs = 32 * kAsmWarps;
+    // rows known to fit a warp's shuffles need no shared memory (more blocks per SM)
+    const bool small = max_cnt > 0 && max_cnt <= 32;
+    const int wmax = small ? 32 : kAsmWarpMax;
+    const size_t smem = small ? 0 : (size_t)kAsmWarps * kAsmWarpMax * sizeof(unsigned long long);
     int64_t g = (rows * 32 + bs - 1) / bs;
     if (g > (int64_t)sms * 32) g = (int64_t)sms * 32;
-    k_assemble<<<(unsigned)g, bs, 0, s>>>(rows, row_ptr, st_off, st_cnt, st_col, st_val, out_col, out_val);
+    k_assemble<<<(unsigned)g, bs, smem, s>>>(rows, row_ptr, st_off, st_cnt, st_col, st_val, out_col, out_val, wmax);
+    if (small) return cudaGetLastError();
     int64_t gl = (rows + kAsmLongThreads - 1) / kAsmLongThreads;
     if (gl > (int64_t)sms * 6) gl = (int64_t)sms * 6;
     k_assemble_long<<<(unsigned)gl, kAsmLongThreads, 0, s>>>(rows, row_ptr, st_off, st_cnt, st_col, st_val, out_col,
-                                                             out_val);
+                                                             out_val, wmax);
     return cudaGetLastError();
 }
 

@@ -29,9 +29,10 @@ cudaError_t launch_walk(const WalkArgs &a, int precision, int table, int acc, bo
 cudaError_t scan_counts(const int32_t *counts, int64_t n, int64_t *out, int64_t *block_tmp, cudaStream_t s);
 size_t scan_tmp_elems(int64_t n);
 
+// max_cnt: an upper bound of the entries of any row, or 0 if unknown
 cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t *st_off, const int32_t *st_cnt,
                             const uint32_t *st_col, const float *st_val, int32_t *out_col, float *out_val,
-                            cudaStream_t s);
+                            int64_t max_cnt, cudaStream_t s);
 // message returned by mcmi_last_error() on this host thread
 void set_error_message(const char *msg);
 
