@@ -69,6 +69,9 @@ def _args():
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64],
                     help="walk weights and accumulator precision of the build")
     ap.add_argument("--no-quality", action="store_true", help="skip the (untimed) estimator-error check")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the launch shape, accumulator size, table and load depth with mcmi_autotune "
+                         "before the warm-up (untimed set-up)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--learned", action="store_true",
                     help="learned vs |c| proposal on the anisotropic 1024^2 problem (one JSON line)")
@@ -282,6 +285,7 @@ def run_ours(a):
     mc.load()
     m, w, p = _params_for(mc, a.workload, seed=1000 + rank, precision=a.precision)
     B = mc.DeviceCsr.from_host(m)
+    tuned = mc.mcmi_autotune(B, p).as_dict() if a.autotune else None
     x = torch.ones(m.n, device="cuda", dtype=torch.float32)
     y = torch.empty(m.n, device="cuda", dtype=torch.float32)
     flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)   # 256 MiB > L2
@@ -431,6 +435,9 @@ def run_ours(a):
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"rows on one GPU; {world} independent builds (one per GPU)",
                        "stage_ms": {"prepare": last.ms_prepare, "walk": last.ms_walk, "assemble": last.ms_assemble},
+                       "launch": {"threads": last.threads, "chains_per_thread": last.chains_per_thread,
+                                  "hash_log2": last.hash_log2, "load_depth": last.load_depth,
+                                  "autotuned": tuned},
                        "quality": quality},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": ck}
     print(json.dumps(line), flush=True)

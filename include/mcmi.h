@@ -149,22 +149,24 @@ typedef struct {
     int32_t hash_log2;          /* on-chip accumulator slots (log2) */
     int32_t table;              /* sampling table type */
     int32_t trials;             /* configurations timed */
-    float best_ms;              /* walk time of the sample rows, best configuration */
-    float default_ms;           /* same with the defaults (128 threads, 1 chain, 2^11, cumulative) */
+    float best_ms;              /* walk time of the sample rows, configuration chosen */
+    float default_ms;           /* same with the default plan (p as given, 0 fields = auto) */
     int32_t load_depth;         /* load depth chosen (4 or 8) */
     int64_t sample_rows;        /* rows in the timed sample */
 } mcmi_tune_result;
 
-/* Autotuner: times the walk kernel (CUDA events) on a contiguous sample of
- * about 1/32 of the rows (2048 to 65536 rows, from the middle of the build's
- * row range) for every launch shape (threads per block 64/128/256, 1 or 2
- * chains per thread), on-chip accumulator size (2^10 .. 2^13 slots) and --
- * when p->table is MCMI_TABLE_AUTO -- the three table types, then the best
- * of those at the other load depth, with p's other parameters, and writes
- * the fastest choice into p->threads, p->chains_per_thread, p->hash_log2,
- * p->table and p->load_depth.  p: in/out (host);
- * res: optional (host).  Synchronises `stream`; allocates stream-ordered
- * scratch.  Errors as mcmi_build_ex.                                      */
+/* Autotuner: times the walk kernel (CUDA events; each configuration twice,
+ * the faster launch counts) on a contiguous sample of about 1/32 of the rows
+ * (8192 to 65536 rows, from the middle of the build's row range): first the
+ * default plan (p as given, its 0 fields auto), then every launch shape
+ * (threads per block 64/128/256, 1 or 2 chains per thread) and on-chip
+ * accumulator size (2^9 .. 2^13 slots) for each table type (all three when
+ * p->table is MCMI_TABLE_AUTO), then the best of those at the other load
+ * depth.  The best trial replaces the default plan only when it is at least
+ * 2% faster.  Writes the choice into p->threads, p->chains_per_thread,
+ * p->hash_log2, p->table and p->load_depth.  p: in/out (host); res: optional
+ * (host).  Synchronises `stream`; allocates stream-ordered scratch.  Errors
+ * as mcmi_build_ex.                                                       */
 mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_tune_result *res);
 
 /* Batched build of `count` independent matrices (each n >= 1) with the same

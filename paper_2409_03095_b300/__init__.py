@@ -357,7 +357,8 @@ def mcmi_exclusive_scan_noalloc(counts, offsets, stream=None):
 
 def mcmi_autotune(B: DeviceCsr, p: mcmi_params, stream=None):
     """Times walk configurations on a row sample and writes the fastest into
-    p (threads, chains_per_thread, hash_log2, table); returns the report."""
+    p (threads, chains_per_thread, hash_log2, table, load_depth); returns the
+    report."""
     res = mcmi_tune_result()
     _check(load().mcmi_autotune(C.byref(B.c), C.byref(p), _stream(stream), C.byref(res)))
     return res

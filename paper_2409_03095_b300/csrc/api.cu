@@ -495,19 +495,54 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
     const int64_t re0 = (p->row_begin == 0 && p->row_end == 0) ? n : p->row_end;
     if (rb0 < 0 || re0 <= rb0 || re0 > n) return fail(MCMI_ERR_ARG, "bad row range");
     cudaStream_t s = (cudaStream_t)stream;
-    // sample: a contiguous window of about 1/32 of the rows (2048 .. 65536) in the middle
+    // sample: a contiguous window of about 1/32 of the rows in the middle,
+    // 8192 .. 65536 rows (several rows per resident block, so that the last
+    // rows' tail does not decide a trial)
     int64_t ns = (re0 - rb0) / 32;
-    ns = ns < 2048 ? 2048 : (ns > 65536 ? 65536 : ns);
+    ns = ns < 8192 ? 8192 : (ns > 65536 ? 65536 : ns);
     if (ns > re0 - rb0) ns = re0 - rb0;
     const int64_t sb = rb0 + (re0 - rb0 - ns) / 2, se = sb + ns;
+    int trials = 0;
+    // one configuration: the faster of two launches on the sample
+    auto trial = [&](const mcmi_params &q, const Prepared &P, WalkPlan &W, float *ms, bool *fits) -> mcmi_status {
+        *fits = plan_walk(&q, P, ns, false, W) == MCMI_OK;
+        if (!*fits) return MCMI_OK;
+        float t0 = 0.0f, t1 = 0.0f;
+        mcmi_status rr = time_walk(&q, P, W, sb, se, s, &t0);
+        if (rr == MCMI_OK) rr = time_walk(&q, P, W, sb, se, s, &t1);
+        *ms = t0 < t1 ? t0 : t1;
+        ++trials;
+        return rr;
+    };
+    // the default plan first: a trial replaces it only when at least 2% faster
+    mcmi_params bestp = *p;
+    float dflt = -1.0f;
+    {
+        Scratch S(s);
+        if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
+        Prepared P;
+        r = prepare(B, p, s, S, P, false);
+        if (r != MCMI_OK) return r;
+        WalkPlan W;
+        bool fits = false;
+        r = trial(*p, P, W, &dflt, &fits);
+        if (r != MCMI_OK) return r;
+        if (!fits) return fail(MCMI_ERR_ARG, "walk kernel does not fit with the given parameters");
+        bestp.threads = W.threads;
+        bestp.chains_per_thread = W.cpt;
+        bestp.hash_log2 = W.log2H;
+        bestp.load_depth = W.depth;
+        bestp.table = P.table;
+    }
+    float best = dflt;
+    const float bar = 0.98f * dflt;
     struct Shape { int threads, cpt; } shapes[] = {{128, 1}, {256, 1}, {128, 2}, {64, 2}};
-    const int hashes[] = {10, 11, 12, 13};
+    const int hashes[] = {9, 10, 11, 12, 13};
     int tables[3] = {MCMI_TABLE_CUMULATIVE, MCMI_TABLE_ALIAS, MCMI_TABLE_HYBRID};
     const int ntab = p->table == MCMI_TABLE_AUTO ? 3 : 1;
     if (p->table != MCMI_TABLE_AUTO) tables[0] = p->table;
-    float best = 1e30f, dflt = -1.0f;
-    mcmi_params bestp = *p;
-    int trials = 0;
+    mcmi_params cand = bestp;
+    float cand_ms = 1e30f;
     for (int ti = 0; ti < ntab; ++ti) {
         mcmi_params q = *p;
         q.table = tables[ti];
@@ -522,41 +557,39 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
                 q.chains_per_thread = sh.cpt;
                 q.hash_log2 = hl;
                 WalkPlan W;
-                if (plan_walk(&q, P, ns, false, W) != MCMI_OK) continue;   // does not fit
                 float ms = 0.0f;
-                r = time_walk(&q, P, W, sb, se, s, &ms);
+                bool fits = false;
+                r = trial(q, P, W, &ms, &fits);
                 if (r != MCMI_OK) return r;
-                ++trials;
-                if (sh.threads == 128 && sh.cpt == 1 && hl == 11 && ti == 0) dflt = ms;
-                if (ms < best) {
-                    best = ms;
-                    bestp = q;
+                if (fits && ms < cand_ms) {
+                    cand_ms = ms;
+                    cand = q;
+                    cand.load_depth = W.depth;
                 }
             }
     }
     // the best shape at the other load depth
     {
-        mcmi_params q = bestp;
+        mcmi_params q = cand;
         Scratch S(s);
         if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
         Prepared P;
         r = prepare(B, &q, s, S, P, false);
         if (r != MCMI_OK) return r;
+        q.load_depth = cand.load_depth == 8 ? 4 : 8;
         WalkPlan W;
-        if (plan_walk(&q, P, ns, false, W) == MCMI_OK) {
-            bestp.load_depth = W.depth;
-            q.load_depth = W.depth == 8 ? 4 : 8;
-            if (plan_walk(&q, P, ns, false, W) == MCMI_OK) {
-                float ms = 0.0f;
-                r = time_walk(&q, P, W, sb, se, s, &ms);
-                if (r != MCMI_OK) return r;
-                ++trials;
-                if (ms < best) {
-                    best = ms;
-                    bestp = q;
-                }
-            }
+        float ms = 0.0f;
+        bool fits = false;
+        r = trial(q, P, W, &ms, &fits);
+        if (r != MCMI_OK) return r;
+        if (fits && ms < cand_ms) {
+            cand_ms = ms;
+            cand = q;
         }
+    }
+    if (cand_ms < bar) {
+        best = cand_ms;
+        bestp = cand;
     }
     p->threads = bestp.threads;
     p->chains_per_thread = bestp.chains_per_thread;
