@@ -96,8 +96,10 @@ typedef struct {
     int32_t load_depth;  /* global loads each walk thread keeps in flight in the loops after the
                           * walks: 4 (FP32: 64 registers, eight 128-thread blocks per SM) or 8
                           * (72 registers, seven blocks; fewer L2 round trips through the overflow
-                          * log); 0 = auto: 8 for FP32 walks on matrices of more than six
-                          * off-diagonals per row on average, else 4 */
+                          * log, and FP32 tau builds drop the log's columns that a magnitude
+                          * sketch proves below the threshold before reducing it); 0 = auto: 8
+                          * for FP32 walks on matrices of more than six off-diagonals per row on
+                          * average, else 4 */
     const struct mcmi_proposal_s *proposal; /* learned proposal (mcmi_proposal_*), NULL = p_ij = |c_ij|/s_i */
 } mcmi_params;
 
@@ -111,7 +113,9 @@ typedef struct {
     int32_t max_len_bound;  /* no chain can take more transitions than this */
     int32_t table;          /* table type used */
     int32_t hash_log2;      /* accumulator slots used (log2) */
-    int64_t spilled;        /* distinct columns whose visits overflowed the on-chip table (reduced from the log) */
+    int64_t spilled;        /* distinct columns reduced from the overflow log (visits that did not fit on
+                             * chip); with tau, FP32 builds at load depth 8 first drop the log's columns
+                             * whose magnitude bound is below the threshold, and those are not counted */
     int64_t deferred_rows;  /* rows re-run because the first output buffer was full */
     float ms_prepare;       /* split + tables (CUDA events on the build stream) */
     float ms_walk;          /* walk stage incl. overflow-log set-up and deferred rows */

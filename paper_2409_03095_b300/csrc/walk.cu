@@ -39,6 +39,8 @@ namespace {
 
 constexpr int kProbeOnChip = 32;   // on-chip probe window before overflowing
 constexpr uint32_t kPartMul = 0x85EBCA77u;   // odd: col -> col * kPartMul permutes the 32-bit keys
+constexpr uint32_t kSketchMul = 0xC2B2AE35u;  // odd: cell of a column in the log's magnitude sketch
+constexpr uint32_t kSketchOne = 65536u;       // sketch units per lowthr
 
 __device__ __forceinline__ uint32_t hash_home(uint32_t key, int log2)
 {
@@ -199,12 +201,15 @@ __device__ __forceinline__ void load_slot(const uint4 *sp, uint32_t (&w)[16])
 // an FP32 walk with one chain per thread at 64 registers, so eight 128-thread
 // blocks (1024 chains) share an SM; DEPTH 8 needs 72 (seven blocks) but
 // halves the L2 round trips of those loops, which pays for rows that send
-// most of their visits through the overflow log.  FP64 walks take 72
-// registers at either depth rather than spill.
+// most of their visits through the overflow log, and its FP32 variant also
+// filters the log through a magnitude sketch before reducing it.  FP64 walks
+// take 72 registers at either depth rather than spill.
 template <int PREC, int TABLE, int ACC, bool DUMP, int CPT, int DEPTH>
 __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 64)) k_walk(WalkArgs a)
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
+    // log magnitude sketch (tau builds), in the variant for log-heavy rows
+    constexpr bool SKETCH = FIX && PREC == 32 && !DUMP && DEPTH == 8;
     // finished values and the filter work in the build's precision: FP32
     // builds use no FP64 instruction per entry (FP64 issues at a small
     // fraction of the FP32 rate)
@@ -619,6 +624,51 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     lowthr = (VT)__fmul_rd(__double2float_rd(a.tau), (float)rm);
                 }
             }
+            // Magnitude sketch (FP32 fixed-point builds with tau): the 2H value
+            // words of the emptied table become cells holding, per hash of the
+            // column, the sum of the log entries' magnitudes rounded up, in
+            // units of lowthr / 65536.  A column's finished |M_ij| is at most
+            // the sum of its entries' magnitudes (times 1 + 2^-22 for the
+            // finish's roundings), so a column whose cell stays below 65535
+            // units is under lowthr and can never pass the tau rule: its
+            // entries are neither bucketed nor reduced.
+            const bool sketch = SKETCH && lowthr > (VT)0;   // block-uniform
+            uint32_t *cells = s_lo;                         // s_lo, s_hi: 2H words
+            const int cell_shift = 32 - (a.log2H + 1);
+            if (sketch) {
+                for (int b = tid; b < 256; b += B) s_hist[b] = 0u;
+                const float qs = __fdiv_ru((float)kSketchOne, (float)lowthr);
+                for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
+                    uint2 key[UL];
+                    unsigned long long val[UL];
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) val[u] = key[u].x != kEmpty ? lv[e0 + u * B] : 0ull;
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) {
+                        if (key[u].x == kEmpty) continue;
+                        uint32_t *cell = &cells[(key[u].x * kSketchMul) >> cell_shift];
+                        if (*(volatile uint32_t *)cell >= kSketchOne - 1u) continue;   // already kept
+                        const long long x = (long long)val[u];
+                        const float m = __ull2float_ru((unsigned long long)(x < 0 ? -x : x));
+                        const float v = __fmul_ru(__fmul_ru(m, a.fin_scale), fabsf(__uint_as_float(key[u].y)));
+                        const float q = ceilf(__fmul_ru(v, qs));
+                        atomicAdd(cell, q < (float)kSketchOne ? (uint32_t)q : kSketchOne);   // NaN: kept
+                    }
+                }
+                __syncthreads();
+                for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
+                    uint32_t key[UL];
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B].x : kEmpty;
+#pragma unroll
+                    for (int u = 0; u < UL; ++u)
+                        if (key[u] != kEmpty && cells[(key[u] * kSketchMul) >> cell_shift] >= kSketchOne - 1u)
+                            atomicAdd(&s_hist[(key[u] * kPartMul) >> 24], 1u);
+                }
+                __syncthreads();
+            }
             // bucket starts: exclusive scan of the 256 counts (warp 0, 8 per lane)
             if (tid < 32) {
                 uint32_t c8[8], tot = 0;
@@ -652,6 +702,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 #pragma unroll
                 for (int u = 0; u < UL; ++u) {
                     if (key[u].x == kEmpty) continue;
+                    if (sketch && cells[(key[u].x * kSketchMul) >> cell_shift] < kSketchOne - 1u) continue;
                     const uint32_t p = atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
                     lc2[p] = key[u];
                     lv2[p] = val[u];
@@ -659,6 +710,10 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             }
             if (tid == 0) s_fill = 0;
             __syncthreads();
+            if (sketch) {   // the table's value words back to zero
+                for (int h = tid; h < 2 * H; h += B) cells[h] = 0u;
+                __syncthreads();
+            }
             // Buckets of at most 32 entries: one warp each.  Lanes holding the
             // same column find each other with __match_any_sync; the group's
             // lowest lane sums it in a per-warp scratch row of 64-bit words
