@@ -587,6 +587,7 @@ def run_batched(a):
     Ms, st = mc.mcmi_build_batched(Bs, p)          # warm-up with the autotuner
     del Ms
     p.threads, p.chains_per_thread, p.hash_log2, p.table = st.threads, st.chains_per_thread, st.hash_log2, st.table
+    p.load_depth = st.load_depth
     for _ in range(max(0, a.warmup - 1)):
         Ms, st = mc.mcmi_build_batched(Bs, p)
         del Ms
@@ -630,7 +631,8 @@ def run_batched(a):
                        "rows": int(st.rows), "rows_per_s": st.rows * a.steps * world / (tot_ms / 1e3),
                        "steps_per_build": int(st.steps), "generation_s": gen_s,
                        "autotuned": {"threads": st.threads, "chains_per_thread": st.chains_per_thread,
-                                     "hash_log2": st.hash_log2, "table": ["cumulative", "alias", "hybrid"][st.table]},
+                                     "hash_log2": st.hash_log2, "table": ["cumulative", "alias", "hybrid"][st.table],
+                                     "load_depth": st.load_depth},
                        "walk_ms": float(np.median(walk_ms)), "l2": "flushed between timed steps (256 MiB write)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_walk (batched)",

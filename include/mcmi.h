@@ -160,8 +160,9 @@ typedef struct {
 } mcmi_tune_result;
 
 /* Autotuner: times the walk kernel (CUDA events; each configuration twice,
- * the faster launch counts) on a contiguous sample of about 1/32 of the rows
- * (8192 to 65536 rows, from the middle of the build's row range): first the
+ * the faster launch counts) on a sample of about 1/32 of the rows (8192 to
+ * 65536 rows, in 32 windows spread evenly over the build's row range; a
+ * batch's block-diagonal matrix mixes very different matrices): first the
  * default plan (p as given, its 0 fields auto), then every launch shape
  * (threads per block 64/128/256, 1 or 2 chains per thread) and on-chip
  * accumulator size (2^9 .. 2^13 slots) for each table type (all three when

@@ -444,18 +444,19 @@ void reset_queue(DevState *st, cudaStream_t s)
     cudaMemsetAsync(&st->work, 0, sizeof(unsigned long long), s);
 }
 
-// One timed walk launch over rows [rb, re) with plan W (autotuner trial).
-mcmi_status time_walk(const mcmi_params *p, const Prepared &P, WalkPlan W, int64_t rb, int64_t re,
+// One timed walk launch over the rows of a device list with plan W
+// (autotuner trial).
+mcmi_status time_walk(const mcmi_params *p, const Prepared &P, WalkPlan W, const int64_t *list, int64_t rows,
                       cudaStream_t s, float *ms)
 {
     Scratch S(s);
     WalkArgs a;
     fill_walk_args(a, p, P, W);
-    a.row_begin = rb;
-    a.row_end = re;
+    a.row_list = list;
+    a.n_list = rows;
+    a.out_by_row = 0;
     mcmi_status r = alloc_overflow(S, W, P, false, a);
     if (r != MCMI_OK) return r;
-    const int64_t rows = re - rb;
     const uint64_t per_row = p->top_k > 0 ? (uint64_t)(p->top_k + 1) : 512;
     a.st_cap = (uint64_t)rows * per_row + 1024;
     a.st_col = S.get<uint32_t>(a.st_cap);
@@ -495,21 +496,38 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
     const int64_t re0 = (p->row_begin == 0 && p->row_end == 0) ? n : p->row_end;
     if (rb0 < 0 || re0 <= rb0 || re0 > n) return fail(MCMI_ERR_ARG, "bad row range");
     cudaStream_t s = (cudaStream_t)stream;
-    // sample: a contiguous window of about 1/32 of the rows in the middle,
-    // 8192 .. 65536 rows (several rows per resident block, so that the last
-    // rows' tail does not decide a trial)
-    int64_t ns = (re0 - rb0) / 32;
+    // sample: about 1/32 of the rows, 8192 .. 65536 (several rows per
+    // resident block, so that the last rows' tail does not decide a trial),
+    // in 32 equal windows spread evenly over the row range (a batch's
+    // block-diagonal matrix mixes very different matrices)
+    const int64_t range = re0 - rb0;
+    int64_t ns = range / 32;
     ns = ns < 8192 ? 8192 : (ns > 65536 ? 65536 : ns);
-    if (ns > re0 - rb0) ns = re0 - rb0;
-    const int64_t sb = rb0 + (re0 - rb0 - ns) / 2, se = sb + ns;
+    if (ns > range) ns = range;
+    std::vector<int64_t> hrows((size_t)ns);
+    {
+        const int64_t nwin = ns < 32 ? 1 : 32, wlen = ns / nwin;
+        int64_t k = 0;
+        for (int64_t w = 0; w < nwin; ++w) {
+            const int64_t len = w == nwin - 1 ? ns - k : wlen;
+            const int64_t start = rb0 + (nwin == 1 ? 0 : (range - len) * w / (nwin - 1));
+            for (int64_t j = 0; j < len; ++j) hrows[(size_t)k++] = start + j;
+        }
+    }
+    Scratch SL(s);
+    int64_t *sample = SL.get<int64_t>((size_t)ns);
+    if (SL.err != cudaSuccess) return cuda_fail(SL.err, "allocation (autotune sample)");
+    cudaError_t ce = cudaMemcpyAsync(sample, hrows.data(), (size_t)ns * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "autotune sample copy");
     int trials = 0;
     // one configuration: the faster of two launches on the sample
     auto trial = [&](const mcmi_params &q, const Prepared &P, WalkPlan &W, float *ms, bool *fits) -> mcmi_status {
         *fits = plan_walk(&q, P, ns, false, W) == MCMI_OK;
         if (!*fits) return MCMI_OK;
         float t0 = 0.0f, t1 = 0.0f;
-        mcmi_status rr = time_walk(&q, P, W, sb, se, s, &t0);
-        if (rr == MCMI_OK) rr = time_walk(&q, P, W, sb, se, s, &t1);
+        mcmi_status rr = time_walk(&q, P, W, sample, ns, s, &t0);
+        if (rr == MCMI_OK) rr = time_walk(&q, P, W, sample, ns, s, &t1);
         *ms = t0 < t1 ? t0 : t1;
         ++trials;
         return rr;

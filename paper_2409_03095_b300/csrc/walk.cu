@@ -535,9 +535,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // batch instead of one per element.
         constexpr int UF = DEPTH, UL = DEPTH / 2;
         VT lmax = (VT)0;   // largest |M_ij| this thread has finished
-        // Entries of the log below lowthr can never pass the tau rule: lowthr
-        // is tau times a lower bound of the row maximum, rounded down, so the
-        // entry list keeps only possible candidates (0: keep everything).
+        // Entries of the log below lowthr can never be kept: lowthr is tau
+        // times a lower bound of the row maximum, rounded down, or with top-k
+        // a lower bound of the k-th largest off-diagonal magnitude, whichever
+        // is larger, so the entry list keeps only possible candidates (0: keep
+        // everything).
         VT lowthr = (VT)0;
         uint32_t nred = 0;   // distinct log columns this thread reduced (statistics)
         // Finishes the on-chip entries, in place, or appended to the entry
@@ -624,14 +626,35 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     lowthr = (VT)__fmul_rd(__double2float_rd(a.tau), (float)rm);
                 }
             }
-            // Magnitude sketch (FP32 fixed-point builds with tau): the 2H value
+            if (!DUMP && PREC == 32 && a.top_k > 0 && a.top_k < B) {
+                // top-k bound: the (k+1)-th largest of the threads' maxima over
+                // the on-chip entries.  At least k + 1 distinct entries reach
+                // it, at most one of them the diagonal, so the row's k-th
+                // largest off-diagonal |M_ij| does too: an entry below it is
+                // not selected (or fails tau, if fewer than k pass).
+                __syncthreads();
+                s_bstart[tid] = __float_as_uint((float)lmax);   // |v| >= 0: bit order is value order
+                __syncthreads();
+                const uint32_t mine = s_bstart[tid];
+                int rank = 0;
+                for (int u = 0; u < B; ++u) {
+                    const uint32_t o = s_bstart[u];
+                    rank += (o > mine) || (o == mine && u < tid);
+                }
+                if (rank == a.top_k) s_digit = mine;
+                __syncthreads();
+                const float kb = __uint_as_float(s_digit);
+                if (kb > (float)lowthr) lowthr = (VT)kb;
+                __syncthreads();
+            }
+            // Magnitude sketch (FP32 fixed-point builds with tau or top-k): the 2H value
             // words of the emptied table become cells holding, per hash of the
             // column, the sum of the log entries' magnitudes rounded up, in
             // units of lowthr / 65536.  A column's finished |M_ij| is at most
             // the sum of its entries' magnitudes (times 1 + 2^-22 for the
             // finish's roundings), so a column whose cell stays below 65535
-            // units is under lowthr and can never pass the tau rule: its
-            // entries are neither bucketed nor reduced.
+            // units is under lowthr and can never be kept: its entries are
+            // neither bucketed nor reduced.
             const bool sketch = SKETCH && lowthr > (VT)0;   // block-uniform
             uint32_t *cells = s_lo;                         // s_lo, s_hi: 2H words
             const int cell_shift = 32 - (a.log2H + 1);

@@ -268,26 +268,31 @@ def test_build_through_the_overflow_log():
         for tau, k in [(5e-3, 0), (0.0, 8)]:
             M, *_ = _check_build(m, rows, 128, 256, 1e-3, tau, k, prec=prec, extra={"hash_log2": log2h},
                                  seed=17)
-            assert M.stats.spilled > 0
+            # with 2^11 slots the FP32 top-k build's sketch may prove every log column below the bound
+            if log2h <= 8 or prec == 64 or k == 0:
+                assert M.stats.spilled > 0
 
 
 def test_load_depth_leaves_the_result_unchanged():
-    """The load depth only batches the loads after the walks: builds at depth
-    4 and 8 are bit-identical (log-heavy rows, both precisions, 1 and 2
-    chains per thread); auto picks 8 only for FP32 on long-row matrices."""
+    """The load depth batches the loads after the walks, and the FP32 depth-8
+    variant drops log columns that a magnitude sketch proves below the tau or
+    top-k bound: builds at depth 4 and 8 are bit-identical (log-heavy rows,
+    both precisions, 1 and 2 chains per thread, tau, top-k and both); auto
+    picks 8 only for FP32 on long-row matrices."""
     m = _cases_small()["powerlaw_4k"]
     B = mc.DeviceCsr.from_host(m)
     for prec in (32, 64):
         for cpt in (1, 2):
-            out = {}
-            for depth in (4, 8):
-                p = mc.params(chains=128, max_len=256, delta=1e-3, filter_tau=5e-3, seed=17, precision=prec,
-                              hash_log2=8, chains_per_thread=cpt, load_depth=depth)
-                M = mc.mcmi_build_ex(B, p)
-                assert M.stats.load_depth == depth and M.stats.spilled > 0
-                out[depth] = [t.cpu().numpy() for t in M.to_torch()]
-            for u, v in zip(out[4], out[8]):
-                assert np.array_equal(u, v)
+            for tau, k in ((5e-3, 0), (0.0, 8), (1e-3, 24)):
+                out = {}
+                for depth in (4, 8):
+                    p = mc.params(chains=128, max_len=256, delta=1e-3, filter_tau=tau, top_k=k, seed=17,
+                                  precision=prec, hash_log2=8, chains_per_thread=cpt, load_depth=depth)
+                    M = mc.mcmi_build_ex(B, p)
+                    assert M.stats.load_depth == depth and (depth == 8 or M.stats.spilled > 0)
+                    out[depth] = [t.cpu().numpy() for t in M.to_torch()]
+                for u, v in zip(out[4], out[8]):
+                    assert np.array_equal(u, v)
     assert mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8)).stats.load_depth == 8
     assert mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8, precision=64)).stats.load_depth == 4
     S = mc.DeviceCsr.from_host(synth.stencil3d_7pt(8, seed=1))
