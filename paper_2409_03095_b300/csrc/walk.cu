@@ -922,8 +922,27 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             const double thr64 = use_tau ? __dmul_rn(a.tau, (double)rowmax) : 0.0;
             const VT thr = PREC == 64 ? (VT)thr64 : (VT)__double2float_ru(thr64);
             const uint32_t rowc = (uint32_t)row;
+            // top-k (FP32): only entries reaching kb, the (k+1)-th largest of
+            // the threads' maxima, can be selected (k + 1 distinct entries
+            // reach it, at most one the diagonal); the rest are not candidates
+            float kb = 0.0f;
+            if (PREC == 32 && a.top_k > 0 && a.top_k < B) {
+                __syncthreads();
+                s_bstart[tid] = __float_as_uint((float)lmax);
+                __syncthreads();
+                const uint32_t mine = s_bstart[tid];
+                int rank = 0;
+                for (int u = 0; u < B; ++u) {
+                    const uint32_t o = s_bstart[u];
+                    rank += (o > mine) || (o == mine && u < tid);
+                }
+                if (rank == a.top_k) s_digit = mine;
+                __syncthreads();
+                kb = __uint_as_float(s_digit);
+                __syncthreads();
+            }
             auto is_cand = [&](uint32_t k, VT v) -> bool {
-                return k != rowc && (!use_tau || fabs(v) >= thr);
+                return k != rowc && (!use_tau || fabs(v) >= thr) && (PREC != 32 || fabsf((float)v) >= kb);
             };
             // candidates: on-chip slot h as h, entry-list element e as H + e
             const uint32_t list_cap = (uint32_t)H;
