@@ -24,6 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 TABLE_CUMULATIVE = 0
 TABLE_ALIAS = 1
 TABLE_HYBRID = 2   # per row: cumulative for at most 6 transitions, alias for longer rows
+TABLE_COMPACT = 3  # cumulative sampling from weights at the scale 2^20 instead of 2^31
 
 
 def compile_lib(force: bool = False) -> str:
@@ -55,6 +56,8 @@ def _L():
         lib.orc_pick_alias_many.argtypes = [P, P, i64, u64, P, i64, P]
         lib.orc_tables.argtypes = [i64, P, P, P, P, P, P, P, P, P, P]
         lib.orc_tables.restype = i32
+        lib.orc_tables_ex.argtypes = [i64, P, P, P, P, P, i32, P, P, P, P, P]
+        lib.orc_tables_ex.restype = i32
         lib.orc_max_walk_len.argtypes = [f64, f64, i64]
         lib.orc_max_walk_len.restype = i64
         lib.orc_chains_from_eps.argtypes = [f64, f64]
@@ -123,9 +126,10 @@ def split(m, alpha: float = 0.0):
     return d, s
 
 
-def tables(m, d, s, alias: bool = False):
+def tables(m, d, s, alias: bool = False, table: int = TABLE_CUMULATIVE):
     """Integer sampling tables of every row (p of Eq. 2 as integers).
-    Returns dict(off, Q, q[, prob, alias]) over off-diagonals in CSR order."""
+    Returns dict(off, Q, q[, prob, alias]) over off-diagonals in CSR order;
+    table=TABLE_COMPACT gives the weights at the scale 2^20."""
     rp, col, val = _csr(m)
     noff = int(rp[-1]) - int(np.sum(col == np.repeat(np.arange(m.n), np.diff(rp))))
     off = np.zeros(m.n + 1, dtype=np.int64)
@@ -133,9 +137,9 @@ def tables(m, d, s, alias: bool = False):
     q = np.zeros(max(noff, 1), dtype=np.uint32)
     prob = np.zeros(max(noff, 1), dtype=np.uint32) if alias else None
     al = np.zeros(max(noff, 1), dtype=np.int32) if alias else None
-    _L().orc_tables(m.n, _p(rp), _p(col), _p(val), _p(np.ascontiguousarray(d)),
-                    _p(np.ascontiguousarray(s)), _p(off), _p(Q), _p(q),
-                    _p(prob) if alias else None, _p(al) if alias else None)
+    _L().orc_tables_ex(m.n, _p(rp), _p(col), _p(val), _p(np.ascontiguousarray(d)),
+                       _p(np.ascontiguousarray(s)), int(table), _p(off), _p(Q), _p(q),
+                       _p(prob) if alias else None, _p(al) if alias else None)
     out = dict(off=off, Q=Q, q=q[:noff])
     if alias:
         out["prob"] = prob[:noff]

@@ -13,7 +13,9 @@
  *     s_i = ||c_i||_1 summed in CSR order;
  *   - the transition probabilities p_ij = |c_ij| / s_i (the p of Eq. 2), held
  *     as integer weights q_ij = max(1, floor(p_ij 2^31)) (0 for c_ij == 0)
- *     so that every sampled transition is an integer decision;
+ *     so that every sampled transition is an integer decision (the compact
+ *     table type uses the scale 2^20 instead of 2^31, so that a row of at
+ *     most six transitions fits a 32-byte record on the GPU);
  *   - the estimator of Eq. 2: N chains per row r, each starting at r with
  *     weight 1 (the empty product, j = 0 term), moving r -> s1 -> s2 ... with
  *     probability p, multiplying the weight by a/p = sign(c) s, and adding
@@ -45,7 +47,14 @@
 
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_BAD_CSR = 2, ORC_ERR_ZERO_DIAG = 3,
        ORC_ERR_NOT_CONTRACTIVE = 4, ORC_ERR_CAPACITY = 5 };
-enum { ORC_TABLE_CUMULATIVE = 0, ORC_TABLE_ALIAS = 1, ORC_TABLE_HYBRID = 2 };
+enum { ORC_TABLE_CUMULATIVE = 0, ORC_TABLE_ALIAS = 1, ORC_TABLE_HYBRID = 2, ORC_TABLE_COMPACT = 3 };
+
+/* Scale of the integer weights: 2^31, or 2^20 for the compact table (which */
+/* samples cumulatively, like ORC_TABLE_CUMULATIVE, from the coarser q).    */
+static double table_scale(int table)
+{
+    return table == ORC_TABLE_COMPACT ? 1048576.0 : 2147483648.0;
+}
 
 /* The hybrid table chooses per row: rows with at most ORC_HYBRID_CUM_MAX
  * transitions sample from the cumulative table, longer rows from the alias
@@ -118,27 +127,28 @@ int orc_split(int64_t n, const int64_t *rp, const int32_t *col, const double *va
     return ORC_OK;
 }
 
-/* Integer weight of one off-diagonal entry: q = max(1, floor(|c|/s * 2^31)),  */
-/* 0 for an entry whose c is exactly zero (never sampled).                    */
-static uint32_t weight_of(double b, double di, double si)
+/* Integer weight of one off-diagonal entry: q = max(1, floor(|c|/s * scale)), */
+/* scale = 2^31 (2^20 compact), 0 for an entry whose c is exactly zero (never */
+/* sampled).                                                                */
+static uint32_t weight_of(double b, double di, double si, double scale)
 {
     double c = -b / di;
     if (c == 0.0) return 0u;
-    double x = floor(fabs(c) / si * 2147483648.0);
+    double x = floor(fabs(c) / si * scale);
     uint32_t q = (uint32_t)x;
     return q < 1u ? 1u : q;
 }
 
 /* Row i's off-diagonal weights in CSR order; returns the degree.           */
 static int64_t row_weights(int64_t i, const int64_t *rp, const int32_t *col, const double *val,
-                           const double *d, const double *s, uint32_t *q, int32_t *cols,
+                           const double *d, const double *s, double scale, uint32_t *q, int32_t *cols,
                            uint8_t *neg, uint64_t *Q)
 {
     int64_t m = 0;
     uint64_t tot = 0;
     for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
         if (col[k] == i) continue;
-        uint32_t w = s[i] > 0.0 ? weight_of(val[k], d[i], s[i]) : 0u;
+        uint32_t w = s[i] > 0.0 ? weight_of(val[k], d[i], s[i], scale) : 0u;
         if (q) q[m] = w;
         if (cols) cols[m] = col[k];
         if (neg) neg[m] = (-val[k] / d[i]) < 0.0;
@@ -216,20 +226,29 @@ void orc_pick_alias_many(const uint32_t *prob, const int32_t *alias, int64_t deg
 
 /* Per-row integer tables, for the table-parity tests.  Output per row i:    */
 /* Q[i]; per off-diagonal entry (in CSR order, offsets off[i]):            */
-/* q, and for the alias table prob and alias (row-local index).            */
-int orc_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
-               const double *d, const double *s, int64_t *off, uint64_t *Q,
-               uint32_t *q, uint32_t *prob, int32_t *alias)
+/* q, and for the alias table prob and alias (row-local index).  table     */
+/* selects the scale of q (ORC_TABLE_COMPACT: 2^20).                       */
+int orc_tables_ex(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+                  const double *d, const double *s, int table, int64_t *off, uint64_t *Q,
+                  uint32_t *q, uint32_t *prob, int32_t *alias)
 {
     int64_t o = 0;
+    const double scale = table_scale(table);
     for (int64_t i = 0; i < n; ++i) {
         off[i] = o;
-        int64_t deg = row_weights(i, rp, col, val, d, s, q + o, NULL, NULL, &Q[i]);
+        int64_t deg = row_weights(i, rp, col, val, d, s, scale, q + o, NULL, NULL, &Q[i]);
         if (prob && alias && deg > 0) orc_alias_build(q + o, deg, Q[i], prob + o, alias + o);
         o += deg;
     }
     off[n] = o;
     return ORC_OK;
+}
+
+int orc_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val,
+               const double *d, const double *s, int64_t *off, uint64_t *Q,
+               uint32_t *q, uint32_t *prob, int32_t *alias)
+{
+    return orc_tables_ex(n, rp, col, val, d, s, ORC_TABLE_CUMULATIVE, off, Q, q, prob, alias);
 }
 
 /* Longest possible chain: every factor is at most fl32(max_i s_i) in        */
@@ -472,7 +491,8 @@ static int mat_prepare(orc_mat *M, int table)
         int64_t deg = M->theta
                           ? row_weights_learned(i, M->rp, M->col, M->val, M->d, M->s, degs, M->theta, M->q + o,
                                                 M->ocol + o, M->neg + o, M->fac + o, NULL, &M->Q[i])
-                          : row_weights(i, M->rp, M->col, M->val, M->d, M->s, M->q + o, M->ocol + o, M->neg + o,
+                          : row_weights(i, M->rp, M->col, M->val, M->d, M->s, table_scale(table), M->q + o,
+                                        M->ocol + o, M->neg + o,
                                         &M->Q[i]);
         if (uses_alias(table, deg) && deg > 0)
             orc_alias_build(M->q + o, deg, M->Q[i], M->prob + o, M->alias + o);

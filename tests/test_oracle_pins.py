@@ -113,6 +113,32 @@ def test_table_weights_follow_transition_probabilities(orc):
         assert np.all(np.abs(q / Q - p) <= (len(q) + 1) / Q)
 
 
+def test_compact_table_weights(orc):
+    """The compact table's weights at the scale 2^20: against the dense
+    transition probabilities, and against the 2^31 table (dropping 11 bits
+    of floor(x 2^31) is floor(x 2^20); both floor at 1 and keep zeros)."""
+    m = synth.random_dd(60, 6, seed=6, zero_frac=0.15, diag_sign="mixed")
+    d, s = orc.split(m)
+    tc = orc.tables(m, d, s, table=orc.TABLE_COMPACT)
+    t31 = orc.tables(m, d, s)
+    assert np.array_equal(tc["off"], t31["off"])
+    q31 = t31["q"].astype(np.int64)
+    want = np.where(q31 == 0, 0, np.maximum(1, q31 >> 11))
+    assert np.array_equal(tc["q"].astype(np.int64), want)
+    B = m.to_scipy().toarray()
+    C = np.eye(m.n) - B / np.diag(B)[:, None]
+    for i in range(m.n):
+        a, b = tc["off"][i], tc["off"][i + 1]
+        q = tc["q"][a:b].astype(np.float64)
+        cols = [c for c in m.col[m.row_ptr[i]:m.row_ptr[i + 1]] if c != i]
+        p = np.abs(C[i, cols]) / np.abs(C[i]).sum()
+        Q = int(tc["Q"][i])
+        assert Q == int(tc["q"][a:b].astype(np.uint64).sum())
+        assert abs(Q - 2**20) <= len(q) and Q < 2**21
+        assert np.all((q == 0) == (p == 0))
+        assert np.all(np.abs(q / Q - p) <= (len(q) + 1) / Q)
+
+
 def test_cumulative_pick_boundaries_are_exact(orc):
     rng = np.random.default_rng(0)
     for trial in range(30):
@@ -317,13 +343,14 @@ def test_path_enumeration_reproduces_neumann_powers(orc):
         assert np.allclose(EY, P[i], rtol=1e-12, atol=1e-14)
 
 
-@pytest.mark.parametrize("delta,L,table", [(0.0, 4, 0), (0.2, 6, 0), (0.05, 5, 1)])
+@pytest.mark.parametrize("delta,L,table", [(0.0, 4, 0), (0.2, 6, 0), (0.05, 5, 1), (0.05, 5, 3)])
 def test_estimator_mean_matches_exact_expectation(orc, delta, L, table):
     """z-scores of the oracle's Eq. 2 estimate against the exact expectation
-    and variance from path enumeration (n = 5)."""
+    and variance from path enumeration (n = 5), with the probabilities q/Q
+    of the table the walks sample (the compact table's are coarser)."""
     m = synth.random_dd(5, 3, seed=21, dominance=0.85, diag_sign="mixed")
     d, s = orc.split(m)
-    tb = orc.tables(m, d, s)
+    tb = orc.tables(m, d, s, table=table if table == 3 else 0)
     N = 200_000
     res, _, _ = orc.walk(m, chains=N, max_len=L, delta=delta, seed=77, table=table)
     worst = 0.0
@@ -401,16 +428,18 @@ def test_first_steps_follow_the_table(orc):
         assert chi2 < 40.0, chi2      # 11 d.o.f.: p ~ 4e-5
 
 
-def test_python_rewalk_of_a_few_chains(orc):
+@pytest.mark.parametrize("table", [0, 3])
+def test_python_rewalk_of_a_few_chains(orc, table):
     """Brute force: re-walk two chains in Python from the oracle's Philox
-    and numpy's searchsorted, and compare the visit counts."""
+    and numpy's searchsorted, and compare the visit counts (cumulative and
+    compact tables)."""
     m = synth.random_dd(12, 4, seed=23, dominance=0.8, diag_sign="mixed")
     d, s = orc.split(m)
-    tb = orc.tables(m, d, s)
+    tb = orc.tables(m, d, s, table=table)
     C, _ = _dense_C(m)
     seed, delta, L, N = 0xDEADBEEF12345, 1e-2, 30, 2
     key = [seed & 0xFFFFFFFF, seed >> 32]
-    res, _, _ = orc.walk(m, rows=[5], chains=N, max_len=L, delta=delta, seed=seed)
+    res, _, _ = orc.walk(m, rows=[5], chains=N, max_len=L, delta=delta, seed=seed, table=table)
     V = np.zeros(m.n, dtype=np.int64)
     X = np.zeros(m.n)
     for k in range(N):
