@@ -231,13 +231,27 @@ def _cpu_baseline(m, w, seconds, table):
             "rows_per_s": nrows / dt}
 
 
+def _auto_table(m):
+    """The library's automatic table choice (FIXED64 accumulator, |c|
+    proposal), from the host copy of the matrix: compact when every row has
+    at most six off-diagonals within |j - i| <= 16383, else cumulative for at
+    most six off-diagonals per row on average, else hybrid."""
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    off = m.col != rows
+    deg = np.bincount(rows[off], minlength=m.n)
+    far = np.abs(m.col[off].astype(np.int64) - rows[off]).max(initial=0)
+    if deg.max(initial=0) <= 6 and far <= 16383:
+        return 3
+    return 0 if int(off.sum()) <= 6 * m.n else 2
+
+
 def run_reference(a):
     world, rank, _ = _dist()
     if rank != 0:
         return 0
     import oracle
     m, w = synth.workload(a.workload)
-    table = 0 if (m.nnz - m.n) <= 6 * m.n else 1
+    table = _auto_table(m)
     cores = os.cpu_count() or 1
     budget = 150.0 / max(1, a.steps + a.warmup)
 
@@ -386,6 +400,10 @@ def run_ours(a):
         return 0
     peaks, peak_src = _peaks()
     walk_total_ms = sum(walk_ms)
+    # algorithmic bytes: two 32-B sectors per visited state (the row's header
+    # and its sampled transition in separate sectors); the compact table's
+    # 32-byte record holds both in one sector, so that kernel reads half
+    rec_bytes = 32 if last.table == mc.TABLE_COMPACT else SLOT_BYTES   # bytes of one row record
     alg_bytes = SLOT_BYTES * visits
     achieved = alg_bytes / (walk_total_ms / 1e3) / 1e9
     traffic = _traffic(os.path.join(ROOT, "paper_2409_03095_b300", "csrc", "walk.cu"))
@@ -394,20 +412,26 @@ def run_ours(a):
             "kernel": "k_walk (walk + accumulate + filter)",
             "peak_source": f"{peak_src} HBM copy bandwidth",
             "algorithmic_bytes_per_launch": alg_bytes / max(1, len(walk_ms)),
-            "bytes_per_unit": "64 B (one 64-B row record, two 32-B sectors) per visited state",
+            "bytes_per_unit": ("64 B (two 32-B sectors: the row header and the sampled transition) per visited "
+                               f"state; the {mc.TABLE_NAMES[last.table]} table's records are {rec_bytes} B"),
             "walk_kernel_ms": walk_total_ms / max(1, len(walk_ms)),
             "walk_share_of_step": walk_total_ms / tot_ms if world == 1 else None}
-    # gather roofline (one 64-B row record per visited state): dependent
-    # random 64-B record reads over a buffer the size of the row records, at
-    # the walk's launch shape and at full occupancy (outside the timed region)
-    foot = SLOT_BYTES * m.n
+    # gather roofline (one row record per visited state): dependent random
+    # reads of records of the table's size over a buffer the size of the row
+    # records, at the walk's launch shape and at full occupancy (outside the
+    # timed region); with compact records also the 64-byte records' ceiling
+    foot = rec_bytes * m.n
     try:
-        g_walk = mc.mcmi_gather_roofline(foot, 128, 8, 64)   # the walk's 8 blocks of 128 threads per SM
-        g_full = mc.mcmi_gather_roofline(foot, 256, 8, 64)
+        g_walk = mc.mcmi_gather_roofline(foot, 128, 8, 64, record_bytes=rec_bytes)   # 8 blocks of 128 threads per SM
+        g_full = mc.mcmi_gather_roofline(foot, 256, 8, 64, record_bytes=rec_bytes)
         visits_per_s = visits / (walk_total_ms / 1e3)
-        roof["gather"] = {"footprint_bytes": foot, "records_per_s_walk_shape": g_walk,
+        roof["gather"] = {"record_bytes": rec_bytes, "footprint_bytes": foot, "records_per_s_walk_shape": g_walk,
                           "records_per_s_full_occupancy": g_full, "walk_visits_per_s": visits_per_s,
                           "frac_walk_shape": visits_per_s / g_walk, "frac_full_occupancy": visits_per_s / g_full}
+        if rec_bytes != SLOT_BYTES:
+            g64 = mc.mcmi_gather_roofline(SLOT_BYTES * m.n, 128, 8, 64, record_bytes=SLOT_BYTES)
+            roof["gather"]["records_per_s_64B_records_walk_shape"] = g64
+            roof["gather"]["frac_of_64B_record_ceiling"] = visits_per_s / g64
     except Exception as exc:  # measurement only
         roof["gather"] = {"error": str(exc)}
     cpu = None
@@ -430,7 +454,7 @@ def run_ours(a):
             "vs_baseline": None, "dtype": "f64" if a.precision == 64 else "f32", "data": "synthetic",
             "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "rows": last.rows,
                        "rows_per_s": rows_per_s, "chains": last.chains,
-                       "table": ["cumulative", "alias", "hybrid"][last.table],
+                       "table": mc.TABLE_NAMES[last.table],
                        "nnz_M": last.nnz, "steps_per_build": last.steps, "max_len_bound": last.max_len_bound,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"rows on one GPU; {world} independent builds (one per GPU)",
@@ -623,7 +647,8 @@ def run_batched(a):
         return 0
     peaks, peak_src = _peaks()
     visits = steps + 128 * st.rows * a.steps
-    achieved = SLOT_BYTES * visits / (sum(walk_ms) / 1e3) / 1e9
+    rec_bytes = 32 if st.table == mc.TABLE_COMPACT else SLOT_BYTES
+    achieved = rec_bytes * visits / (sum(walk_ms) / 1e3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -631,13 +656,13 @@ def run_batched(a):
                        "rows": int(st.rows), "rows_per_s": st.rows * a.steps * world / (tot_ms / 1e3),
                        "steps_per_build": int(st.steps), "generation_s": gen_s,
                        "autotuned": {"threads": st.threads, "chains_per_thread": st.chains_per_thread,
-                                     "hash_log2": st.hash_log2, "table": ["cumulative", "alias", "hybrid"][st.table],
+                                     "hash_log2": st.hash_log2, "table": mc.TABLE_NAMES[st.table],
                                      "load_depth": st.load_depth},
                        "walk_ms": float(np.median(walk_ms)), "l2": "flushed between timed steps (256 MiB write)"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                          "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_walk (batched)",
                          "peak_source": f"{peak_src} HBM copy bandwidth",
-                         "bytes_per_unit": "64 B per visited state"},
+                         "bytes_per_unit": f"{rec_bytes} B per visited state"},
             "cpu_baseline": None, "e2e": None, "gpu_launches": launches, "clocks": ck}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -55,10 +55,16 @@ typedef enum {
 
 /* Sampling table of the transition probabilities p_ij = |c_ij| / s_i.    */
 enum {
-    MCMI_TABLE_AUTO = -1,       /* pick from the degree distribution */
-    MCMI_TABLE_CUMULATIVE = 0,  /* integer cumulative thresholds */
+    MCMI_TABLE_AUTO = -1,       /* compact when every row fits it (and the accumulator is
+                                 * FIXED64, no learned proposal); else cumulative for at most
+                                 * six off-diagonals per row on average, hybrid otherwise */
+    MCMI_TABLE_CUMULATIVE = 0,  /* integer cumulative thresholds (weights at the scale 2^31) */
     MCMI_TABLE_ALIAS = 1,       /* integer Walker/Vose alias buckets */
-    MCMI_TABLE_HYBRID = 2       /* per row: cumulative for at most 6 transitions (inline), alias otherwise */
+    MCMI_TABLE_HYBRID = 2,      /* per row: cumulative for at most 6 transitions (inline), alias otherwise */
+    MCMI_TABLE_COMPACT = 3      /* cumulative thresholds at the scale 2^20 in one 32-byte record per
+                                 * row (half the gather bytes of the 64-byte records); every row must
+                                 * have at most 6 off-diagonals, each with |j - i| <= 16383, and the
+                                 * accumulator must be FIXED64 (else MCMI_ERR_ARG) */
 };
 
 /* Row accumulator of the walk kernel.                                    */
@@ -165,8 +171,9 @@ typedef struct {
  * batch's block-diagonal matrix mixes very different matrices): first the
  * default plan (p as given, its 0 fields auto), then every launch shape
  * (threads per block 64/128/256, 1 or 2 chains per thread) and on-chip
- * accumulator size (2^9 .. 2^13 slots) for each table type (all three when
- * p->table is MCMI_TABLE_AUTO), then the best of those at the other load
+ * accumulator size (2^9 .. 2^13 slots) for each table type (all four when
+ * p->table is MCMI_TABLE_AUTO; compact only where the rows fit it and the
+ * accumulator is FIXED64), then the best of those at the other load
  * depth.  The best trial replaces the default plan only when it is at least
  * 2% faster.  Writes the choice into p->threads, p->chains_per_thread,
  * p->hash_log2, p->table and p->load_depth.  p: in/out (host); res: optional
@@ -371,16 +378,18 @@ mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *o
 
 /* Gather roofline probe (measurement; the walk's access pattern without its
  * arithmetic).  Fills a device buffer of footprint_bytes with random
- * 64-byte records, then every thread of blocks_per_sm x SMs blocks of
- * threads_per_block threads follows two chains of `steps` dependent random
- * record reads (two 256-bit loads per record, the next index taken from the
+ * records of record_bytes (64: the 64-byte records, two 256-bit loads each;
+ * 32: the compact table's records, one 256-bit load), then every thread of
+ * blocks_per_sm x SMs blocks of threads_per_block threads follows two chains
+ * of `steps` dependent random record reads (the next index taken from the
  * record read).  *records_per_s (host) receives the rate, timed with CUDA
  * events on `stream`.  Allocates and frees its buffer stream-ordered;
- * synchronises `stream`.  Errors: MCMI_ERR_ARG (footprint < 4096, bad
- * launch shape), MCMI_ERR_OOM, MCMI_ERR_CUDA.  The paper names random
- * memory access as the method's limiter (Sec. I, Sec. IV-B).             */
-mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int threads_per_block, int blocks_per_sm,
-                                 int steps, double *records_per_s, void *stream);
+ * synchronises `stream`.  Errors: MCMI_ERR_ARG (footprint < 4096,
+ * record_bytes not 32 or 64, bad launch shape), MCMI_ERR_OOM, MCMI_ERR_CUDA.
+ * The paper names random memory access as the method's limiter (Sec. I,
+ * Sec. IV-B).                                                            */
+mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int record_bytes, int threads_per_block,
+                                 int blocks_per_sm, int steps, double *records_per_s, void *stream);
 
 /* ---------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a

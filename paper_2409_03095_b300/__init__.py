@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_PKG, "libmcmi.so")
 MCMI_OK = 0
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_BAD_CSR", 3: "ERR_ZERO_DIAG", 4: "ERR_NOT_CONTRACTIVE",
           5: "ERR_OOM", 6: "ERR_CUDA", 7: "ERR_TIMEOUT", 8: "ERR_CAPACITY"}
-TABLE_AUTO, TABLE_CUMULATIVE, TABLE_ALIAS, TABLE_HYBRID = -1, 0, 1, 2
+TABLE_AUTO, TABLE_CUMULATIVE, TABLE_ALIAS, TABLE_HYBRID, TABLE_COMPACT = -1, 0, 1, 2, 3
+TABLE_NAMES = {0: "cumulative", 1: "alias", 2: "hybrid", 3: "compact"}
 ACC_FIXED64, ACC_KAHAN32 = 0, 1
 
 
@@ -96,7 +97,7 @@ def load():
     lib.mcmi_walk_dump.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, i64, i64, P, P, P, P, P, P]
     lib.mcmi_debug_tables.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, P, P, P, P, P, P]
     lib.mcmi_exclusive_scan_noalloc.argtypes = [P, i64, P, P]
-    lib.mcmi_gather_roofline.argtypes = [u64, i32, i32, i32, C.POINTER(f64), P]
+    lib.mcmi_gather_roofline.argtypes = [u64, i32, i32, i32, i32, C.POINTER(f64), P]
     lib.mcmi_gather_roofline.restype = C.c_int
     lib.mcmi_solve.argtypes = [C.POINTER(mcmi_csr), P, P, P, C.c_int, f64, i32, i32, C.POINTER(i32), C.POINTER(f64), P]
     lib.mcmi_solve.restype = C.c_int
@@ -344,7 +345,10 @@ def mcmi_debug_tables(B: DeviceCsr, p: mcmi_params, stream=None):
                                     _ptr(c), _stream(stream)))
     torch.cuda.synchronize()
     u = lambda t: t.cpu().numpy().view(np.uint32)
-    return dict(d=d.cpu().numpy(), s=s.cpu().numpy(), slot=u(slot).reshape(n, 16), a=u(a), b=u(b), c=u(c))
+    out = dict(d=d.cpu().numpy(), s=s.cpu().numpy(), slot=u(slot).reshape(n, 16), a=u(a), b=u(b), c=u(c))
+    # the compact table's 32-byte records are packed at the start
+    out["rec32"] = u(slot)[:8 * n].reshape(n, 8)
+    return out
 
 
 def mcmi_exclusive_scan_noalloc(counts, offsets, stream=None):
@@ -432,12 +436,14 @@ def mcmi_solve(B: DeviceCsr, M, b, x, method=SOLVE_BICGSTAB, rtol=1e-8, maxit=10
     return it.value, rr.value
 
 
-def mcmi_gather_roofline(footprint_bytes, threads_per_block=128, blocks_per_sm=6, steps=64, stream=None):
-    """Random dependent 64-byte record reads per second over a buffer of the
-    given size at the given occupancy (the walk's access pattern)."""
+def mcmi_gather_roofline(footprint_bytes, threads_per_block=128, blocks_per_sm=6, steps=64, stream=None,
+                         record_bytes=64):
+    """Random dependent record reads (64- or 32-byte records) per second over
+    a buffer of the given size at the given occupancy (the walk's access
+    pattern)."""
     r = C.c_double()
-    _check(load().mcmi_gather_roofline(int(footprint_bytes), threads_per_block, blocks_per_sm, steps, C.byref(r),
-                                       _stream(stream)))
+    _check(load().mcmi_gather_roofline(int(footprint_bytes), int(record_bytes), threads_per_block, blocks_per_sm,
+                                       steps, C.byref(r), _stream(stream)))
     return r.value
 
 

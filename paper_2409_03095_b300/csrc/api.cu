@@ -173,6 +173,7 @@ struct Prepared {
     uint32_t *a = nullptr, *b = nullptr, *c = nullptr;
     uint4 *bkt = nullptr;
     uint4 *lbkt = nullptr;       // learned proposal: 32-byte buckets
+    float *invd32 = nullptr;     // compact table: fl32(1/d_i)
     bool learned = false;
     double2 *rowd = nullptr;
     double smax = 0.0, smin = 0.0;
@@ -200,7 +201,11 @@ mcmi_status check_params(const mcmi_params *p)
     if (p->chains < 0 || p->max_len < 0 || p->top_k < 0) return fail(MCMI_ERR_ARG, "negative count");
     if (p->chains == 0 && !(p->eps > 0.0)) return fail(MCMI_ERR_ARG, "chains == 0 needs eps > 0");
     if (p->precision != 32 && p->precision != 64) return fail(MCMI_ERR_ARG, "precision must be 32 or 64");
-    if (p->table < -1 || p->table > 2) return fail(MCMI_ERR_ARG, "unknown table type");
+    if (p->table < -1 || p->table > 3) return fail(MCMI_ERR_ARG, "unknown table type");
+    if (p->table == MCMI_TABLE_COMPACT && p->accumulator != MCMI_ACC_FIXED64)
+        return fail(MCMI_ERR_ARG, "the compact table needs the FIXED64 accumulator");
+    if (p->table == MCMI_TABLE_COMPACT && p->proposal)
+        return fail(MCMI_ERR_ARG, "a learned proposal uses its own alias table");
     if (p->chains_per_thread < 0 || p->chains_per_thread > 2)
         return fail(MCMI_ERR_ARG, "chains_per_thread must be 0, 1 or 2");
     if (p->threads != 0 && p->threads != 64 && p->threads != 128 && p->threads != 256)
@@ -259,10 +264,23 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     P.smax = smax;
     if (h.smin_bits != ~0ull) memcpy(&P.smin, &h.smin_bits, sizeof(double));
     int table = p->table;
-    // automatic choice: short rows on average favour the inline cumulative
-    // table (one 64-byte load per step); otherwise the hybrid table keeps
-    // rows of at most 6 transitions inline and gives longer rows alias buckets
-    if (table == MCMI_TABLE_AUTO) table = (nnz - (int64_t)h.ndiag) <= 6 * n ? MCMI_TABLE_CUMULATIVE : MCMI_TABLE_HYBRID;
+    // the compact table needs every row within its 32-byte record
+    const bool compact_fits = h.max_deg <= (unsigned long long)kCompactMaxDeg &&
+                              h.max_off <= (unsigned long long)kCompactMaxOff;
+    if (table == MCMI_TABLE_COMPACT && !compact_fits)
+        return fail(MCMI_ERR_ARG, "compact table: a row has %llu off-diagonals or |j - i| = %llu (at most %d and %d)",
+                    (unsigned long long)h.max_deg, (unsigned long long)h.max_off, kCompactMaxDeg, kCompactMaxOff);
+    // automatic choice: the compact table (one 32-byte load per step) where
+    // every row fits it; else short rows on average favour the inline
+    // cumulative table (one 64-byte load per step); otherwise the hybrid
+    // table keeps rows of at most 6 transitions inline and gives longer rows
+    // alias buckets
+    if (table == MCMI_TABLE_AUTO) {
+        if (compact_fits && p->accumulator == MCMI_ACC_FIXED64 && !p->proposal)
+            table = MCMI_TABLE_COMPACT;
+        else
+            table = (nnz - (int64_t)h.ndiag) <= 6 * n ? MCMI_TABLE_CUMULATIVE : MCMI_TABLE_HYBRID;
+    }
     if (p->proposal) table = MCMI_TABLE_ALIAS;   // learned proposals use 32-byte alias buckets
     P.table = table;
     P.learned = p->proposal != nullptr;
@@ -275,13 +293,15 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     }
     // learned weights are not bounded by max_i s_i: no shorter bound than L
     P.Lb = P.learned ? p->max_len : walk_len_bound(smax, p->delta, p->max_len);
-    P.slots = S.get<uint4>((size_t)n * 4);
+    const bool alias_kind = table == MCMI_TABLE_ALIAS || table == MCMI_TABLE_HYBRID;
+    P.slots = S.get<uint4>((size_t)n * (table == MCMI_TABLE_COMPACT ? 2 : 4));
+    if (table == MCMI_TABLE_COMPACT) P.invd32 = S.get<float>(n);
     P.a = S.get<uint32_t>(nnz);
     P.b = S.get<uint32_t>(nnz);
     unsigned long long *wscr = nullptr;
     uint32_t *sstk = nullptr, *lstk = nullptr;
-    if (table != MCMI_TABLE_CUMULATIVE || keep_debug) P.c = S.get<uint32_t>(nnz);
-    if (table != MCMI_TABLE_CUMULATIVE) {
+    if (alias_kind || keep_debug) P.c = S.get<uint32_t>(nnz);
+    if (alias_kind) {
         P.bkt = S.get<uint4>(nnz);
         wscr = S.get<unsigned long long>(nnz);
         sstk = S.get<uint32_t>(nnz);
@@ -307,7 +327,7 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
         S.release(deg);
     } else {
         launch_tables(n, B->row_ptr, B->col, B->val, P.d, P.s, table, P.slots, P.a, P.b, P.c, P.bkt, wscr, sstk,
-                      lstk, P.rowd, s);
+                      lstk, P.rowd, P.invd32, s);
     }
     if (wscr) S.release(wscr);
     if (sstk) S.release(sstk);
@@ -363,6 +383,7 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
 {
     memset(&a, 0, sizeof(a));
     a.slots = P.slots;
+    a.invd32 = P.invd32;
     a.ool_a = P.a;
     a.ool_b = P.b;
     a.ool_bkt = P.bkt;
@@ -556,8 +577,9 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
     const float bar = 0.98f * dflt;
     struct Shape { int threads, cpt; } shapes[] = {{128, 1}, {256, 1}, {128, 2}, {64, 2}};
     const int hashes[] = {9, 10, 11, 12, 13};
-    int tables[3] = {MCMI_TABLE_CUMULATIVE, MCMI_TABLE_ALIAS, MCMI_TABLE_HYBRID};
-    const int ntab = p->table == MCMI_TABLE_AUTO ? 3 : 1;
+    int tables[4] = {MCMI_TABLE_CUMULATIVE, MCMI_TABLE_ALIAS, MCMI_TABLE_HYBRID, MCMI_TABLE_COMPACT};
+    const bool compact_ok = p->accumulator == MCMI_ACC_FIXED64 && !p->proposal;
+    const int ntab = p->table == MCMI_TABLE_AUTO ? (compact_ok ? 4 : 3) : 1;
     if (p->table != MCMI_TABLE_AUTO) tables[0] = p->table;
     mcmi_params cand = bestp;
     float cand_ms = 1e30f;
@@ -568,6 +590,7 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
         if (S.err != cudaSuccess) return cuda_fail(S.err, "memory pool");
         Prepared P;
         r = prepare(B, &q, s, S, P, false);
+        if (r != MCMI_OK && q.table == MCMI_TABLE_COMPACT && p->table == MCMI_TABLE_AUTO) continue;   // rows do not fit
         if (r != MCMI_OK) return r;
         for (const Shape &sh : shapes)
             for (int hl : hashes) {
@@ -1167,7 +1190,8 @@ mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *o
     const int64_t n = B->n, nnz = B->nnz;
     cudaMemcpyAsync(out_d, P.d, n * 8, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(out_s, P.s, n * 8, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(out_slot, P.slots, n * 64, cudaMemcpyDeviceToDevice, s);
+    // 64-byte records, or the compact table's 32-byte records packed at the start
+    cudaMemcpyAsync(out_slot, P.slots, n * (P.table == MCMI_TABLE_COMPACT ? 32 : 64), cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(out_a, P.a, nnz * 4, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(out_b, P.b, nnz * 4, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(out_c, P.c, nnz * 4, cudaMemcpyDeviceToDevice, s);

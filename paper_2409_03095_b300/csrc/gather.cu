@@ -20,9 +20,10 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x)
     return x;
 }
 
-__global__ void k_fill_records(uint4 *rec, uint64_t nrec, uint32_t seed)
+// n16: 16-byte words to fill
+__global__ void k_fill_records(uint4 *rec, uint64_t n16, uint32_t seed)
 {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < nrec * 4;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n16;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t a = mix32((uint32_t)i ^ seed), b = mix32(a + 0x9E3779B9u);
         rec[i] = make_uint4(a, b, mix32(b), mix32(a ^ b));
@@ -39,6 +40,14 @@ __device__ __forceinline__ void load64(const uint4 *p, uint32_t (&w)[16])
                  : "l"(p + 2));
 }
 
+__device__ __forceinline__ void load32(const uint4 *p, uint32_t (&w)[16])
+{
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                 : "l"(p));
+}
+
+template <int RB>
 __global__ void k_gather_probe(const uint4 *rec, uint64_t nrec, int steps, uint32_t seed, unsigned long long *sink)
 {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,11 +57,16 @@ __global__ void k_gather_probe(const uint4 *rec, uint64_t nrec, int steps, uint3
 #pragma unroll 1
     for (int s = 0; s < steps; ++s) {
         uint32_t w0[16], w1[16];
-        load64(rec + 4 * i0, w0);
-        load64(rec + 4 * i1, w1);
+        if (RB == 64) {
+            load64(rec + 4 * i0, w0);
+            load64(rec + 4 * i1, w1);
+        } else {
+            load32(rec + 2 * i0, w0);
+            load32(rec + 2 * i1, w1);
+        }
         uint32_t x0 = 0, x1 = 0;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) { x0 ^= w0[k]; x1 ^= w1[k]; }
+        for (int k = 0; k < RB / 4; ++k) { x0 ^= w0[k]; x1 ^= w1[k]; }
         acc += x0 + x1;
         i0 = ((uint64_t)x0 * nrec) >> 32;
         i1 = ((uint64_t)x1 * nrec) >> 32;
@@ -64,37 +78,38 @@ __global__ void k_gather_probe(const uint4 *rec, uint64_t nrec, int steps, uint3
 
 }  // namespace mcmi
 
-extern "C" mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int threads_per_block, int blocks_per_sm,
-                                            int steps, double *records_per_s, void *stream)
+extern "C" mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int record_bytes, int threads_per_block,
+                                            int blocks_per_sm, int steps, double *records_per_s, void *stream)
 {
     using namespace mcmi;
-    if (!records_per_s || footprint_bytes < 4096 || threads_per_block < 32 || threads_per_block > 1024 ||
-        blocks_per_sm < 1 || steps < 1) {
+    if (!records_per_s || footprint_bytes < 4096 || (record_bytes != 32 && record_bytes != 64) ||
+        threads_per_block < 32 || threads_per_block > 1024 || blocks_per_sm < 1 || steps < 1) {
         set_error_message("mcmi_gather_roofline: bad argument");
         return MCMI_ERR_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
-    const uint64_t nrec = footprint_bytes / 64;
+    const uint64_t nrec = footprint_bytes / (uint64_t)record_bytes;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     uint4 *rec = nullptr;
     unsigned long long *sink = nullptr;
-    cudaError_t e = cudaMallocAsync(&rec, nrec * 64, s);
+    cudaError_t e = cudaMallocAsync(&rec, nrec * (uint64_t)record_bytes, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&sink, 8, s);
     if (e != cudaSuccess) {
         if (rec) cudaFreeAsync(rec, s);
         set_error_message("mcmi_gather_roofline: allocation failed");
         return MCMI_ERR_OOM;
     }
-    k_fill_records<<<sms * 8, 256, 0, s>>>(rec, nrec, 0x1234567u);
+    k_fill_records<<<sms * 8, 256, 0, s>>>(rec, nrec * (uint64_t)record_bytes / 16, 0x1234567u);
     const int grid = sms * blocks_per_sm;
-    k_gather_probe<<<grid, threads_per_block, 0, s>>>(rec, nrec, 8, 1u, sink);   // warm-up
+    auto probe = record_bytes == 64 ? k_gather_probe<64> : k_gather_probe<32>;
+    probe<<<grid, threads_per_block, 0, s>>>(rec, nrec, 8, 1u, sink);   // warm-up
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
     cudaEventRecord(a, s);
-    k_gather_probe<<<grid, threads_per_block, 0, s>>>(rec, nrec, steps, 2u, sink);
+    probe<<<grid, threads_per_block, 0, s>>>(rec, nrec, steps, 2u, sink);
     cudaEventRecord(b, s);
     e = cudaEventSynchronize(b);
     float ms = 0.0f;

@@ -16,7 +16,7 @@ void launch_split(int64_t n, const int64_t *rp, const int32_t *col, const double
 void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
                    const double *sv, int table, uint4 *slots, uint32_t *a, uint32_t *b, uint32_t *c,
                    uint4 *bkt, unsigned long long *wscr, uint32_t *sstk, uint32_t *lstk, double2 *rowd,
-                   cudaStream_t s);
+                   float *invd32, cudaStream_t s);
 
 size_t walk_smem_bytes(int precision, int log2H, bool dump);
 // depth: loads per thread in flight after the walks (4 or 8)

@@ -206,20 +206,21 @@ __global__ void k_row_moments(WalkArgs a, int64_t n, float *__restrict__ m)
         uint4 r4 = make_uint4(0, 0, 0, 0);
         for (int t = 0;; ++t) {
             uint32_t s[16];
-            const uint4 *sp = a.slots + 4 * (size_t)st;
+            constexpr int kWords = TABLE == MCMI_TABLE_COMPACT ? 2 : 4;   // uint4 per record
+            const uint4 *sp = a.slots + kWords * (size_t)st;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const uint4 v = __ldg(sp + u);
+                const uint4 v = u < kWords ? __ldg(sp + u) : make_uint4(0u, 0u, 0u, 0u);
                 s[4 * u] = v.x; s[4 * u + 1] = v.y; s[4 * u + 2] = v.z; s[4 * u + 3] = v.w;
             }
-            if (t == a.L || !(fabsf(w) >= a.delta_f) || s[0] == 0u) break;
+            if (t == a.L || !(fabsf(w) >= a.delta_f) || record_q<TABLE>(s) == 0u) break;
             if ((t & 3) == 0)
                 r4 = philox4x32_10(make_uint4((uint32_t)(t >> 2), k, (uint32_t)row, (uint32_t)((uint64_t)row >> 32)),
                                    a.key0, a.key1);
             const int ph = t & 3;
             const uint32_t r = ph == 0 ? r4.x : ph == 1 ? r4.y : ph == 2 ? r4.z : r4.w;
             float f;
-            const uint32_t cs = pick_transition<TABLE>(s, r, a, &f);
+            const uint32_t cs = pick_transition<TABLE>(s, r, a, &f, st);
             w = __fmul_rn(w, f);
             sum = __fadd_rn(sum, __fmul_rn(w, w));
             st = cs & ~kNegBit;
@@ -424,7 +425,9 @@ int grid_of(int64_t work, int bs, int cap)
 cudaError_t launch_row_moments(const WalkArgs &a, int table, int64_t n, float *m, cudaStream_t s)
 {
     const int g = grid_of(n * (int64_t)a.N, 256, 148 * 16);
-    if (table != MCMI_TABLE_CUMULATIVE)   // alias and hybrid tables
+    if (table == MCMI_TABLE_COMPACT)
+        k_row_moments<MCMI_TABLE_COMPACT><<<g, 256, 0, s>>>(a, n, m);
+    else if (table != MCMI_TABLE_CUMULATIVE)   // alias and hybrid tables
         k_row_moments<MCMI_TABLE_ALIAS><<<g, 256, 0, s>>>(a, n, m);
     else
         k_row_moments<MCMI_TABLE_CUMULATIVE><<<g, 256, 0, s>>>(a, n, m);

@@ -22,6 +22,15 @@ constexpr uint32_t kNegBit = 0x80000000u;     // record: sign of c_ij
 constexpr int kInlineCum = 6;                 // cumulative pairs that fit a 64-byte slot
 constexpr int kInlineAlias = 4;               // alias triples that fit a 64-byte slot
 constexpr int kMlpParams = 1377;              // learned proposal: 8-32-32-1 network parameters
+// Compact table: one 32-byte record per row (at most six transitions, each
+// column within kCompactMaxOff of the row), weights at the scale 2^20.
+//   word 0:    fl32(s_i)
+//   words 1-2: Q | T_1 << 21 | T_2 << 42 (a 64-bit word of 21-bit fields)
+//   words 3-4: T_3 | T_4 << 21 | T_5 << 42 (unused thresholds hold Q)
+//   words 5-7: six 16-bit fields (col - i) << 1 | sign(c_ij), two per word
+constexpr int kCompactMaxDeg = 6;
+constexpr int kCompactMaxOff = 16383;
+constexpr uint32_t kField21 = 0x1FFFFFu;
 
 // Device-side counters and the first error of a launch sequence.
 struct DevState {
@@ -35,6 +44,8 @@ struct DevState {
     unsigned long long deferred;   // rows that found the staging buffer full
     unsigned long long work;       // next row-queue position
     unsigned long long ndiag;      // rows that have a stored diagonal
+    unsigned long long max_deg;    // largest off-diagonal count of a row
+    unsigned long long max_off;    // largest |j - i| of an off-diagonal entry
 };
 
 __device__ __forceinline__ void report(DevState *st, long long row, int code)
@@ -62,7 +73,8 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 
 // Arguments of the walk kernel.
 struct WalkArgs {
-    const uint4 *slots;           // 4 x uint4 per row
+    const uint4 *slots;           // 4 x uint4 per row (compact table: 2 x uint4)
+    const float *invd32;          // compact table: fl32(1/d_i) per row
     const uint32_t *ool_a, *ool_b;    // cumulative out-of-line: thresholds, col|sign
     const uint4 *ool_bkt;             // alias out-of-line buckets {prob, own, alias, 0}
     const uint4 *lbkt;                // learned proposal: 32-byte alias buckets with weight factors
@@ -112,6 +124,13 @@ struct WalkArgs {
     DevState *st;
 };
 
+// Total weight Q of a row's record (0: no transition, the chain stops).
+template <int TABLE>
+__device__ __forceinline__ uint32_t record_q(const uint32_t (&s)[16])
+{
+    return TABLE == MCMI_TABLE_COMPACT ? (s[1] & kField21) : s[0];
+}
+
 // One transition out of the row whose 64-byte record is s[16], driven by the
 // 32-bit random word r.  Returns col | neg << 31 of the picked entry and the
 // FP32 weight factor in *f: sign(c) fl32(s_i) for the |c| proposal, the
@@ -121,11 +140,29 @@ struct WalkArgs {
 //   alias:      bucket b = floor(r deg / 2^32), the low 32 bits of r deg
 //               scaled to [0, Q) against the bucket's threshold;
 //   hybrid:     the alias kernels; rows flagged kCumFlag (at most 6
-//               transitions) hold an inline cumulative record.
+//               transitions) hold an inline cumulative record;
+//   compact:    the cumulative rule on the 32-byte record (row: its index,
+//               for the column offsets).
 template <int TABLE>
 __device__ __forceinline__ uint32_t pick_transition(const uint32_t (&s)[16], uint32_t r, const WalkArgs &a,
-                                                    float *f)
+                                                    float *f, uint32_t row = 0u)
 {
+    if (TABLE == MCMI_TABLE_COMPACT) {
+        const unsigned long long A = (unsigned long long)s[1] | ((unsigned long long)s[2] << 32);
+        const unsigned long long Bt = (unsigned long long)s[3] | ((unsigned long long)s[4] << 32);
+        const uint32_t Qc = (uint32_t)A & kField21;
+        const uint32_t x = __umulhi(r, Qc);
+        const uint32_t m = (((uint32_t)(A >> 21) & kField21) <= x) + ((uint32_t)(A >> 42) <= x) +
+                           (((uint32_t)Bt & kField21) <= x) + (((uint32_t)(Bt >> 21) & kField21) <= x) +
+                           ((uint32_t)(Bt >> 42) <= x);
+        const uint32_t pair = m < 2u ? s[5] : (m < 4u ? s[6] : s[7]);
+        const uint32_t h = (m & 1u) ? (pair >> 16) : (pair & 0xFFFFu);
+        const int off = (int)(int16_t)(uint16_t)h >> 1;
+        const uint32_t cs = (uint32_t)((int)row + off) | ((h & 1u) ? kNegBit : 0u);
+        const float fs = __uint_as_float(s[0]);
+        *f = (h & 1u) ? -fs : fs;
+        return cs;
+    }
     const uint32_t Q = s[0];
     const uint32_t deg = s[3] & ~(kOolFlag | kCumFlag);
     uint32_t cs;

@@ -56,8 +56,19 @@ __global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = rp[i], b = rp[i + 1];
         double bii = 0.0;
-        for (int64_t k = a; k < b; ++k)
-            if (col[k] == i) bii = val[k];
+        unsigned long long ndeg = 0, moff = 0;   // off-diagonals and their largest |j - i|
+        for (int64_t k = a; k < b; ++k) {
+            if (col[k] == i) {
+                bii = val[k];
+            } else {
+                ++ndeg;
+                const long long o = (long long)col[k] - (long long)i;
+                const unsigned long long ao = (unsigned long long)(o < 0 ? -o : o);
+                moff = ao > moff ? ao : moff;
+            }
+        }
+        atomicMax(&st->max_deg, ndeg);
+        atomicMax(&st->max_off, moff);
         double di = bii;
         if (alpha > 0.0) di = __dadd_rn(bii, __dmul_rn(__dmul_rn(alpha, bnorm), bii < 0.0 ? -1.0 : 1.0));
         if (di == 0.0) {
@@ -79,13 +90,15 @@ __global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t
     }
 }
 
-// Integer weight of one entry: max(1, floor(|c|/s 2^31)); 0 if c == 0.
-__device__ __forceinline__ uint32_t entry_weight(double b, double di, double si, bool *neg)
+// Integer weight of one entry: max(1, floor(|c|/s scale)); 0 if c == 0.
+// scale = 2^31, or 2^20 for the compact table.
+__device__ __forceinline__ uint32_t entry_weight(double b, double di, double si, bool *neg,
+                                                double scale = 2147483648.0)
 {
     const double c = __ddiv_rn(-b, di);
     *neg = c < 0.0;
     if (c == 0.0 || !(si > 0.0)) return 0u;
-    const double x = floor(__dmul_rn(__ddiv_rn(fabs(c), si), 2147483648.0));
+    const double x = floor(__dmul_rn(__ddiv_rn(fabs(c), si), scale));
     const uint32_t q = (uint32_t)x;
     return q < 1u ? 1u : q;
 }
@@ -103,12 +116,44 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
                          uint32_t *__restrict__ ool_c, uint4 *__restrict__ ool_bkt,
                          unsigned long long *__restrict__ wscratch,
                          uint32_t *__restrict__ small_stk, uint32_t *__restrict__ large_stk,
-                         double2 *__restrict__ rowd)
+                         double2 *__restrict__ rowd, float *__restrict__ invd32)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = rp[i], b = rp[i + 1];
         const double di = d[i], si = s[i];
+        if (table == MCMI_TABLE_COMPACT) {
+            // 32-byte record (layout in mcmi_internal.cuh); the host checked
+            // that every row has at most six off-diagonals within the offset range
+            uint32_t T[kCompactMaxDeg], h[kCompactMaxDeg];
+#pragma unroll
+            for (int u = 0; u < kCompactMaxDeg; ++u) { T[u] = 0u; h[u] = 0u; }
+            uint32_t Q = 0, m = 0;
+            for (int64_t k = a; k < b; ++k) {
+                if (col[k] == i) continue;
+                bool ng;
+                Q += entry_weight(val[k], di, si, &ng, 1048576.0);
+                const uint32_t hv = ((uint32_t)(col[k] - (int32_t)i) << 1 | (ng ? 1u : 0u)) & 0xFFFFu;
+#pragma unroll
+                for (int u = 0; u < kCompactMaxDeg; ++u)
+                    if (u == (int)m) { T[u] = Q; h[u] = hv; }
+                ++m;
+            }
+            // thresholds past the last transition hold Q: never below a draw
+#pragma unroll
+            for (int u = 0; u < kCompactMaxDeg; ++u)
+                if (u >= (int)m) T[u] = Q;
+            const unsigned long long A = (unsigned long long)Q | ((unsigned long long)T[0] << 21) |
+                                         ((unsigned long long)T[1] << 42);
+            const unsigned long long Bt = (unsigned long long)T[2] | ((unsigned long long)T[3] << 21) |
+                                          ((unsigned long long)T[4] << 42);
+            uint4 *o = slots + 2 * i;
+            o[0] = make_uint4(__float_as_uint(__double2float_rn(si)), (uint32_t)A, (uint32_t)(A >> 32), (uint32_t)Bt);
+            o[1] = make_uint4((uint32_t)(Bt >> 32), h[0] | h[1] << 16, h[2] | h[3] << 16, h[4] | h[5] << 16);
+            invd32[i] = __double2float_rn(__ddiv_rn(1.0, di));
+            if (rowd) rowd[i] = make_double2(si, __ddiv_rn(1.0, di));
+            continue;
+        }
         uint32_t w[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) w[k] = 0u;
@@ -237,12 +282,12 @@ void launch_split(int64_t n, const int64_t *rp, const int32_t *col, const double
 void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
                    const double *sv, int table, uint4 *slots, uint32_t *a, uint32_t *b, uint32_t *c,
                    uint4 *bkt, unsigned long long *wscr, uint32_t *sstk, uint32_t *lstk, double2 *rowd,
-                   cudaStream_t s)
+                   float *invd32, cudaStream_t s)
 {
     const int bs = 128;
     const int64_t g = (n + bs - 1) / bs;
     k_tables<<<(unsigned)(g < 148 * 64 ? g : 148 * 64), bs, 0, s>>>(n, rp, col, val, d, sv, table, slots, a,
-                                                                     b, c, bkt, wscr, sstk, lstk, rowd);
+                                                                     b, c, bkt, wscr, sstk, lstk, rowd, invd32);
 }
 
 }  // namespace mcmi

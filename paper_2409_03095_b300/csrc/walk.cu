@@ -194,6 +194,14 @@ __device__ __forceinline__ void load_slot(const uint4 *sp, uint32_t (&w)[16])
                  : "l"(sp + 2));
 }
 
+// 32-byte compact record as one 256-bit load (one sector); w[8..15] unused.
+__device__ __forceinline__ void load_rec32(const uint4 *sp, uint32_t (&w)[16])
+{
+    asm volatile("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7])
+                 : "l"(sp));
+}
+
 }  // namespace
 
 // Register cap and load depth.  The loops after the walks take their global
@@ -208,6 +216,7 @@ template <int PREC, int TABLE, int ACC, bool DUMP, int CPT, int DEPTH>
 __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 64)) k_walk(WalkArgs a)
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
+    constexpr bool CMP = TABLE == MCMI_TABLE_COMPACT;   // 32-byte records, 1/d_j from invd32
     // log magnitude sketch (tau builds), in the variant for log-heavy rows
     constexpr bool SKETCH = FIX && PREC == 32 && !DUMP && DEPTH == 8;
     // finished values and the filter work in the build's precision: FP32
@@ -411,7 +420,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 #pragma unroll
             for (int j = 0; j < CPT; ++j)
                 if (k[j] < a.N) {
-                    load_slot(a.slots + 4 * (size_t)st[j], s[j]);
+                    if (CMP) load_rec32(a.slots + 2 * (size_t)st[j], s[j]);
+                    else load_slot(a.slots + 4 * (size_t)st[j], s[j]);
                     if (PREC == 64) rd[j] = __ldg(a.rowd + st[j]);
                 }
 #pragma unroll
@@ -445,7 +455,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     if (to_log) {
                         const uint32_t pos = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
                         if (pos < a.log_cap) {
-                            lc[pos] = make_uint2(st[j], s[j][2]);
+                            lc[pos] = make_uint2(st[j], CMP ? 0u : s[j][2]);   // compact: 1/d_j looked up later
                             lv[pos] = add;
                         } else {
                             report(a.st, s_row, MCMI_ERR_CAPACITY);   // cannot happen: a row makes at most N Lb visits
@@ -453,7 +463,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     }
                 }
                 if (!live) continue;
-                const uint32_t Q = s[j][0];
+                const uint32_t Q = record_q<TABLE>(s[j]);
                 if (t[j] == a.L || !(fabsf(w[j]) >= a.delta_f) || Q == 0u) {
                     my_steps += (unsigned long long)t[j];
                     k[j] = atomicAdd(&s_next_chain, 1);
@@ -468,7 +478,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 const int ph = t[j] & 3;
                 const uint32_t r = ph == 0 ? r4[j].x : ph == 1 ? r4[j].y : ph == 2 ? r4[j].z : r4[j].w;
                 float fl;
-                const uint32_t cs = pick_transition<TABLE>(s[j], r, a, &fl);
+                const uint32_t cs = pick_transition<TABLE>(s[j], r, a, &fl, st[j]);
                 const bool neg = (cs & kNegBit) != 0u;
                 w[j] = __fmul_rn(w[j], fl);
                 if (PREC == 64) w64[j] = __dmul_rn(w64[j], neg ? -rd[j].x : rd[j].x);
@@ -495,6 +505,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         auto load_invd = [&](uint32_t col) -> VT {
             if (!FIX) return (VT)0;
             if (PREC == 64) return (VT)__ldg(&a.rowd[col].y);
+            if (CMP) return (VT)__ldg(a.invd32 + col);
             return (VT)__uint_as_float(__ldg(&a.slots[4 * (size_t)col].z));
         };
         auto finish = [&](unsigned long long raw, VT invd) -> VT {
@@ -675,7 +686,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         if (*(volatile uint32_t *)cell >= kSketchOne - 1u) continue;   // already kept
                         const long long x = (long long)val[u];
                         const float m = __ull2float_ru((unsigned long long)(x < 0 ? -x : x));
-                        const float v = __fmul_ru(__fmul_ru(m, a.fin_scale), fabsf(__uint_as_float(key[u].y)));
+                        const float id = CMP ? (float)load_invd(key[u].x) : __uint_as_float(key[u].y);
+                        const float v = __fmul_ru(__fmul_ru(m, a.fin_scale), fabsf(id));
                         const float q = ceilf(__fmul_ru(v, qs));
                         atomicAdd(cell, q < (float)kSketchOne ? (uint32_t)q : kSketchOne);   // NaN: kept
                     }
@@ -782,7 +794,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         VT v = (VT)0;
                         bool keep = false;
                         if (lead) {
-                            const VT invd = PREC == 64 ? load_invd(key[u].x) : (VT)__uint_as_float(key[u].y);
+                            const VT invd = (PREC == 64 || CMP) ? load_invd(key[u].x) : (VT)__uint_as_float(key[u].y);
                             v = finish(single ? val[u] : scratch[lane], invd);
                             const VT av = v < (VT)0 ? -v : v;
                             lmax = av > lmax ? av : lmax;
@@ -1118,10 +1130,15 @@ using WalkFn = void (*)(WalkArgs);
 template <bool D, int C, int U>
 WalkFn pick_walk(int precision, int table, int acc)
 {
-    if (precision == 64)
+    // table: MCMI_TABLE_* (hybrid runs the alias kernels); the compact table
+    // only with the fixed-point accumulator (the parameter check enforces it)
+    if (precision == 64) {
+        if (table == MCMI_TABLE_COMPACT) return k_walk<64, MCMI_TABLE_COMPACT, MCMI_ACC_FIXED64, D, C, U>;
         return table ? k_walk<64, 1, MCMI_ACC_FIXED64, D, C, U> : k_walk<64, 0, MCMI_ACC_FIXED64, D, C, U>;
+    }
     if (acc == MCMI_ACC_KAHAN32)
         return table ? k_walk<32, 1, MCMI_ACC_KAHAN32, D, C, U> : k_walk<32, 0, MCMI_ACC_KAHAN32, D, C, U>;
+    if (table == MCMI_TABLE_COMPACT) return k_walk<32, MCMI_TABLE_COMPACT, MCMI_ACC_FIXED64, D, C, U>;
     return table ? k_walk<32, 1, MCMI_ACC_FIXED64, D, C, U> : k_walk<32, 0, MCMI_ACC_FIXED64, D, C, U>;
 }
 

@@ -84,6 +84,57 @@ def test_tables_bit_exact(name, table):
             assert np.array_equal(got[:, 0], prob) and np.array_equal(got[:, 1], cs) and np.array_equal(got[:, 2], cs[al])
 
 
+@pytest.mark.parametrize("name", ["stencil2d", "stencil3d_12"])
+def test_compact_tables_bit_exact(name):
+    """The compact table's 32-byte records against the oracle's weights at
+    the scale 2^20: fl32(s_i), Q and the cumulative thresholds in 21-bit
+    fields (thresholds past the last transition hold Q), and per transition
+    (j - i) << 1 | sign(c_ij) in 16 bits."""
+    orc = _orc()
+    m = _cases_small()[name]
+    B = mc.DeviceCsr.from_host(m)
+    g = mc.mcmi_debug_tables(B, mc.params(table=mc.TABLE_COMPACT))
+    d, s = orc.split(m)
+    tb = orc.tables(m, d, s, table=orc.TABLE_COMPACT)
+    rec = g["rec32"].astype(np.uint64)
+    assert np.array_equal(rec[:, 0].astype(np.uint32), s.astype(np.float32).view(np.uint32))
+    A = rec[:, 1] | (rec[:, 2] << np.uint64(32))
+    Bt = rec[:, 3] | (rec[:, 4] << np.uint64(32))
+    f = lambda x, k: ((x >> np.uint64(21 * k)) & np.uint64(0x1FFFFF)).astype(np.int64)
+    assert np.array_equal(f(A, 0), tb["Q"].astype(np.int64))
+    for i in range(m.n):
+        a, b = tb["off"][i], tb["off"][i + 1]
+        deg = b - a
+        T = np.cumsum(tb["q"][a:b].astype(np.int64))
+        Q = int(tb["Q"][i])
+        got_T = [f(A, 1)[i], f(A, 2)[i], f(Bt, 0)[i], f(Bt, 1)[i], f(Bt, 2)[i]]
+        want_T = [int(T[k]) if k < deg else Q for k in range(5)]
+        assert got_T == want_T, (i, got_T, want_T)
+        cols = np.array([c for c in m.col[m.row_ptr[i]:m.row_ptr[i + 1]] if c != i], dtype=np.int64)
+        vals = np.array([v for c, v in zip(m.col[m.row_ptr[i]:m.row_ptr[i + 1]], m.val[m.row_ptr[i]:m.row_ptr[i + 1]]) if c != i])
+        h = [(int(rec[i, 5 + k // 2]) >> (16 * (k % 2))) & 0xFFFF for k in range(deg)]
+        off = [((x ^ 0x8000) - 0x8000) >> 1 for x in h]
+        neg = [x & 1 for x in h]
+        assert off == list(cols - i) and neg == [int(-v / d[i] < 0) for v in vals]
+
+
+def test_compact_table_refuses_rows_that_do_not_fit():
+    for name in ("rand_long", "powerlaw_4k"):
+        B = mc.DeviceCsr.from_host(_cases_small()[name])
+        with pytest.raises(mc.McmiError) as e:
+            mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8, table=mc.TABLE_COMPACT))
+        assert e.value.status == 1
+    B = mc.DeviceCsr.from_host(_cases_small()["stencil2d"])
+    with pytest.raises(mc.McmiError) as e:
+        mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8, table=mc.TABLE_COMPACT, accumulator=1))
+    assert e.value.status == 1
+    # the automatic choice: compact for the stencil, not for the long rows
+    assert mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8)).stats.table == mc.TABLE_COMPACT
+    R = mc.DeviceCsr.from_host(_cases_small()["rand_long"])
+    assert mc.mcmi_build_ex(R, mc.params(chains=8, max_len=8)).stats.table != mc.TABLE_COMPACT
+    assert mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8, accumulator=1)).stats.table == mc.TABLE_CUMULATIVE
+
+
 # ------------------------------------------------------------------ walks
 
 
@@ -110,6 +161,11 @@ WALK_CASES = [
     ("powerlaw_4k", 64, 1, 128, 256, 1e-3, {"hash_log2": 6}),
     ("rand_long", 32, 1, 300, 256, 1e-3, {"hash_log2": 8, "threads": 64, "chains_per_thread": 2}),
     ("stencil2d", 32, 0, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 64}),
+    # compact table: 32-byte records, weights at the scale 2^20
+    ("stencil2d", 64, 3, 1000, 64, 1e-3, {}),
+    ("stencil2d", 32, 3, 1000, 64, 1e-3, {"hash_log2": 7, "threads": 64}),   # log entries look up 1/d_j
+    ("stencil3d_12", 32, 3, 256, 128, 1e-2, {"threads": 128, "chains_per_thread": 2}),
+    ("stencil3d_12", 64, 3, 256, 128, 1e-2, {"hash_log2": 6}),
     # the FP32 Kahan accumulator
     ("stencil3d_12", 32, 0, 256, 128, 1e-2, {"accumulator": 1}),
     ("rand_mixed", 32, 1, 300, 80, 1e-4, {"accumulator": 1}),
@@ -293,6 +349,15 @@ def test_load_depth_leaves_the_result_unchanged():
                     out[depth] = [t.cpu().numpy() for t in M.to_torch()]
                 for u, v in zip(out[4], out[8]):
                     assert np.array_equal(u, v)
+    # compact table through the log (1/d_j looked up by column), sketch at depth 8
+    S12 = mc.DeviceCsr.from_host(_cases_small()["stencil3d_12"])
+    out = {}
+    for depth in (4, 8):
+        p = mc.params(chains=256, max_len=128, delta=1e-2, filter_tau=1e-2, seed=5, table=mc.TABLE_COMPACT,
+                      hash_log2=6, load_depth=depth)
+        out[depth] = [t.cpu().numpy() for t in mc.mcmi_build_ex(S12, p).to_torch()]
+    for u, v in zip(out[4], out[8]):
+        assert np.array_equal(u, v)
     assert mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8)).stats.load_depth == 8
     assert mc.mcmi_build_ex(B, mc.params(chains=8, max_len=8, precision=64)).stats.load_depth == 4
     S = mc.DeviceCsr.from_host(synth.stencil3d_7pt(8, seed=1))
