@@ -52,11 +52,14 @@ __global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t
                         double *__restrict__ s, DevState *st)
 {
     const double bnorm = __longlong_as_double((long long)st->bnorm_bits);
+    // this thread's extremes over its rows, combined per warp before the
+    // device-wide atomics (s_i >= 0: the bit patterns order like the values)
+    unsigned long long smax = 0, smin = ~0ull, dmax = 0, omax = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = rp[i], b = rp[i + 1];
         double bii = 0.0;
-        unsigned long long ndeg = 0, moff = 0;   // off-diagonals and their largest |j - i|
+        unsigned long long ndeg = 0;   // off-diagonals and their largest |j - i|
         for (int64_t k = a; k < b; ++k) {
             if (col[k] == i) {
                 bii = val[k];
@@ -64,11 +67,10 @@ __global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t
                 ++ndeg;
                 const long long o = (long long)col[k] - (long long)i;
                 const unsigned long long ao = (unsigned long long)(o < 0 ? -o : o);
-                moff = ao > moff ? ao : moff;
+                omax = ao > omax ? ao : omax;
             }
         }
-        atomicMax(&st->max_deg, ndeg);
-        atomicMax(&st->max_off, moff);
+        dmax = ndeg > dmax ? ndeg : dmax;
         double di = bii;
         if (alpha > 0.0) di = __dadd_rn(bii, __dmul_rn(__dmul_rn(alpha, bnorm), bii < 0.0 ? -1.0 : 1.0));
         if (di == 0.0) {
@@ -85,8 +87,22 @@ __global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t
         d[i] = di;
         s[i] = si;
         if (!(si < 1.0)) report(st, i, MCMI_ERR_NOT_CONTRACTIVE);
-        atomicMax(&st->smax_bits, (unsigned long long)__double_as_longlong(si));
-        if (si > 0.0) atomicMin(&st->smin_bits, (unsigned long long)__double_as_longlong(si));
+        const unsigned long long sb = (unsigned long long)__double_as_longlong(si);
+        smax = sb > smax ? sb : smax;
+        if (si > 0.0) smin = sb < smin ? sb : smin;
+    }
+    // every lane reaches this point (the row loop has no early exit)
+    for (int o = 16; o > 0; o >>= 1) {
+        smax = max(smax, __shfl_xor_sync(0xFFFFFFFFu, smax, o));
+        smin = min(smin, __shfl_xor_sync(0xFFFFFFFFu, smin, o));
+        dmax = max(dmax, __shfl_xor_sync(0xFFFFFFFFu, dmax, o));
+        omax = max(omax, __shfl_xor_sync(0xFFFFFFFFu, omax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st->smax_bits, smax);
+        if (smin != ~0ull) atomicMin(&st->smin_bits, smin);
+        atomicMax(&st->max_deg, dmax);
+        atomicMax(&st->max_off, omax);
     }
 }
 
