@@ -295,6 +295,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     auto onchip_slot = [&](uint32_t col) -> int {
         uint32_t bkt = hash_home(col, a.log2H - 2);
         const uint32_t nb = (uint32_t)(H >> 2);
+        // the cap is read once, alongside the first bucket: lanes probing at
+        // the same time may each still insert, so the table can pass the cap
+        // by up to a block's threads (a small table may fill up; a probe then
+        // gives up after its bucket limit and the visit is logged)
+        const bool capped = *(volatile uint32_t *)&s_fill >= fill_cap;
 #pragma unroll 1
         for (int p = 0; p < kProbeOnChip / 4; ++p) {
             uint4 kv;
@@ -305,7 +310,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             if (slot >= 0) return (int)(4 * bkt) + slot;
             const int e = kv.x == kEmpty ? 0 : kv.y == kEmpty ? 1 : kv.z == kEmpty ? 2 : kv.w == kEmpty ? 3 : -1;
             if (e >= 0) {
-                if (*(volatile uint32_t *)&s_fill >= fill_cap) return -1;
+                if (capped) return -1;
                 const uint32_t old = atomicCAS(&s_keys[4 * bkt + e], kEmpty, col);
                 if (old == kEmpty) atomicAdd(&s_fill, 1u);
                 if (old == kEmpty || old == col) return (int)(4 * bkt) + e;
@@ -315,7 +320,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             // a full bucket without the key: once the table is at its cap, the
             // search stops here (the visit is logged; the merge after the walks
             // finds the key if it sits further on)
-            if (*(volatile uint32_t *)&s_fill >= fill_cap) return -1;
+            if (capped) return -1;
             bkt = (bkt + 1) & (nb - 1);
         }
         return -1;
