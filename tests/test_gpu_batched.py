@@ -46,6 +46,25 @@ def test_batched_equals_individual_builds(table):
     assert st.steps == total_steps
 
 
+@pytest.mark.parametrize("table", [mc.TABLE_COMPACT, mc.TABLE_AUTO])
+def test_batched_compact_equals_individual_builds(table):
+    """Stencils only: the block-diagonal batch fits the compact table (column
+    offsets stay inside each block), and AUTO picks it for the batch as for
+    each matrix alone."""
+    mats = [m for k, m in enumerate(_mats()) if k in (0, 1, 3, 4)]
+    Bs = [mc.DeviceCsr.from_host(m) for m in mats]
+    # a fixed launch shape: no autotuner, so AUTO resolves as in a single build
+    kw = dict(chains=96, max_len=100, delta=1e-3, filter_tau=1e-2, top_k=8, seed=77, table=table, threads=128,
+              chains_per_thread=1, hash_log2=11)
+    Ms, st = mc.mcmi_build_batched(Bs, mc.params(**kw))
+    assert st.table == mc.TABLE_COMPACT
+    for B, M in zip(Bs, Ms):
+        Mi = mc.mcmi_build_ex(B, mc.params(**kw))
+        assert Mi.stats.table == mc.TABLE_COMPACT
+        for u, v in zip(_csr(M), _csr(Mi)):
+            assert np.array_equal(u, v)
+
+
 def test_batched_fixed_shape_and_errors():
     mats = _mats()[:3]
     Bs = [mc.DeviceCsr.from_host(m) for m in mats]
