@@ -47,22 +47,19 @@ __device__ __forceinline__ uint32_t hash_home(uint32_t key, int log2)
     return (key * 0x9E3779B1u) >> (32 - log2);
 }
 
-// w * 2^F rounded to the nearest integer, from the bits of an FP32 w (|w| < 1).
-__device__ __forceinline__ long long fix_f32(float w, int F)
+// w * 2^F (scale = 2^F as a float) rounded to the nearest integer, ties to
+// even, by one float-to-integer conversion: the product is exact, and for
+// FP32 walks with the |c| proposal F makes it an integer (every weight is a
+// multiple of 2^-F), so the result is exact too.  (A learned proposal's F
+// leaves head-room instead; its products may round.)
+__device__ __forceinline__ long long fix_f32s(float w, float scale)
 {
-    const uint32_t b = __float_as_uint(w);
-    const int e = (int)((b >> 23) & 0xFFu);
-    if (e == 0) return 0;
-    const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
-    const int s = e - 150 + F;
-    long long v;
-    if (s >= 0) v = m << (s < 39 ? s : 39);   // |w| beyond the scale's range is reported by the caller
-    else if (s > -40) v = (m + (1ll << (-s - 1))) >> (-s);
-    else v = 0;
-    return (b >> 31) ? -v : v;
+    return __float2ll_rn(__fmul_rn(w, scale));
 }
 
-// Same for an FP64 w (|w| < 1).
+// w * 2^F rounded to the nearest integer for an FP64 w (|w| < 1), with
+// integer instructions (FP64 arithmetic issues at a small fraction of the
+// FP32 rate).
 __device__ __forceinline__ long long fix_f64(double w, int F)
 {
     const unsigned long long b = (unsigned long long)__double_as_longlong(w);
@@ -75,26 +72,6 @@ __device__ __forceinline__ long long fix_f64(double w, int F)
     else if (s > -63) v = (m + (1ll << (-s - 1))) >> (-s);
     else v = 0;
     return (b >> 63) ? -v : v;
-}
-
-// u (a 64-bit magnitude) rounded to the nearest FP32 value, ties to even,
-// with integer instructions.  Being correctly rounded, the result scales
-// exactly with powers of two of u, so finished values do not depend on the
-// fixed-point scale.
-__device__ __forceinline__ float u64_to_f32_rn(unsigned long long u)
-{
-    if (u == 0ull) return 0.0f;
-    const int lz = __clzll((long long)u);
-    const unsigned long long n = u << lz;            // leading one at bit 63
-    uint32_t mant = (uint32_t)(n >> 40);             // 24 significant bits
-    const unsigned long long rest = n << 24;         // the 40 bits below them, at the top
-    if (rest > 0x8000000000000000ull || (rest == 0x8000000000000000ull && (mant & 1u))) ++mant;
-    int e = 63 - lz;
-    if (mant == (1u << 24)) {
-        mant >>= 1;
-        ++e;
-    }
-    return __uint_as_float(((uint32_t)(e + 127) << 23) | (mant & 0x7FFFFFu));
 }
 
 // Exact 64-bit add into a shared word from two native 32-bit atomics.
@@ -275,6 +252,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     uint32_t *ecn = DUMP ? a.ent_cnt + (size_t)blockIdx.x * a.ent_cap : nullptr;
     const long long total = a.row_list ? a.n_list : a.row_end - a.row_begin;
     const int F = a.fix_shift;
+    const float scaleF = __uint_as_float((uint32_t)(F + 127) << 23);   // 2^F (F <= 62)
     const bool use_tau = a.tau > 0.0;
 
     for (int h = tid; h < H; h += B) {
@@ -439,7 +417,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     // a learned proposal's weights are not bounded by 1: the host
                     // leaves head-room in the fixed-point scale up to w_limit
                     if (FIX && a.lbkt && !(fabsf(w[j]) <= a.w_limit)) report(a.st, s_row, MCMI_ERR_CAPACITY);
-                    if (FIX) add = (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32(w[j], F));
+                    if (FIX) add = (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32s(w[j], scaleF));
                     else add = (unsigned long long)__float_as_uint(__fmul_rn(w[j], __uint_as_float(s[j][2])));
                     h = onchip_slot(st[j]);
                 }
@@ -520,7 +498,9 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             } else if (FIX) {
                 // fl32(|X| 2^F), then (2^-F / N) and 1/d_j: three FP32 roundings
                 const long long x = (long long)raw;
-                const float m = u64_to_f32_rn((unsigned long long)(x < 0 ? -x : x));
+                // correctly rounded (ties to even), so the result scales exactly
+                // with powers of two of |X| and does not depend on F
+                const float m = __ull2float_rn((unsigned long long)(x < 0 ? -x : x));
                 const float v = __fmul_rn(__fmul_rn(m, a.fin_scale), (float)invd);
                 return (VT)(x < 0 ? -v : v);
             } else {
