@@ -400,11 +400,11 @@ def run_ours(a):
         return 0
     peaks, peak_src = _peaks()
     walk_total_ms = sum(walk_ms)
-    # algorithmic bytes: two 32-B sectors per visited state (the row's header
-    # and its sampled transition in separate sectors); the compact table's
-    # 32-byte record holds both in one sector, so that kernel reads half
+    # algorithmic bytes per visited state: the sectors that hold the row's
+    # header and its sampled transition -- two 32-B sectors of a 64-byte
+    # record, one for the compact table's 32-byte record
     rec_bytes = 32 if last.table == mc.TABLE_COMPACT else SLOT_BYTES   # bytes of one row record
-    alg_bytes = SLOT_BYTES * visits
+    alg_bytes = rec_bytes * visits
     achieved = alg_bytes / (walk_total_ms / 1e3) / 1e9
     traffic = _traffic(os.path.join(ROOT, "paper_2409_03095_b300", "csrc", "walk.cu"))
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -412,8 +412,9 @@ def run_ours(a):
             "kernel": "k_walk (walk + accumulate + filter)",
             "peak_source": f"{peak_src} HBM copy bandwidth",
             "algorithmic_bytes_per_launch": alg_bytes / max(1, len(walk_ms)),
-            "bytes_per_unit": ("64 B (two 32-B sectors: the row header and the sampled transition) per visited "
-                               f"state; the {mc.TABLE_NAMES[last.table]} table's records are {rec_bytes} B"),
+            "bytes_per_unit": (f"{rec_bytes} B per visited state: the {rec_bytes // 32} 32-B sector"
+                               f"{'s' if rec_bytes > 32 else ''} holding the row header and the sampled "
+                               f"transition ({mc.TABLE_NAMES[last.table]} table, {rec_bytes}-B records)"),
             "walk_kernel_ms": walk_total_ms / max(1, len(walk_ms)),
             "walk_share_of_step": walk_total_ms / tot_ms if world == 1 else None}
     # gather roofline (one row record per visited state): dependent random
