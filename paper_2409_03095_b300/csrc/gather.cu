@@ -1,6 +1,7 @@
 // Gather roofline probe: the memory access pattern of the walk without its
 // arithmetic.  Every thread follows two chains of dependent random reads of
-// 64-byte records (two 256-bit loads each, as the walk reads a row record);
+// 64-byte records (two 256-bit loads each, as the walk reads a row record)
+// or of 32-byte records (one 256-bit load, the compact table's records);
 // the next record index comes from the record just read.  Records per second
 // at a given footprint and occupancy bound what the walk kernel can reach.
 #include <cstring>

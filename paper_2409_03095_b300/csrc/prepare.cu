@@ -120,7 +120,8 @@ __device__ __forceinline__ uint32_t entry_weight(double b, double di, double si,
 }
 
 // One thread per row: the 64-byte slot (header + inline table) or the
-// out-of-line table at [row_ptr[i], row_ptr[i] + deg).
+// out-of-line table at [row_ptr[i], row_ptr[i] + deg); for the compact
+// table the 32-byte record and the FP32 1/d_i.
 //   cumulative: T_m = q_0 + ... + q_m; a draw x = floor(r Q / 2^32) picks
 //               the smallest m with x < T_m.
 //   alias:      Walker/Vose over weights q_j * deg with bucket capacity Q;
