@@ -118,6 +118,42 @@ def test_compact_tables_bit_exact(name):
         assert off == list(cols - i) and neg == [int(-v / d[i] < 0) for v in vals]
 
 
+def _banded(n, far, seed):
+    """Tridiagonal plus one entry `far` columns to the right of every row that
+    has room (and one to the left of the rows it reaches), signs mixed."""
+    rng = np.random.default_rng(seed)
+    r, c, v = [], [], []
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1, i + far, i - far) if 0 <= j < n]
+        w = rng.uniform(0.2, 1.0, len(nb)) * rng.choice([-1.0, 1.0], len(nb))
+        r += [i] * (len(nb) + 1)
+        c += nb + [i]
+        v += list(w) + [np.abs(w).sum() / 0.8]
+    return synth._from_coo(n, r, c, v)
+
+
+def test_compact_table_column_offset_limit():
+    """|j - i| = 16383 fits the compact record's 16-bit offsets (walks
+    bit-exact against the oracle, both signs of the offset); 16384 does not
+    (AUTO takes the cumulative table, an explicit request is refused)."""
+    orc = _orc()
+    m = _banded(20000, 16383, seed=3)
+    B = mc.DeviceCsr.from_host(m)
+    p = mc.params(chains=64, max_len=64, delta=1e-3, seed=9)
+    assert mc.mcmi_build_ex(B, p).stats.table == mc.TABLE_COMPACT
+    rows = np.array([0, 1, 3616, 16382, 16383, 16384, 19999], dtype=np.int64)
+    orows, d, _ = orc.walk(m, rows=rows, chains=64, max_len=64, delta=1e-3, seed=9, table=orc.TABLE_COMPACT)
+    grows = mc.mcmi_walk_dump(B, mc.params(chains=64, max_len=64, delta=1e-3, seed=9, table=mc.TABLE_COMPACT),
+                              rows, max(len(r["col"]) for r in orows) + 16)
+    assert P.compare_dump(grows, orows, d)[2] <= 1.0
+    m2 = _banded(20000, 16384, seed=3)
+    B2 = mc.DeviceCsr.from_host(m2)
+    assert mc.mcmi_build_ex(B2, p).stats.table == mc.TABLE_CUMULATIVE
+    with pytest.raises(mc.McmiError) as e:
+        mc.mcmi_build_ex(B2, mc.params(chains=8, max_len=8, table=mc.TABLE_COMPACT))
+    assert e.value.status == 1
+
+
 def test_compact_table_refuses_rows_that_do_not_fit():
     for name in ("rand_long", "powerlaw_4k"):
         B = mc.DeviceCsr.from_host(_cases_small()[name])
