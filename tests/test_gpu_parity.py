@@ -349,6 +349,25 @@ def test_build_rows_of_every_length_class():
     _check_build(m, np.unique(picks), 512, 64, 1e-4, 1e-4, 0)
 
 
+def test_build_rows_with_crowded_columns():
+    """Rows of several hundred entries whose columns crowd into narrow
+    ranges far apart (a chain with long walks plus a link 20000 columns
+    away), sorted by the assembly's bitonic network.  Rows against the
+    oracle."""
+    n, far = 40000, 20000
+    rng = np.random.default_rng(12)
+    r, c, v = [], [], []
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1, i + far, i - far) if 0 <= j < n]
+        w = rng.uniform(0.5, 1.0, len(nb))
+        r += [i] * (len(nb) + 1)
+        c += nb + [i]
+        v += list(-w) + [w.sum() / 0.99]
+    m = synth._from_coo(n, r, c, v)
+    M, rp, _, _ = _check_build(m, np.array([0, 10000, 19999, 20000, 39999]), 256, 2000, 1e-7, 0.0, 0)
+    assert np.diff(rp).max() > 300
+
+
 def test_build_through_the_overflow_log():
     """Rows that reach far more columns than a 64-slot on-chip table: visits
     go to the log and are reduced in several hash-range passes."""
