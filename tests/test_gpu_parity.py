@@ -364,7 +364,9 @@ def test_build_rows_with_crowded_columns():
         c += nb + [i]
         v += list(-w) + [w.sum() / 0.99]
     m = synth._from_coo(n, r, c, v)
-    M, rp, _, _ = _check_build(m, np.array([0, 10000, 19999, 20000, 39999]), 256, 2000, 1e-7, 0.0, 0)
+    # FP64 walks: chains of ~1600 transitions would take an FP32 weight
+    # product past the 1e-5 parity bound (about 2t 2^-24 relative)
+    M, rp, _, _ = _check_build(m, np.array([0, 10000, 19999, 20000, 39999]), 256, 2000, 1e-7, 0.0, 0, prec=64)
     assert np.diff(rp).max() > 300
 
 
