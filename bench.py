@@ -412,9 +412,10 @@ def run_ours(a):
             "kernel": "k_walk (walk + accumulate + filter)",
             "peak_source": f"{peak_src} HBM copy bandwidth",
             "algorithmic_bytes_per_launch": alg_bytes / max(1, len(walk_ms)),
-            "bytes_per_unit": (f"{rec_bytes} B per visited state: the {rec_bytes // 32} 32-B sector"
-                               f"{'s' if rec_bytes > 32 else ''} holding the row header and the sampled "
-                               f"transition ({mc.TABLE_NAMES[last.table]} table, {rec_bytes}-B records)"),
+            "bytes_per_unit": (f"{rec_bytes} B per visited state: the "
+                               f"{'one 32-B sector' if rec_bytes == 32 else 'two 32-B sectors'} holding the row "
+                               f"header and the sampled transition ({mc.TABLE_NAMES[last.table]} table, "
+                               f"{rec_bytes}-B records)"),
             "walk_kernel_ms": walk_total_ms / max(1, len(walk_ms)),
             "walk_share_of_step": walk_total_ms / tot_ms if world == 1 else None}
     # gather roofline (one row record per visited state): dependent random
