@@ -61,3 +61,23 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     class A:
         workload, steps, warmup, gpus = "stencil3d_64", 1, 1, 2
     assert bench.run_reference(A()) == 0
+
+
+def test_reference_arm_takes_the_librarys_table_choice():
+    """bench.py's reference arm runs the oracle with the table the library
+    picks automatically: compact for stencils (at most six off-diagonals
+    within 16383 columns), hybrid for long rows, cumulative for short rows
+    that do not fit the compact record."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    import synth
+    assert bench._auto_table(synth.stencil3d_7pt(6, seed=1)) == 3
+    assert bench._auto_table(synth.stencil2d_5pt(8, 8, seed=1)) == 3
+    assert bench._auto_table(synth.powerlaw_random(2000, seed=2)) == 2
+    # short rows, one column 20000 away: the compact record's offsets do not reach it
+    n = 20001
+    rows = np.concatenate([np.arange(n), [0]])
+    cols = np.concatenate([np.arange(n), [20000]])
+    vals = np.concatenate([np.full(n, 4.0), [1.0]])
+    assert bench._auto_table(synth._from_coo(n, rows, cols, vals)) == 0
