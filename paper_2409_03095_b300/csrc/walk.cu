@@ -993,7 +993,34 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 }
             };
             uint32_t vstar = 0, cstar_inv = 0;
-            if (select) {
+            if (select && compact && nc <= 64u) {
+                // few candidates: warp 0 ranks the keys (magnitude bits << 32 |
+                // ~col; larger is preferred) by shuffles, two per lane; the
+                // top_k-th key gives the magnitude and tie bounds of the rule
+                if (tid < 32) {
+                    auto key_of = [&](uint32_t i) -> unsigned long long {
+                        const uint32_t c = list_at(i);
+                        const uint32_t col = c < (uint32_t)H ? s_keys[c] : ec[c - H];
+                        const VT v = c < (uint32_t)H ? sval(c) : dec(ev[c - H]);
+                        return ((unsigned long long)__float_as_uint(fabsf((float)v)) << 32) | (~col);
+                    };
+                    const uint32_t l = (uint32_t)tid;
+                    const unsigned long long K0 = l < nc ? key_of(l) : 0ull;           // 0: no entry
+                    const unsigned long long K1 = l + 32u < nc ? key_of(l + 32u) : 0ull;
+                    int r0 = 0, r1 = 0;
+                    for (int j = 0; j < 32; ++j) {
+                        const unsigned long long x0 = __shfl_sync(0xFFFFFFFFu, K0, j);
+                        const unsigned long long x1 = __shfl_sync(0xFFFFFFFFu, K1, j);
+                        r0 += (x0 > K0) + (x1 > K0);
+                        r1 += (x0 > K1) + (x1 > K1);
+                    }
+                    if (l < nc && r0 == a.top_k - 1) s_pass_lo = K0;
+                    if (l + 32u < nc && r1 == a.top_k - 1) s_pass_lo = K1;
+                }
+                __syncthreads();
+                vstar = (uint32_t)(s_pass_lo >> 32);
+                cstar_inv = (uint32_t)s_pass_lo;
+            } else if (select) {
                 // magnitude bits of compact candidate i
                 auto cand_mag = [&](uint32_t i) -> uint32_t {
                     const uint32_t c = list_at(i);
