@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kAsmLongThreads) k_assemble_long(
                 }
             }
         }
-        __syncthreads();   // list and nlist are rewritten by the next round
+        __syncthreads();   // list and nlist are rewritten in the next iteration
     }
 }
 

@@ -742,7 +742,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             const bool by_warp = 2 * B <= H;
             if (by_warp) {
                 unsigned long long *scratch = reinterpret_cast<unsigned long long *>(s_lo) + (tid & ~31);
-                constexpr int UB = 2;   // buckets per round: their loads are in flight together
+                constexpr int UB = 2;   // buckets per iteration: their loads are in flight together
                 const int nw = B >> 5;
                 for (int bk0 = tid >> 5; bk0 < 256; bk0 += UB * nw) {
                     uint2 key[UB];
