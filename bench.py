@@ -443,8 +443,19 @@ def run_ours(a):
     quality = None
     if not a.no_quality:
         try:
-            qrows = np.random.default_rng(5).choice(m.n, 16, replace=False)
-            eps_hat, _ = _estimator_error(mc, B, m, p, qrows, _exact_rows(mc, m, p.alpha, qrows))
+            # up to 1024 seeded sample rows (all rows of a smaller matrix), in
+            # chunks of 128, within about 40 s of exact solves
+            qrows = np.random.default_rng(5).choice(m.n, min(1024, m.n), replace=False)
+            errs, done, tq = [], 0, time.perf_counter()
+            for c0 in range(0, len(qrows), 128):
+                if c0 and time.perf_counter() - tq > 40.0:
+                    break
+                ch = qrows[c0:c0 + 128]
+                e, _ = _estimator_error(mc, B, m, p, ch, _exact_rows(mc, m, p.alpha, ch))
+                errs.append(e * len(ch))
+                done += len(ch)
+            qrows = qrows[:done]
+            eps_hat = float(sum(errs) / done)
             quality = {"eps_hat": eps_hat, "sample_rows": len(qrows),
                        "definition": "mean relative L2 error of unfiltered rows against exact rows of B^-1 "
                                      "(FP64 BiCGstab on B^T to 1e-11)"}
@@ -498,7 +509,7 @@ def _exact_rows(mc, m, alpha, rows):
 def _estimator_error(mc, B, m, p, rows, exact):
     """eps_hat: mean over sample rows of ||X_i - x_i*||_2 / ||x_i*||_2 for the
     unfiltered estimate X_i (the parity dump of the same walks)."""
-    dump = mc.mcmi_walk_dump(B, p, rows, 400000)
+    dump = mc.mcmi_walk_dump(B, p, rows, min(400000, m.n))
     errs = []
     for g, xe in zip(dump, exact):
         est = np.zeros(m.n)
