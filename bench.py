@@ -623,8 +623,9 @@ def run_batched(a):
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
     Ms, st = mc.mcmi_build_batched(Bs, p)          # warm-up with the autotuner
     del Ms
-    p.threads, p.chains_per_thread, p.hash_log2, p.table = st.threads, st.chains_per_thread, st.hash_log2, st.table
-    p.load_depth = st.load_depth
+    # later builds keep the tuned launch shape; the table type and the load
+    # depth stay automatic, so that a batch mixing table types keeps its split
+    p.threads, p.chains_per_thread, p.hash_log2 = st.threads, st.chains_per_thread, st.hash_log2
     for _ in range(max(0, a.warmup - 1)):
         Ms, st = mc.mcmi_build_batched(Bs, p)
         del Ms

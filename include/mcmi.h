@@ -189,9 +189,14 @@ mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_
  * Ms[b] equals what mcmi_build_ex gives for Bs[b] alone with the same
  * parameters and table type.  If p->threads, p->chains_per_thread and
  * p->hash_log2 are all 0, mcmi_autotune picks them (and the table type if
- * AUTO) on the batch.  Bs: host array of device CSRs; Ms: host array of
- * `count` handles, set on success (NULL on error); stats: optional
- * aggregate.  Row ranges are not allowed.  Synchronises `stream`.       */
+ * AUTO) on the batch.  With p->table AUTO (FIXED64 accumulator, no
+ * learned proposal), a batch in which the compact table fits some matrices
+ * but not others is built as two batches, one per group (each autotuned as
+ * above when the shape is 0); stats then sum the two, and report the table
+ * and launch shape of the group with more rows.  Bs: host array of device
+ * CSRs; Ms: host array of `count` handles, set on success (NULL on error);
+ * stats: optional aggregate.  Row ranges are not allowed.  Synchronises
+ * `stream`.                                                              */
 mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_params *p, void *stream,
                                mcmi_matrix *Ms, mcmi_stats *stats);
 

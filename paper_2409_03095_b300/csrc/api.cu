@@ -857,8 +857,8 @@ mcmi_status mcmi_build(const mcmi_csr *B, double eps, double delta, int32_t chai
     return mcmi_build_ex(B, &p, stream, M_out, nullptr);
 }
 
-mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_params *p_in, void *stream,
-                               mcmi_matrix *Ms, mcmi_stats *stats)
+static mcmi_status batched_impl(const mcmi_csr *Bs, int32_t count, const mcmi_params *p_in, void *stream,
+                                mcmi_matrix *Ms, mcmi_stats *stats)
 {
     if (!Bs || !Ms || count < 1) return fail(MCMI_ERR_ARG, "batched build needs count >= 1 matrices and outputs");
     for (int32_t b = 0; b < count; ++b) Ms[b] = nullptr;
@@ -1079,6 +1079,83 @@ mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_par
         stats->threads = W.threads;
         stats->chains_per_thread = W.cpt;
         stats->load_depth = W.depth;
+    }
+    return MCMI_OK;
+}
+
+// A batch whose matrices differ in table type (AUTO choosing the compact
+// table for some and not for others) is built as two batches, one per group,
+// so that the stencil-like matrices keep their 32-byte records; the outputs
+// keep the callers' order.
+mcmi_status mcmi_build_batched(const mcmi_csr *Bs, int32_t count, const mcmi_params *p_in, void *stream,
+                               mcmi_matrix *Ms, mcmi_stats *stats)
+{
+    if (!Bs || !Ms || count < 1 || !p_in) return batched_impl(Bs, count, p_in, stream, Ms, stats);
+    const bool may_split = count > 1 && p_in->table == MCMI_TABLE_AUTO && p_in->accumulator == MCMI_ACC_FIXED64 &&
+                           !p_in->proposal && !p_in->row_begin && !p_in->row_end;
+    if (!may_split) return batched_impl(Bs, count, p_in, stream, Ms, stats);
+    for (int32_t b = 0; b < count; ++b) {
+        Ms[b] = nullptr;
+        mcmi_status r = check_csr(&Bs[b]);
+        if (r != MCMI_OK || Bs[b].n < 1) return batched_impl(Bs, count, p_in, stream, Ms, stats);   // reports it
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<unsigned long long> fit(2 * (size_t)count);
+    {
+        Scratch S(s);
+        std::vector<BatchIn> in(count);
+        for (int32_t b = 0; b < count; ++b) in[b] = BatchIn{Bs[b].row_ptr, Bs[b].col, Bs[b].val, Bs[b].n, Bs[b].nnz, 0, 0};
+        BatchIn *d_in = S.get<BatchIn>(count);
+        unsigned long long *d_fit = S.get<unsigned long long>(2 * (size_t)count);
+        if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (batch table check)");
+        cudaError_t e = cudaMemcpyAsync(d_in, in.data(), sizeof(BatchIn) * count, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = launch_fit_stats(d_in, count, d_fit, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(fit.data(), d_fit, sizeof(unsigned long long) * 2 * count, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "batch table check");
+    }
+    std::vector<int32_t> grp[2];
+    for (int32_t b = 0; b < count; ++b) {
+        const bool fits = fit[2 * b] <= (unsigned long long)kCompactMaxDeg && fit[2 * b + 1] <= (unsigned long long)kCompactMaxOff;
+        grp[fits ? 0 : 1].push_back(b);
+    }
+    if (grp[0].empty() || grp[1].empty()) return batched_impl(Bs, count, p_in, stream, Ms, stats);
+    mcmi_stats st[2];
+    int64_t rows[2] = {0, 0};
+    for (int g = 0; g < 2; ++g) {
+        std::vector<mcmi_csr> sub;
+        for (int32_t b : grp[g]) {
+            sub.push_back(Bs[b]);
+            rows[g] += Bs[b].n;
+        }
+        std::vector<mcmi_matrix> out(sub.size(), nullptr);
+        memset(&st[g], 0, sizeof(mcmi_stats));
+        mcmi_status r = batched_impl(sub.data(), (int32_t)sub.size(), p_in, stream, out.data(), &st[g]);
+        if (r != MCMI_OK) {
+            for (int32_t b = 0; b < count; ++b) {
+                if (Ms[b]) mcmi_free(Ms[b]);
+                Ms[b] = nullptr;
+            }
+            return r;
+        }
+        for (size_t k = 0; k < out.size(); ++k) Ms[grp[g][k]] = out[k];
+    }
+    if (stats) {
+        const mcmi_stats &big = rows[0] >= rows[1] ? st[0] : st[1];
+        *stats = big;   // table, launch shape and chains of the group with more rows
+        stats->steps = st[0].steps + st[1].steps;
+        stats->rows = st[0].rows + st[1].rows;
+        stats->nnz = st[0].nnz + st[1].nnz;
+        stats->max_s = st[0].max_s > st[1].max_s ? st[0].max_s : st[1].max_s;
+        stats->max_len_bound = st[0].max_len_bound > st[1].max_len_bound ? st[0].max_len_bound : st[1].max_len_bound;
+        stats->spilled = st[0].spilled + st[1].spilled;
+        stats->deferred_rows = st[0].deferred_rows + st[1].deferred_rows;
+        stats->ms_prepare = st[0].ms_prepare + st[1].ms_prepare;
+        stats->ms_walk = st[0].ms_walk + st[1].ms_walk;
+        stats->ms_assemble = st[0].ms_assemble + st[1].ms_assemble;
+        stats->ms_walk_kernel = st[0].ms_walk_kernel + st[1].ms_walk_kernel;
+        stats->launches = st[0].launches + st[1].launches + 1;
     }
     return MCMI_OK;
 }

@@ -17,6 +17,35 @@ __device__ __forceinline__ int find_block(const int64_t *base, int count, int64_
     return lo;
 }
 
+// per matrix of a batch: the largest off-diagonal count of a row (out[2b])
+// and the largest |j - i| of an off-diagonal entry (out[2b + 1]); blockIdx.y
+// + y0 is the matrix
+__global__ void k_fit_stats(const BatchIn *in, int y0, unsigned long long *out)
+{
+    const int b = y0 + (int)blockIdx.y;
+    const BatchIn m = in[b];
+    unsigned long long dmax = 0, omax = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m.n; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long deg = 0;
+        for (int64_t k = m.rp[i]; k < m.rp[i + 1]; ++k) {
+            const long long o = (long long)m.col[k] - (long long)i;
+            if (o == 0) continue;
+            ++deg;
+            const unsigned long long ao = (unsigned long long)(o < 0 ? -o : o);
+            omax = ao > omax ? ao : omax;
+        }
+        dmax = deg > dmax ? deg : dmax;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = max(dmax, __shfl_xor_sync(0xFFFFFFFFu, dmax, o));
+        omax = max(omax, __shfl_xor_sync(0xFFFFFFFFu, omax, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&out[2 * b], dmax);
+        atomicMax(&out[2 * b + 1], omax);
+    }
+}
+
 __global__ void k_concat_rows(const BatchIn *in, int count, const int64_t *row_base, int64_t total_rows,
                               int64_t total_nnz, int64_t *rp)
 {
@@ -83,6 +112,16 @@ int grid_for(int64_t work)
 }
 
 }  // namespace
+
+cudaError_t launch_fit_stats(const BatchIn *in, int count, unsigned long long *out, cudaStream_t s)
+{
+    cudaMemsetAsync(out, 0, sizeof(unsigned long long) * 2 * (size_t)count, s);
+    for (int y0 = 0; y0 < count; y0 += 65535) {
+        const int ny = count - y0 < 65535 ? count - y0 : 65535;
+        k_fit_stats<<<dim3(4, (unsigned)ny), 256, 0, s>>>(in, y0, out);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_concat(const BatchIn *in, int count, const int64_t *row_base, const int64_t *nnz_base,
                           int64_t total_rows, int64_t total_nnz, int64_t *rp, int32_t *col, double *val,

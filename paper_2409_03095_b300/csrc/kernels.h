@@ -64,6 +64,9 @@ struct BatchOut {
     float *val;
     int64_t n, row_base, nnz_base;   // nnz_base: first entry of this matrix in the batched M
 };
+// per matrix b: out[2b] = largest off-diagonal count of a row, out[2b + 1] =
+// largest |j - i| (device, 2 count words)
+cudaError_t launch_fit_stats(const BatchIn *in, int count, unsigned long long *out, cudaStream_t s);
 cudaError_t launch_concat(const BatchIn *in, int count, const int64_t *row_base, const int64_t *nnz_base,
                           int64_t total_rows, int64_t total_nnz, int64_t *rp, int32_t *col, double *val,
                           cudaStream_t s);

@@ -65,6 +65,26 @@ def test_batched_compact_equals_individual_builds(table):
             assert np.array_equal(u, v)
 
 
+def test_batched_split_by_table_type_equals_individual_builds():
+    """A batch of stencils and power-law matrices with the table left to AUTO:
+    the stencils take the compact table and the others the hybrid one, each
+    group in its own batch; every M equals the matrix's own AUTO build."""
+    mats = _mats()
+    Bs = [mc.DeviceCsr.from_host(m) for m in mats]
+    kw = dict(chains=96, max_len=100, delta=1e-3, filter_tau=1e-2, top_k=8, seed=77, threads=128,
+              chains_per_thread=1, hash_log2=11)
+    Ms, st = mc.mcmi_build_batched(Bs, mc.params(**kw))
+    assert st.rows == sum(m.n for m in mats)
+    tables, steps = set(), 0
+    for B, M in zip(Bs, Ms):
+        Mi = mc.mcmi_build_ex(B, mc.params(**kw))
+        tables.add(Mi.stats.table)
+        steps += Mi.stats.steps
+        for u, v in zip(_csr(M), _csr(Mi)):
+            assert np.array_equal(u, v)
+    assert tables == {mc.TABLE_COMPACT, mc.TABLE_HYBRID} and st.steps == steps
+
+
 def test_batched_fixed_shape_and_errors():
     mats = _mats()[:3]
     Bs = [mc.DeviceCsr.from_host(m) for m in mats]

@@ -94,11 +94,14 @@ def test_full_size_batched_sampled_rows():
     Bs = [mc.DeviceCsr.from_host(m) for m in mats]
     p = mc.params(chains=128, max_len=128, delta=1e-3, top_k=16, seed=SEED)
     Ms, st = mc.mcmi_build_batched(Bs, p)
-    q = mc.params(chains=128, max_len=128, delta=1e-3, top_k=16, seed=SEED, table=st.table,
-                  threads=st.threads, chains_per_thread=st.chains_per_thread, hash_log2=st.hash_log2)
     for b in (0, 1, 2, 22, 23):
+        # the table the batch gave this matrix: its own automatic choice (the
+        # batch splits compact-table matrices from the others)
+        tb = mc.mcmi_build_ex(Bs[b], mc.params(chains=1, max_len=0)).stats.table
+        q = mc.params(chains=128, max_len=128, delta=1e-3, top_k=16, seed=SEED, table=tb,
+                      threads=st.threads, chains_per_thread=st.chains_per_thread, hash_log2=st.hash_log2)
         _check(f"batch matrix {b} (n={mats[b].n})", mats[b], Bs[b], q, Ms[b], _sample(mats[b].n, 8, b),
-               st.table, 0.0, 16)
+               tb, 0.0, 16)
 
 
 def test_full_size_learned_sampled_rows():
