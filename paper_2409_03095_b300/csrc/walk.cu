@@ -395,21 +395,35 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // All lanes of a warp run every iteration (the loop test is a warp
         // vote), so that the shared atomics of a step are issued by the whole
         // warp at once; lanes without a live chain only take part in the votes.
+        // Every chain takes its step t = 0 in an iteration whose number is a
+        // multiple of 4 (a lane whose chain stopped waits up to 3 iterations,
+        // t < 0, before the next one starts), so that t = it (mod 4) for every
+        // live chain and the Philox blocks of a warp are drawn together.
         const uint32_t lane = (uint32_t)tid & 31u;
+        uint32_t it = 0;
 #pragma unroll 1
         while (__any_sync(0xFFFFFFFFu, k[0] < a.N || (CPT > 1 && k[CPT - 1] < a.N))) {
             uint32_t s[CPT][16];
             double2 rd[CPT];
 #pragma unroll
             for (int j = 0; j < CPT; ++j)
-                if (k[j] < a.N) {
+                if (k[j] < a.N && t[j] >= 0) {
                     if (CMP) load_rec32(a.slots + 2 * (size_t)st[j], s[j]);
                     else load_slot(a.slots + 4 * (size_t)st[j], s[j]);
                     if (PREC == 64) rd[j] = __ldg(a.rowd + st[j]);
                 }
+            // the block of step t (Eq. 2's draws, four per counter), computed
+            // while the gathers are in flight; a chain that stops in this
+            // iteration, or has not started, draws a block it does not use
+            const uint32_t ph = it & 3u;
+            if (ph == 0u) {
+#pragma unroll
+                for (int j = 0; j < CPT; ++j)
+                    r4[j] = philox4x32_10(make_uint4((uint32_t)(t[j] >> 2), (uint32_t)k[j], rlo, rhi), a.key0, a.key1);
+            }
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
-                const bool live = k[j] < a.N;
+                const bool live = k[j] < a.N && t[j] >= 0;
                 const bool acc = live && t[j] > 0;   // the visit of st[j] (t = 0 is counted at the row start)
                 unsigned long long add = 0ull;
                 int h = -1;
@@ -445,7 +459,10 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         }
                     }
                 }
-                if (!live) continue;
+                if (!live) {
+                    t[j] += t[j] < 0;   // waiting for an iteration that is a multiple of 4
+                    continue;
+                }
                 const uint32_t Q = record_q<TABLE>(s[j]);
                 if (t[j] == a.L || !(fabsf(w[j]) >= a.delta_f) || Q == 0u) {
                     my_steps += (unsigned long long)t[j];
@@ -453,13 +470,10 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     st[j] = (uint32_t)row;
                     w[j] = 1.0f;
                     w64[j] = 1.0;
-                    t[j] = 0;
+                    t[j] = -(int)(3u - ph);   // its step 0 comes in the next iteration that is a multiple of 4
                     continue;
                 }
-                if ((t[j] & 3) == 0)
-                    r4[j] = philox4x32_10(make_uint4((uint32_t)(t[j] >> 2), (uint32_t)k[j], rlo, rhi), a.key0, a.key1);
-                const int ph = t[j] & 3;
-                const uint32_t r = ph == 0 ? r4[j].x : ph == 1 ? r4[j].y : ph == 2 ? r4[j].z : r4[j].w;
+                const uint32_t r = ph == 0u ? r4[j].x : ph == 1u ? r4[j].y : ph == 2u ? r4[j].z : r4[j].w;
                 float fl;
                 const uint32_t cs = pick_transition<TABLE>(s[j], r, a, &fl, st[j]);
                 const bool neg = (cs & kNegBit) != 0u;
@@ -468,6 +482,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 st[j] = cs & ~kNegBit;
                 ++t[j];
             }
+            ++it;
         }
         __syncthreads();
 
