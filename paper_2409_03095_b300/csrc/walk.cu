@@ -241,7 +241,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     __shared__ uint32_t s_digit, s_rank;
 
     const int tid = threadIdx.x, B = blockDim.x;
-    const uint32_t fill_cap = (uint32_t)(H - (H >> 2));      // on-chip table kept <= 75% full
+    // on-chip table kept <= 87.5% full during the walks with the compact table
+    // (banded rows: a 64^3 7-point stencil row visits up to ~1600 columns, all
+    // of which then stay in a 2^11-slot table), <= 75% with the others (rows
+    // that overflow anyway gain more from shorter probes)
+    const uint32_t fill_cap = (uint32_t)(H - (H >> (CMP ? 3 : 2)));
     // log: the visits in arrival order, then the same entries bucketed by hash range
     uint2 *lc = a.log_key + (size_t)blockIdx.x * 2 * a.log_cap;
     unsigned long long *lv = a.log_val + (size_t)blockIdx.x * 2 * a.log_cap;
@@ -826,7 +830,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             // per_pass of their entries (so at most per_pass distinct columns)
             // through the on-chip table; a pass that still does not fit is
             // retried on the lower half of its range.
-            const uint32_t per_pass = fill_cap - (fill_cap >> 2);
+            const uint32_t per_pass = (uint32_t)(H - (H >> 2)) - (uint32_t)((H - (H >> 2)) >> 2);
             unsigned long long lo = 0, retry_hi = 0;
             for (;;) {
                 __syncthreads();
