@@ -123,9 +123,12 @@ def _peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-def _traffic(kernel_src):
-    """DRAM bytes per walk launch from the committed ncu summary, if it was
-    taken on the current kernel source (else null)."""
+def _traffic(kernel_src, workload):
+    """DRAM bytes per walk launch from the committed ncu summary of the
+    stencil3d_64 workload, if it was taken on the current kernel source (else
+    null; null for every other workload)."""
+    if workload != "stencil3d_64":
+        return None
     path = os.path.join(ROOT, "profiles", "walk_stencil3d_64_traffic.txt")
     try:
         kv = dict(l.split(":", 1) for l in open(path).read().splitlines() if ":" in l)
@@ -406,7 +409,7 @@ def run_ours(a):
     rec_bytes = 32 if last.table == mc.TABLE_COMPACT else SLOT_BYTES   # bytes of one row record
     alg_bytes = rec_bytes * visits
     achieved = alg_bytes / (walk_total_ms / 1e3) / 1e9
-    traffic = _traffic(os.path.join(ROOT, "paper_2409_03095_b300", "csrc", "walk.cu"))
+    traffic = _traffic(os.path.join(ROOT, "paper_2409_03095_b300", "csrc", "walk.cu"), a.workload)
     roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
             "kernel": "k_walk (walk + accumulate + filter)",
