@@ -325,15 +325,20 @@ def test_build_staging_regrowth_reruns_rows():
 
 def test_build_rows_of_every_length_class():
     """The CSR assembly orders a row by column in ways that depend on its
-    length (up to a warp, up to 1024 entries, one 4096-entry tile, several
-    tiles): rows of each class against the oracle."""
+    length (up to a warp by shuffle ranks, up to 1024 entries by a warp in
+    shared memory, padded to 64 ... 1024, one 4096-entry tile, several
+    tiles): rows of each class against the oracle, and every row of the
+    build strictly increasing in column."""
     m = synth.powerlaw_random(4096, seed=9)
     B = mc.DeviceCsr.from_host(m)
     p = mc.params(chains=256, max_len=64, delta=1e-4, seed=11, filter_tau=3e-3)
-    rp = mc.mcmi_build_ex(B, p).to_torch()[0].cpu().numpy()
+    rp, col, _ = (t.cpu().numpy() for t in mc.mcmi_build_ex(B, p).to_torch())
     ln = np.diff(rp)
+    inner = np.ones(col.size, dtype=bool)
+    inner[rp[:-1][ln > 0]] = False          # first entry of each row
+    assert np.all(np.diff(col.astype(np.int64))[inner[1:]] > 0)
     picks = []
-    for lo, hi in ((0, 32), (33, 1024), (1025, 1 << 30)):
+    for lo, hi in ((0, 32), (33, 64), (65, 128), (129, 256), (257, 512), (513, 1024), (1025, 1 << 30)):
         idx = np.flatnonzero((ln >= lo) & (ln <= hi))
         assert idx.size > 0, (lo, hi, ln.min(), ln.max())
         picks += [idx[0], idx[-1], idx[idx.size // 2]]
