@@ -149,6 +149,42 @@ __device__ __forceinline__ void bitonic_shared(unsigned long long *a, int P, int
     }
 }
 
+// bitonic_shared for one warp and a compile-time P: each lane first loads
+// the pairs of all its comparators of a step (they are disjoint), then
+// compares and stores, so the loads of a step are in flight together
+// instead of each waiting for the stores before it
+template <int P>
+__device__ __forceinline__ void bitonic_warp_batched(unsigned long long *a, int t)
+{
+    constexpr int C = P / 64;             // comparators per lane and step
+    constexpr int CB = C < 8 ? C : 8;     // taken in batches of at most 8 (registers)
+#pragma unroll 1
+    for (int k = 2; k <= P; k <<= 1) {
+#pragma unroll 1
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const bool mirror = j == (k >> 1);   // first step of a merge: (i, i ^ (k - 1))
+#pragma unroll
+            for (int c0 = 0; c0 < C; c0 += CB) {
+                int lo[CB];
+                unsigned long long x[CB], y[CB];
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    lo[c] = (int)pair_lo(t + 32 * (c0 + c), j);
+                    x[c] = a[lo[c]];
+                    y[c] = a[mirror ? (lo[c] ^ (k - 1)) : (lo[c] + j)];
+                }
+#pragma unroll
+                for (int c = 0; c < CB; ++c)
+                    if (x[c] > y[c]) {
+                        a[lo[c]] = y[c];
+                        a[mirror ? (lo[c] ^ (k - 1)) : (lo[c] + j)] = x[c];
+                    }
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // rows of at most wmax entries (32, or kAsmWarpMax with kAsmWarpMax keys of
 // dynamic shared memory per warp), one warp per row; longer rows are left to
 // k_assemble_long
@@ -183,7 +219,13 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(
             while (P < cnt) P <<= 1;
             for (int i = lane; i < P; i += 32) key[i] = i < cnt ? pack_entry(st_col[off + i], st_val[off + i]) : kKeyInf;
             __syncwarp();
-            bitonic_shared<32, true>(key, P, lane);
+            switch (P) {
+            case 64: bitonic_warp_batched<64>(key, lane); break;
+            case 128: bitonic_warp_batched<128>(key, lane); break;
+            case 256: bitonic_warp_batched<256>(key, lane); break;
+            case 512: bitonic_warp_batched<512>(key, lane); break;
+            default: bitonic_warp_batched<1024>(key, lane); break;
+            }
             for (int i = lane; i < cnt; i += 32) {
                 const unsigned long long x = key[i];
                 out_col[dst + i] = (int32_t)(x >> 32);
