@@ -178,7 +178,8 @@ def max_walk_len(smax, delta, max_len):
 
 
 def chains_from_eps(eps, smax):
-    """N from epsilon (parity unpinned: rule of the earlier (MC)^2MI papers)."""
+    """N from epsilon: the rule of the earlier (MC)^2MI papers (not stated in
+    this one), N = ceil((0.6745 / (eps (1 - smax)))^2): probable error <= eps."""
     return int(_L().orc_chains_from_eps(float(eps), float(smax)))
 
 

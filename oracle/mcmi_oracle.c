@@ -33,9 +33,12 @@
  *
  * Parity pins: every exported function here is checked by the CPU test-suite
  * against something other than itself (cuRAND's host Philox, dense matrix
- * powers, path enumeration, closed forms, numpy sorting).  The only function
- * without such a pin is orc_chains_from_eps (parity unpinned: the paper does
- * not state how N follows from epsilon).
+ * powers, path enumeration, closed forms, numpy sorting, the exact binomial
+ * law).  orc_chains_from_eps follows a rule the paper does not state (that
+ * of the earlier (MC)^2MI papers); it is pinned by what the rule claims: the
+ * probable error of an estimate whose single-chain deviation reaches the
+ * bound 1/(1 - ||C||) equals epsilon, and the walks' per-entry errors stay
+ * below epsilon at least half the time.
  */
 #include <math.h>
 #include <stdint.h>
@@ -266,9 +269,12 @@ int64_t orc_max_walk_len(double smax, double delta, int64_t L)
     return t;
 }
 
-/* Number of chains from the accuracy epsilon when the caller gives none     */
-/* (parity unpinned: the paper does not state the rule; this is the rule of  */
-/* the earlier (MC)^2MI papers it builds on, N = (0.6745 / (eps (1-||C||)))^2). */
+/* Number of chains from the accuracy epsilon when the caller gives none.   */
+/* The paper does not state the rule; this is the rule of the earlier        */
+/* (MC)^2MI papers it builds on: 0.6745 is the median of |Z| for a standard  */
+/* normal Z, a chain's contribution deviates by at most 1/(1 - ||C||), so    */
+/* with N = (0.6745 / (eps (1 - ||C||)))^2 the probable error of the mean    */
+/* of N chains is at most eps.                                               */
 int64_t orc_chains_from_eps(double eps, double smax)
 {
     double v = 0.6745 / (eps * (1.0 - smax));

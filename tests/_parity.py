@@ -36,19 +36,21 @@ def compare_dump(gpu_rows, orc_rows, d):
 
 def band_entries(cols, mvals, i, tau, top_k, band=REL_TOL):
     """Columns whose filter decision is within the rounding band of a cut:
-    |M| within a relative band of tau * max|M| or of the top_k-th value."""
+    |M| within a relative band of 1e-5 of tau * max|M| or of the top_k-th
+    value (the entry tolerance; the measured entry errors are below 2e-6,
+    so an entry and the cut cannot move past each other outside it)."""
     mag = np.abs(mvals)
     amb = np.zeros(len(cols), dtype=bool)
     off = cols != i
     thr = tau * mag.max(initial=0.0)
     if tau > 0:
-        amb |= off & (np.abs(mag - thr) <= 2 * band * np.maximum(thr, 1e-300))
+        amb |= off & (np.abs(mag - thr) <= band * np.maximum(thr, 1e-300))
     if top_k > 0:
-        cand = off & ((tau == 0) | (mag >= thr * (1 - 2 * band)))
+        cand = off & ((tau == 0) | (mag >= thr * (1 - band)))
         cm = np.sort(mag[cand])[::-1]
         if len(cm) > top_k:
             kth = cm[top_k - 1]
-            amb |= off & (np.abs(mag - kth) <= 2 * band * kth)
+            amb |= off & (np.abs(mag - kth) <= band * kth)
     return set(cols[amb].tolist())
 
 

@@ -53,9 +53,9 @@ def test_bicgstab_matches_scipy(name):
         Mop = _scipy_M(M, m.n) if Mh is not None else None
         xr, its, info = _scipy_bicgstab_iters(A, bh, Mop, 1e-8)
         assert info == 0
-        # same algorithm (right-preconditioned BiCGstab); on nonsymmetric
-        # problems its iteration count moves with rounding
-        assert abs(it - its) <= max(3, int(0.15 * its)), (it, its)
+        # same algorithm (right-preconditioned BiCGstab), same M: iteration
+        # counts within 2 of scipy's
+        assert abs(it - its) <= 2, (it, its)
     it_m, _ = mc.mcmi_solve(B, M, b, x, mc.SOLVE_BICGSTAB, rtol=1e-8)
     it_0, _ = mc.mcmi_solve(B, None, b, x, mc.SOLVE_BICGSTAB, rtol=1e-8)
     assert it_m < it_0, (it_m, it_0)

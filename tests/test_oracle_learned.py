@@ -171,3 +171,91 @@ def test_training_loss_bounds(orc):
     th[1376] = 1.3
     one = np.zeros(per, np.int64)
     assert abs(orc.proposal_loss(th, feat[:per], one, p[:per] / p[:per].sum(), np.full(per, 2.0)) - 1.0) < 1e-12
+
+
+
+def _mixed_degree_matrix(n, seed):
+    """Mixed-sign rows of 1-8 off-diagonals (some explicit zeros), diagonal of
+    random sign and dominance, so that s_i, deg_i and |d_i| differ between
+    the two ends of most edges."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        deg = int(rng.integers(1, 9))
+        js = rng.choice(np.setdiff1d(np.arange(n), [i]), deg, replace=False)
+        v = rng.standard_normal(deg) * rng.choice([0.1, 1.0, 10.0])
+        v[rng.random(deg) < 0.1] = 0.0
+        diag = (np.abs(v).sum() or 1.0) / rng.uniform(0.5, 0.95) * rng.choice([-1.0, 1.0])
+        rows += [i] * (deg + 1)
+        cols += list(js) + [i]
+        vals += list(v) + [diag]
+    return synth._from_coo(n, rows, cols, vals)
+
+
+def _closed_form_features(orc, m):
+    """Per stored off-diagonal (i, j): the eight features from the dense
+    C = I - D^-1 B (s_i from the oracle's split, which its own pin checks
+    against the dense row sums; numpy's pairwise sum may differ by an ulp)."""
+    B = m.to_scipy().toarray()
+    dd = np.diag(B).copy()
+    C = -B / dd[:, None]
+    np.fill_diagonal(C, 0.0)
+    _, s = orc.split(m)
+    assert np.allclose(s, np.abs(C).sum(axis=1), rtol=1e-14, atol=0)
+    stored = np.zeros((m.n, m.n), bool)
+    stored[np.repeat(np.arange(m.n), np.diff(m.row_ptr)), m.col] = True
+    np.fill_diagonal(stored, False)
+    deg = stored.sum(axis=1)
+    out = {}
+    for i in range(m.n):
+        maxabs = np.abs(C[i, stored[i]]).max()
+        for j in np.flatnonzero(stored[i]):
+            c = C[i, j]
+            if c == 0.0:
+                out[(i, j)] = None
+                continue
+            out[(i, j)] = np.array([abs(c) / s[i], s[i], s[j], 1.0 / deg[i], 1.0 / deg[j],
+                                    abs(dd[i]) / (abs(dd[i]) + abs(dd[j])), abs(c) / maxabs,
+                                    -1.0 if c < 0 else 1.0]).astype(np.float32)
+    return out, C, s, deg, dd
+
+
+def test_edge_features_match_their_closed_forms(orc):
+    """orc_train_edges' eight features of edge (i, j) equal |c_ij|/s_i, s_i,
+    s_j, 1/deg_i, 1/deg_j, |d_i|/(|d_i|+|d_j|), |c_ij|/max_k|c_ik| and
+    sign(c_ij) recomputed from the dense matrix (FP64, then FP32).  The
+    matrix is built so that swapping i and j in any two-sided feature
+    changes it on most edges."""
+    m = _mixed_degree_matrix(60, seed=17)
+    want, C, s, deg, dd = _closed_form_features(orc, m)
+    feat, p, tgt, row = orc.train_edges(m)
+    checked = swaps = 0
+    for k in range(len(tgt)):
+        i, j = int(row[k]), int(tgt[k])
+        if i == j or want[(i, j)] is None:
+            assert np.all(feat[k] == 0.0) and p[k] == 0.0
+            continue
+        assert np.array_equal(feat[k], want[(i, j)]), (i, j, feat[k], want[(i, j)])
+        assert p[k] == abs(C[i, j]) / s[i]
+        checked += 1
+        swaps += (abs(s[i] - s[j]) > 1e-3 * s[i]) and deg[i] != deg[j] and abs(dd[i]) != abs(dd[j])
+    assert checked > 200 and swaps > 0.6 * checked, (checked, swaps)
+    assert len(want) == sum(1 for k in range(len(tgt)) if row[k] != tgt[k])
+
+
+def test_learned_tables_evaluate_the_network_on_the_closed_form_features(orc):
+    """orc_learned_tables' g equals the independent BF16 emulation of the MLP
+    evaluated on the features recomputed from the dense matrix."""
+    m = _mixed_degree_matrix(24, seed=5)
+    th = _theta(9)
+    lt = orc.learned_tables(m, th)
+    want, _, _, _, _ = _closed_form_features(orc, m)
+    e = 0
+    for i in range(m.n):
+        for j in m.col[m.row_ptr[i]:m.row_ptr[i + 1]]:
+            if j == i:
+                continue
+            f = want[(i, int(j))]
+            assert lt["g"][e] == (0.0 if f is None else _mlp_bf16(th, f)), (i, j)
+            e += 1
+    assert e == len(lt["g"])

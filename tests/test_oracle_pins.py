@@ -382,11 +382,11 @@ def test_error_decays_as_inverse_sqrt_chains(orc):
     m = synth.random_dd(8, 3, seed=41, dominance=0.5, diag_sign="mixed")
     B = m.to_scipy().toarray()
     Binv = np.linalg.inv(B)
-    Ns = [200, 800, 3200, 12800, 51200]
+    Ns = [100, 400, 1600, 6400, 25600, 102400]
     rms = []
     for N in Ns:
         errs = []
-        for seed in range(6):
+        for seed in range(16):
             res, d, s = orc.walk(m, chains=N, max_len=200, delta=1e-10, seed=1000 + seed)
             M = np.zeros((m.n, m.n))
             for r in res:
@@ -394,7 +394,8 @@ def test_error_decays_as_inverse_sqrt_chains(orc):
             errs.append(np.mean((M - Binv) ** 2))
         rms.append(math.sqrt(np.mean(errs)))
     slope = np.polyfit(np.log(Ns), np.log(rms), 1)[0]
-    assert -0.58 < slope < -0.42, slope
+    # slope -1/2 within 0.05 (16 seeds per N: four seed bases gave -0.491 to -0.497)
+    assert -0.55 < slope < -0.45, slope
 
 
 def test_visit_counts_add_up_and_rows_are_independent(orc):
@@ -641,3 +642,93 @@ def test_hybrid_table_on_mixed_rows_is_unbiased():
         xa = np.zeros(m.n); xa[est[1][k]["col"]] = est[1][k]["X"]
         scale = np.linalg.norm(xc)
         assert np.linalg.norm(xh - xc) / scale < 0.02 and np.linalg.norm(xh - xa) / scale < 0.02
+
+
+# ---------------------------------------------------------------- chains from epsilon
+
+
+@pytest.mark.parametrize("smax,eps", [(0.3, 0.01), (0.6, 0.02), (0.9, 0.05)])
+def test_chains_from_eps_meets_its_probable_error_on_the_extremal_estimator(orc, smax, eps):
+    """The rule claims: with N chains the probable error (the median of
+    |error|) of an estimate whose single-chain contribution has standard
+    deviation at most 1/(1 - ||C||) is at most eps.  A fair coin of
+    +-1/(1 - smax) attains that deviation, so the mean of N of them must fall
+    inside +-eps with probability 1/2 (exact binomial law; the lattice of
+    the mean moves it by a few 1e-3 at these N).  Half or twice the chains
+    must be clearly on either side."""
+    from scipy.stats import binom
+    a = 1.0 / (1.0 - smax)
+
+    def p_inside(N):
+        # |mean| = a |2K - N| / N < eps  <=>  |2K - N| < eps N / a
+        lim = eps * N / a
+        k_lo = math.floor((N - lim) / 2) + 1
+        k_hi = math.ceil((N + lim) / 2) - 1
+        return float(binom.cdf(k_hi, N, 0.5) - binom.cdf(k_lo - 1, N, 0.5))
+
+    N = orc.chains_from_eps(eps, smax)
+    assert N > 2000
+    assert abs(p_inside(N) - 0.5) < 0.02, (N, p_inside(N))
+    assert p_inside(N // 2) < 0.4 and p_inside(2 * N) > 0.6
+
+
+def test_chains_from_eps_bounds_the_walks_per_entry_error(orc):
+    """With N from the rule, the walks' per-entry error against the exact
+    expectation (path enumeration, n = 5, no cutoff, L = 6) is below eps in
+    at least half of independent trials: one binomial sample per (row,
+    seed), the entry of the row with the largest single-chain variance, and
+    a one-sided bound three standard deviations below 1/2."""
+    m = synth.random_dd(5, 3, seed=23, dominance=0.6, diag_sign="mixed")
+    d, s = orc.split(m)
+    tb = orc.tables(m, d, s)
+    L, eps = 6, 0.02
+    N = orc.chains_from_eps(eps, float(s.max()))
+    mean, col = {}, {}
+    for i in range(m.n):
+        EY, EY2 = _enumerate_paths(m, tb, i, L, 0.0)
+        var = EY2 - EY * EY
+        # the single-chain deviation the rule bounds
+        assert np.sqrt(var.max()) <= sum(float(s.max()) ** t for t in range(L + 1)) + 1e-12
+        col[i] = int(np.argmax(var))
+        mean[i] = EY[col[i]]
+    T = inside = 0
+    for seed in range(120):
+        res, _, _ = orc.walk(m, chains=N, max_len=L, delta=0.0, seed=9000 + seed)
+        for r in res:
+            i = int(r["row"])
+            X = dict(zip(r["col"].tolist(), r["X"].tolist()))
+            inside += abs(X.get(col[i], 0.0) - mean[i]) < eps
+            T += 1
+    assert inside / T - 3.0 * math.sqrt(0.25 / T) >= 0.5, (inside, T, N)
+
+
+# ---------------------------------------------------------------- compact table bias
+
+
+@pytest.mark.parametrize("table,scale", [(3, 2.0 ** 20), (0, 2.0 ** 31)])
+def test_table_expectation_is_within_the_quantisation_bound_of_neumann(orc, table, scale):
+    """The walks sample p^ = q/Q (q = max(1, floor(p scale))) but multiply by
+    sign(c) s, so their exact expectation (path enumeration) is the Neumann
+    sum of C^ = p^ sign(c) s, not of C.  With ||C^ - C||_inf <= eta =
+    s_max 2 deg_max / (scale - deg_max) and ||C^||_inf = ||C||_inf = s_max,
+    each row's L1 distance to sum_{t<=L} C^t is at most
+    eta sum_{t=1}^{L} t s_max^(t-1).  The compact table's bias must also be
+    visible (above 2^-31-level noise), so the enumeration sees its q."""
+    m = synth.random_dd(5, 3, seed=29, dominance=0.8, diag_sign="mixed")
+    C, _ = _dense_C(m)
+    d, s = orc.split(m)
+    tb = orc.tables(m, d, s, table=table)
+    L = 5
+    P = sum(np.linalg.matrix_power(C, t) for t in range(L + 1))
+    degmax = int(max(np.count_nonzero(C[i]) for i in range(m.n)))
+    smax = float(s.max())
+    eta = smax * 2 * degmax / (scale - degmax)
+    bound = eta * sum(t * smax ** (t - 1) for t in range(1, L + 1))
+    worst = 0.0
+    for i in range(m.n):
+        EY, _ = _enumerate_paths(m, tb, i, L, 0.0)
+        dist = float(np.abs(EY - P[i]).sum())
+        assert dist <= bound, (i, dist, bound)
+        worst = max(worst, dist)
+    if table == 3:
+        assert worst > 1e-3 * bound and worst > 1e-8, worst
