@@ -60,10 +60,10 @@ METRIC = "MC walk steps/s"
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)   # about 1 s of timed walks on the default workload: several clock samples
+    ap.add_argument("--steps", type=int, default=20)   # about 5 s of timed builds on the default workload: many clock samples
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stencil3d_64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="powerlaw_1m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64],
@@ -81,6 +81,9 @@ def _args():
     ap.add_argument("--reduce", action="store_true",
                     help="matrix reduction sweep judged by BiCGstab/GMRES on --workload (one JSON line)")
     ap.add_argument("--train-steps", type=int, default=100)
+    ap.add_argument("--shard", action="store_true",
+                    help="one matrix, its rows split over the ranks (Sec. IV-A), CSR pieces gathered over NCCL "
+                         "(strong scaling); default: one independent build per rank (weak scaling)")
     return ap.parse_args()
 
 
@@ -123,19 +126,24 @@ def _peaks():
         return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
 
 
-def _traffic(kernel_src, workload):
-    """DRAM bytes per walk launch from the committed ncu summary of the
-    stencil3d_64 workload, if it was taken on the current kernel source (else
-    null; null for every other workload)."""
-    if workload != "stencil3d_64":
-        return None
-    path = os.path.join(ROOT, "profiles", "walk_stencil3d_64_traffic.txt")
+def _kernel_hash():
+    """Hash of the walk kernel's sources (walk.cu and its internal header)."""
+    h = hashlib.sha256()
+    for f in ("walk.cu", "mcmi_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2409_03095_b300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload):
+    """DRAM bytes per walk launch from the committed ncu summary of this
+    workload (profiles/walk_<workload>_traffic.txt), if it was taken on the
+    current kernel sources; else null."""
+    path = os.path.join(ROOT, "profiles", f"walk_{workload}_traffic.txt")
     try:
         kv = dict(l.split(":", 1) for l in open(path).read().splitlines() if ":" in l)
     except OSError:
         return None
-    src_hash = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
-    if kv.get("walk_cu_sha256_16", "").strip() != src_hash:
+    if kv.get("kernel_sha256_16", "").strip() != _kernel_hash():
         return None
     try:
         return float(kv["dram_bytes_per_launch_full_size"])
@@ -293,6 +301,103 @@ def run_reference(a):
     return 0
 
 
+def _ool_rows(m, table):
+    """Rows whose sampling table the walk reads out of line (one dependent
+    16-byte alias bucket or a search per step): the hybrid table's rows of
+    more than six transitions, the alias table's of more than four, the
+    cumulative table's of more than six; none for the compact table."""
+    rows = np.repeat(np.arange(m.n), np.diff(m.row_ptr))
+    off = (m.col != rows) & (m.val != 0.0)
+    deg = np.bincount(rows[off], minlength=m.n)
+    if table == 3:
+        return deg, np.zeros(m.n, dtype=bool)
+    return deg, deg > (4 if table == 1 else 6)
+
+
+def _bucket_share(m, table, chains, steps, visits, alpha=0.0):
+    """Share of the walk's record reads followed by an out-of-line read: the
+    transitions taken out of out-of-line rows over all visited states.  The
+    state distribution of a chain after t transitions, averaged over start
+    rows, is u_t = (1/n) 1^T P^t with P_ij = |c_ij|/s_i; the transitions of
+    a mean-length chain (steps / (chains rows) of them) are averaged over
+    t < T."""
+    import scipy.sparse as sp
+    deg, ool = _ool_rows(m, table)
+    if not ool.any() or steps == 0:
+        return 0.0, deg, ool
+    A = m.to_scipy().tocsr().copy()   # to_scipy shares m's arrays
+    A.setdiag(0.0)
+    A.eliminate_zeros()
+    a = abs(A)
+    rs = np.asarray(a.sum(axis=1)).ravel()
+    P = sp.diags(np.where(rs > 0, 1.0 / np.where(rs > 0, rs, 1.0), 0.0)) @ a
+    T = max(1, int(round(steps / (chains * m.n))))
+    u = np.full(m.n, 1.0 / m.n)
+    acc = 0.0
+    PT = P.T.tocsr()
+    for _ in range(T):
+        acc += float(u[ool].sum())
+        u = PT @ u
+    return acc * chains * m.n / visits, deg, ool
+
+
+def _gather_roofline(mc, m, last, visits, walk_total_ms, nlaunch, peaks, peak_src, workload):
+    """Roofline of the walk kernel against the gather ceiling measured in the
+    same run: dependent random reads of the table's own records (and, for
+    out-of-line rows, their 16-byte buckets), at the table's footprint and
+    bucket share and at the walk's launch shape (outside the timed region).
+    Algorithmic bytes per visited state are the 32-B sectors that hold the
+    row's header and its sampled transition: one for a compact record, two
+    for a 64-byte record, plus one for the share of visits whose transition
+    is read out of line.  frac = walk visits/s over the probe's records/s."""
+    compact = last.table == mc.TABLE_COMPACT
+    rec_bytes = 32 if compact else SLOT_BYTES
+    share, deg, ool = _bucket_share(m, last.table, last.chains, last.steps, visits / max(1, nlaunch))
+    bytes_per_visit = rec_bytes + 32.0 * share
+    visits_per_s = visits / (walk_total_ms / 1e3)
+    achieved = bytes_per_visit * visits_per_s / 1e9
+    bpsm = 7 if last.load_depth == 8 else 8   # blocks per SM of the walk launch (72 / 64 registers)
+    foot = rec_bytes * m.n
+    bucket_foot = max(4096, 16 * int(deg[ool].sum()))
+    roof = {"bound": "gather", "unit": "GB/s", "kernel": "k_walk (walk + accumulate + filter)",
+            "bytes_per_unit": (f"{bytes_per_visit:.1f} B per visited state: the 32-B sectors holding the row header "
+                               f"and the sampled transition ({rec_bytes}-B {mc.TABLE_NAMES[last.table]} records"
+                               + (f"; plus one sector for the {share:.3f} of visits whose transition is read out of "
+                                  "line" if share > 0 else "") + ")"),
+            "algorithmic_bytes_per_launch": bytes_per_visit * visits / max(1, nlaunch),
+            "walk_kernel_ms": walk_total_ms / max(1, nlaunch), "walk_visits_per_s": visits_per_s,
+            "traffic": _traffic(workload)}
+    try:
+        if share > 0:
+            g = mc.mcmi_gather_roofline_mix(SLOT_BYTES * m.n, bucket_foot, share, last.threads, bpsm, 64)
+            g_full = mc.mcmi_gather_roofline_mix(SLOT_BYTES * m.n, bucket_foot, share, 256, 8, 64)
+            probe = "mcmi_gather_roofline_mix"
+        else:
+            g = mc.mcmi_gather_roofline(foot, last.threads, bpsm, 64, record_bytes=rec_bytes)
+            g_full = mc.mcmi_gather_roofline(foot, 256, 8, 64, record_bytes=rec_bytes)
+            probe = "mcmi_gather_roofline"
+        peak = bytes_per_visit * g / 1e9
+        roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                     "peak_source": (f"measured in this run: {probe}, dependent random reads of {rec_bytes}-B "
+                                     f"records over {foot / 2**20:.1f} MiB"
+                                     + (f" and 16-B buckets over {bucket_foot / 2**20:.1f} MiB for a share "
+                                        f"{share:.3f}" if share > 0 else "")
+                                     + f", {last.threads} threads x {bpsm} blocks/SM x 2 chains per thread"),
+                     "gather": {"records_per_s_walk_shape": g, "records_per_s_full_occupancy": g_full,
+                                "frac_full_occupancy": visits_per_s / g_full, "record_bytes": rec_bytes,
+                                "footprint_bytes": foot, "bucket_share": share, "bucket_footprint_bytes": bucket_foot}})
+        if compact:
+            g64 = mc.mcmi_gather_roofline(SLOT_BYTES * m.n, last.threads, bpsm, 64, record_bytes=SLOT_BYTES)
+            roof["gather"]["records_per_s_64B_records_walk_shape"] = g64
+            roof["gather"]["frac_of_64B_record_ceiling"] = visits_per_s / g64
+    except Exception as exc:  # measurement only
+        roof.update({"achieved": achieved, "peak": None, "frac": None, "gather": {"error": str(exc)}})
+    # context: the same bytes against the HBM copy bandwidth
+    roof["hbm_context"] = {"peak": peaks["hbm_gbs"], "frac": achieved / peaks["hbm_gbs"],
+                           "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)"}
+    return roof
+
+
 def run_ours(a):
     import torch
     world, rank, local = _dist()
@@ -403,42 +508,8 @@ def run_ours(a):
         return 0
     peaks, peak_src = _peaks()
     walk_total_ms = sum(walk_ms)
-    # algorithmic bytes per visited state: the sectors that hold the row's
-    # header and its sampled transition -- two 32-B sectors of a 64-byte
-    # record, one for the compact table's 32-byte record
-    rec_bytes = 32 if last.table == mc.TABLE_COMPACT else SLOT_BYTES   # bytes of one row record
-    alg_bytes = rec_bytes * visits
-    achieved = alg_bytes / (walk_total_ms / 1e3) / 1e9
-    traffic = _traffic(os.path.join(ROOT, "paper_2409_03095_b300", "csrc", "walk.cu"), a.workload)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-            "kernel": "k_walk (walk + accumulate + filter)",
-            "peak_source": f"{peak_src} HBM copy bandwidth",
-            "algorithmic_bytes_per_launch": alg_bytes / max(1, len(walk_ms)),
-            "bytes_per_unit": (f"{rec_bytes} B per visited state: the "
-                               f"{'one 32-B sector' if rec_bytes == 32 else 'two 32-B sectors'} holding the row "
-                               f"header and the sampled transition ({mc.TABLE_NAMES[last.table]} table, "
-                               f"{rec_bytes}-B records)"),
-            "walk_kernel_ms": walk_total_ms / max(1, len(walk_ms)),
-            "walk_share_of_step": walk_total_ms / tot_ms if world == 1 else None}
-    # gather roofline (one row record per visited state): dependent random
-    # reads of records of the table's size over a buffer the size of the row
-    # records, at the walk's launch shape and at full occupancy (outside the
-    # timed region); with compact records also the 64-byte records' ceiling
-    foot = rec_bytes * m.n
-    try:
-        g_walk = mc.mcmi_gather_roofline(foot, 128, 8, 64, record_bytes=rec_bytes)   # 8 blocks of 128 threads per SM
-        g_full = mc.mcmi_gather_roofline(foot, 256, 8, 64, record_bytes=rec_bytes)
-        visits_per_s = visits / (walk_total_ms / 1e3)
-        roof["gather"] = {"record_bytes": rec_bytes, "footprint_bytes": foot, "records_per_s_walk_shape": g_walk,
-                          "records_per_s_full_occupancy": g_full, "walk_visits_per_s": visits_per_s,
-                          "frac_walk_shape": visits_per_s / g_walk, "frac_full_occupancy": visits_per_s / g_full}
-        if rec_bytes != SLOT_BYTES:
-            g64 = mc.mcmi_gather_roofline(SLOT_BYTES * m.n, 128, 8, 64, record_bytes=SLOT_BYTES)
-            roof["gather"]["records_per_s_64B_records_walk_shape"] = g64
-            roof["gather"]["frac_of_64B_record_ceiling"] = visits_per_s / g64
-    except Exception as exc:  # measurement only
-        roof["gather"] = {"error": str(exc)}
+    roof = _gather_roofline(mc, m, last, visits, walk_total_ms, len(walk_ms), peaks, peak_src, a.workload)
+    roof["walk_share_of_step"] = walk_total_ms / tot_ms if world == 1 else None
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cpu = _cpu_baseline(m, w, a.cpu_seconds, last.table)
@@ -776,6 +847,66 @@ def run_alpha_sweep(a):
     return 0
 
 
+def run_sharded(a):
+    """One build of the workload's matrix per step, its rows split evenly
+    over the ranks; each rank builds its row range and the CSR pieces are
+    all-gathered (paper_2409_03095_b300.shard).  Total work is fixed as N
+    grows (strong scaling); value = the whole matrix's transitions per
+    second of the slowest rank."""
+    import torch
+    import torch.distributed as dist
+    world, rank, local = _dist()
+    _init_ranks(world)
+    torch.cuda.set_device(local)
+    import paper_2409_03095_b300 as mc
+    from paper_2409_03095_b300.shard import build_sharded, partition_rows
+    mc.load()
+    m, w, p = _params_for(mc, a.workload, seed=1000, precision=a.precision)
+    B = mc.DeviceCsr.from_host(m)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, device="cuda", dtype=torch.float32)
+    for _ in range(a.warmup):
+        build_sharded(B, p, stream=stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    times, steps = [], 0
+    for it in range(a.steps):
+        flush.fill_(float(it))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rp, col, val, st = build_sharded(B, p, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        steps += st.steps if st is not None else 0
+    if clocks:
+        clocks.end()
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop() if clocks else None
+    tot_ms, tot_steps = _reduce_ranks(sum(times), steps, "cuda")
+    if rank == 0:
+        b, e = partition_rows(m.n, world)[0]
+        line = {"metric": METRIC, "value": tot_steps / (tot_ms / 1e3), "unit": "steps/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot_ms / a.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64" if a.precision == 64 else "f32",
+                "data": "synthetic",
+                "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "rows": m.n, "nnz_M": int(rp[-1]),
+                           "rows_per_rank": e - b, "l2": "flushed between timed steps (256 MiB write)",
+                           "parallelism": f"rows of one matrix in {world} contiguous ranges, one per GPU; "
+                                          "CSR pieces all-gathered over NCCL inside the timed step"},
+                "clocks": ck}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     a = _args()
     if a.impl == "reference":
@@ -788,6 +919,8 @@ def main():
         return run_alpha_sweep(a)
     if a.workload == "batch_512":
         return run_batched(a)
+    if a.shard:
+        return run_sharded(a)
     return run_ours(a)
 
 

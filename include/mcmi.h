@@ -8,8 +8,10 @@
  * ||C||_inf < 1 (Sec. III-A, Sec. IV-A phases 1-2), estimate the rows of
  * (I - C)^-1 by random walks over the Neumann series (Eq. 2, phase 3),
  * scale column j by 1/d_j (phase 4), and keep per row the entries largest in
- * magnitude (Sec. IV-B).  The recovery of Eq. 3 (phase 5) is not done: the
- * paper notes it costs O(n^3) and is usually skipped (Sec. IV).
+ * magnitude (Sec. IV-B).  The recovery of B^-1 from Bhat^-1 (Eq. 3,
+ * phase 5) is not part of the build: the paper notes it costs O(n^3) and is
+ * usually skipped (Sec. IV); mcmi_recover_dense provides it for small dense
+ * matrices, as a diagnostic.
  *
  * Conventions for every entry point:
  *  - Pointers named "device" must point to device memory of the current CUDA
@@ -17,7 +19,8 @@
  *    caller and only read during the call.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
  *    ordered on it.  Entry points that must learn a size on the host
- *    (mcmi_build*, mcmi_walk_dump) synchronise `stream` before returning;
+ *    (mcmi_build*, mcmi_walk_dump) synchronise `stream` before returning,
+ *    because the size of M is only known once the walks have run;
  *    mcmi_apply and mcmi_debug_tables do not.
  *  - Return value: MCMI_OK or an error code.  On error no output handle is
  *    produced (*M_out == NULL) and mcmi_last_error() describes the cause.
@@ -27,9 +30,13 @@
  *  - Determinism: a walk is a function of (seed, row, chain, step) only, so
  *    the same inputs and seed give the same paths and visit counts on any
  *    launch configuration, row subset or table layout of the same table
- *    type.  FP32 sums are accumulated with compensated (Kahan) additions in
- *    an order that depends on thread timing: results can differ in the last
- *    bits between runs; FP64 sums likewise.
+ *    type.  With the default accumulator (MCMI_ACC_FIXED64) each row sum is
+ *    the exact sum of the walk weights in 64-bit fixed point, independent
+ *    of the order of the additions, so M is bit-reproducible across runs,
+ *    launch shapes, row shardings and batched builds.  The opt-in
+ *    MCMI_ACC_KAHAN32 accumulator adds FP32 values with a compensation word
+ *    in an order that depends on thread timing: its results can differ in
+ *    the last bits between runs.
  */
 #ifndef MCMI_H
 #define MCMI_H
@@ -91,7 +98,7 @@ typedef struct {
     int32_t chains;      /* chains N per row (0: from eps and max_i s_i) */
     int32_t max_len;     /* maximum transitions L per chain (>= 0) */
     int32_t top_k;       /* keep at most top_k off-diagonals per row; 0 disables */
-    int32_t precision;   /* 32: FP32 weights, Kahan FP32 sums; 64: FP64 weights and sums */
+    int32_t precision;   /* 32: FP32 walk weights; 64: FP64 walk weights (row sums per `accumulator`) */
     int32_t table;       /* MCMI_TABLE_* */
     int32_t threads;     /* threads per block of the walk kernel (0 = auto; 64, 128 or 256) */
     int32_t hash_log2;   /* log2 of the on-chip accumulator slots per block (0 = auto) */
@@ -188,8 +195,10 @@ mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_
  * row's random numbers are keyed by its index inside its own matrix, so
  * Ms[b] equals what mcmi_build_ex gives for Bs[b] alone with the same
  * parameters and table type.  If p->threads, p->chains_per_thread and
- * p->hash_log2 are all 0, mcmi_autotune picks them (and the table type if
- * AUTO) on the batch.  With p->table AUTO (FIXED64 accumulator, no
+ * p->hash_log2 are all 0, the autotuner of mcmi_autotune picks them and the
+ * load depth on the batch, for the table type the parameters give (AUTO:
+ * its automatic choice, never another type, so that the batch walks the
+ * same paths whatever the trials' timings).  With p->table AUTO (FIXED64 accumulator, no
  * learned proposal), a batch in which the compact table fits some matrices
  * but not others is built as two batches, one per group (each autotuned as
  * above when the shape is 0); stats then sum the two, and report the table
@@ -396,6 +405,23 @@ mcmi_status mcmi_debug_tables(const mcmi_csr *B, const mcmi_params *p, double *o
 mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int record_bytes, int threads_per_block,
                                  int blocks_per_sm, int steps, double *records_per_s, void *stream);
 
+/* Gather roofline probe for the hybrid table's access pattern (measurement).
+ * Like mcmi_gather_roofline with 64-byte records over
+ * record_footprint_bytes, except that after a share bucket_share (0..1) of
+ * the record reads, chosen by a hash of the record read, the chain reads one
+ * 16-byte bucket (one 128-bit load, dependent on the record) of a second
+ * buffer of bucket_footprint_bytes and takes the next record index from it:
+ * the walk's steps out of rows whose alias table is stored out of line.
+ * *records_per_s (host) receives the record reads per second (each with its
+ * bucket read where taken).  Allocates and frees both buffers
+ * stream-ordered; synchronises `stream`.  Errors: MCMI_ERR_ARG (a footprint
+ * < 4096, bucket_share outside [0, 1], bad launch shape), MCMI_ERR_OOM,
+ * MCMI_ERR_CUDA.  (Sec. I, Sec. IV-B: random memory access limits the
+ * method.)                                                               */
+mcmi_status mcmi_gather_roofline_mix(uint64_t record_footprint_bytes, uint64_t bucket_footprint_bytes,
+                                     double bucket_share, int threads_per_block, int blocks_per_sm, int steps,
+                                     double *records_per_s, void *stream);
+
 /* ---------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is a
  * service for callers that must not allocate device memory at the point of
@@ -412,10 +438,13 @@ mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int record_bytes, int
  * process exits, so n may be at most 33,554,432; larger n returns
  * MCMI_ERR_ARG with a message naming the limit.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All
- * calls share the one array and it keeps the last call's partial sums:
- * calls that may overlap on the GPU (other streams, other host threads)
- * race and must be ordered by the caller.
+ * device current; make that first call before any stream capture.  The
+ * address is kept for the life of the process: cudaDeviceReset, or
+ * anything else that destroys the device's primary context, leaves it
+ * stale, so after a reset this entry point must not be called again in the
+ * same process.  All calls share the one array and it keeps the last
+ * call's partial sums: calls that may overlap on the GPU (other streams,
+ * other host threads) race and must be ordered by the caller.
  * --------------------------------------------------------------------- */
 mcmi_status mcmi_exclusive_scan_noalloc(const int32_t *counts, int64_t n, int64_t *offsets, void *stream);
 

@@ -99,6 +99,8 @@ def load():
     lib.mcmi_exclusive_scan_noalloc.argtypes = [P, i64, P, P]
     lib.mcmi_gather_roofline.argtypes = [u64, i32, i32, i32, i32, C.POINTER(f64), P]
     lib.mcmi_gather_roofline.restype = C.c_int
+    lib.mcmi_gather_roofline_mix.argtypes = [u64, u64, f64, i32, i32, i32, C.POINTER(f64), P]
+    lib.mcmi_gather_roofline_mix.restype = C.c_int
     lib.mcmi_solve.argtypes = [C.POINTER(mcmi_csr), P, P, P, C.c_int, f64, i32, i32, C.POINTER(i32), C.POINTER(f64), P]
     lib.mcmi_solve.restype = C.c_int
     lib.mcmi_autotune.argtypes = [C.POINTER(mcmi_csr), C.POINTER(mcmi_params), P, C.POINTER(mcmi_tune_result)]
@@ -444,6 +446,17 @@ def mcmi_gather_roofline(footprint_bytes, threads_per_block=128, blocks_per_sm=6
     r = C.c_double()
     _check(load().mcmi_gather_roofline(int(footprint_bytes), int(record_bytes), threads_per_block, blocks_per_sm,
                                        steps, C.byref(r), _stream(stream)))
+    return r.value
+
+
+def mcmi_gather_roofline_mix(record_footprint_bytes, bucket_footprint_bytes, bucket_share, threads_per_block=128,
+                             blocks_per_sm=8, steps=64, stream=None):
+    """Dependent 64-byte record reads per second where a share of them is
+    followed by a dependent 16-byte bucket read (the hybrid table's walk)."""
+    r = C.c_double()
+    _check(load().mcmi_gather_roofline_mix(int(record_footprint_bytes), int(bucket_footprint_bytes),
+                                           float(bucket_share), threads_per_block, blocks_per_sm, steps,
+                                           C.byref(r), _stream(stream)))
     return r.value
 
 

@@ -408,10 +408,14 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     //  - FP64 walks: F keeps the rounding of every weight below 2^-25 relative.
     //  - A learned proposal's weights may exceed 1: 10 more bits of head-room,
     //    and the kernel reports MCMI_ERR_CAPACITY if |W| ever passes 1024.
+    //    Its factors |f_ij| = sum_k |c_ik| g_ik / g_ij are at least s_i / 256
+    //    (g is clamped to [1/16, 16]), so its smallest weight is taken 2^8
+    //    below delta min s, which keeps the same 2^-25 relative rounding
+    //    (up to the Fmax cap).
     const double visits = (double)P.N * (double)(P.Lb + 1) + 1.0;
     const int Fmax = 62 - (int)std::ceil(std::log2(visits)) - (P.learned ? 10 : 0);
     int F = Fmax;
-    const double wmin = p->delta * (double)(float)P.smin;
+    const double wmin = p->delta * (double)(float)P.smin / (P.learned ? 256.0 : 1.0);
     if (p->precision == 32 && !P.learned && a.delta_f > 0.0f && P.smin > 0.0) {
         const float wmin32 = a.delta_f * (float)P.smin;   // IEEE single product, no contraction
         int e = 0;
@@ -456,7 +460,12 @@ mcmi_status alloc_overflow(Scratch &S, WalkPlan &W, const Prepared &P, bool dump
     a.ent_col = S.get<uint32_t>(G * entc);
     a.ent_val = S.get<unsigned long long>(G * entc);
     a.ent_cnt = dump ? S.get<uint32_t>(G * entc) : nullptr;
+    a.cells = dump ? nullptr : S.get<uint32_t>(G * walk_sketch_cells());
     if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (overflow log)");
+    if (a.cells) {
+        const cudaError_t e = cudaMemsetAsync(a.cells, 0, G * walk_sketch_cells() * sizeof(uint32_t), S.s);
+        if (e != cudaSuccess) return cuda_fail(e, "sketch cells");
+    }
     return MCMI_OK;
 }
 
@@ -506,7 +515,11 @@ mcmi_status time_walk(const mcmi_params *p, const Prepared &P, WalkPlan W, const
 
 }  // namespace
 
-extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_tune_result *res)
+// keep_table: only the table the parameters give (AUTO: its automatic
+// choice) is tried, so that the tuned build walks the same paths as an
+// untuned one and its output does not depend on the trials' timings.
+static mcmi_status autotune_impl(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_tune_result *res,
+                                 bool keep_table)
 {
     mcmi_status r = check_csr(B);
     if (r == MCMI_OK) r = check_params(p);
@@ -579,8 +592,9 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
     const int hashes[] = {9, 10, 11, 12, 13};
     int tables[4] = {MCMI_TABLE_CUMULATIVE, MCMI_TABLE_ALIAS, MCMI_TABLE_HYBRID, MCMI_TABLE_COMPACT};
     const bool compact_ok = p->accumulator == MCMI_ACC_FIXED64 && !p->proposal;
-    const int ntab = p->table == MCMI_TABLE_AUTO ? (compact_ok ? 4 : 3) : 1;
+    const int ntab = (p->table == MCMI_TABLE_AUTO && !keep_table) ? (compact_ok ? 4 : 3) : 1;
     if (p->table != MCMI_TABLE_AUTO) tables[0] = p->table;
+    else if (keep_table) tables[0] = bestp.table;   // the automatic choice, resolved by the default trial
     mcmi_params cand = bestp;
     float cand_ms = 1e30f;
     for (int ti = 0; ti < ntab; ++ti) {
@@ -649,6 +663,11 @@ extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *st
         res->sample_rows = ns;
     }
     return MCMI_OK;
+}
+
+extern "C" mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_tune_result *res)
+{
+    return autotune_impl(B, p, stream, res, false);
 }
 
 void mcmi::set_error_message(const char *msg) { g_err = msg; }
@@ -908,7 +927,10 @@ static mcmi_status batched_impl(const mcmi_csr *Bs, int32_t count, const mcmi_pa
     mcmi_params q = *p_in;
     mcmi_tune_result tune{};
     if (q.threads == 0 && q.chains_per_thread == 0 && q.hash_log2 == 0) {
-        r = mcmi_autotune(&Ball, &q, stream, &tune);
+        // launch shape, accumulator size and load depth only: the table stays
+        // the one the parameters give, so the batch's paths do not depend on
+        // the autotuner's timings
+        r = autotune_impl(&Ball, &q, stream, &tune, true);
         if (r != MCMI_OK) return r;
     }
     Prepared P;

@@ -75,6 +75,41 @@ __global__ void k_gather_probe(const uint4 *rec, uint64_t nrec, int steps, uint3
     if (acc == 0x12345678u) atomicAdd(sink, 1ull);   // keeps the loads live
 }
 
+// The hybrid table's pattern: each step reads a 64-byte record; a share
+// `ool` (out of 2^32) of the records, chosen by a hash of their contents,
+// also leads to a 16-byte bucket of a second buffer (one 128-bit load,
+// dependent on the record), and the next record index comes from the
+// bucket.  This is the walk on rows whose alias table is out of line.
+__global__ void k_gather_probe_mix(const uint4 *rec, uint64_t nrec, const uint4 *bkt, uint64_t nbkt, uint32_t ool,
+                                   int steps, uint32_t seed, unsigned long long *sink)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t i0 = ((uint64_t)mix32(t ^ seed) * nrec) >> 32;
+    uint64_t i1 = ((uint64_t)mix32(t ^ ~seed) * nrec) >> 32;
+    uint32_t acc = 0;
+#pragma unroll 1
+    for (int s = 0; s < steps; ++s) {
+        uint32_t w0[16], w1[16];
+        load64(rec + 4 * i0, w0);
+        load64(rec + 4 * i1, w1);
+        uint32_t x0 = 0, x1 = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) { x0 ^= w0[k]; x1 ^= w1[k]; }
+        if (mix32(x0) < ool) {
+            const uint4 b = __ldg(bkt + (((uint64_t)x0 * nbkt) >> 32));
+            x0 = mix32(x0 ^ b.x ^ b.y ^ b.z ^ b.w);
+        }
+        if (mix32(x1) < ool) {
+            const uint4 b = __ldg(bkt + (((uint64_t)x1 * nbkt) >> 32));
+            x1 = mix32(x1 ^ b.x ^ b.y ^ b.z ^ b.w);
+        }
+        acc += x0 + x1;
+        i0 = ((uint64_t)x0 * nrec) >> 32;
+        i1 = ((uint64_t)x1 * nrec) >> 32;
+    }
+    if (acc == 0x12345678u) atomicAdd(sink, 1ull);   // keeps the loads live
+}
+
 }  // namespace
 
 }  // namespace mcmi
@@ -121,6 +156,60 @@ extern "C" mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int record
     cudaFreeAsync(sink, s);
     if (e != cudaSuccess) {
         set_error_message("mcmi_gather_roofline: kernel failed");
+        return MCMI_ERR_CUDA;
+    }
+    *records_per_s = (double)grid * threads_per_block * 2.0 * steps / (ms * 1e-3);
+    return MCMI_OK;
+}
+
+extern "C" mcmi_status mcmi_gather_roofline_mix(uint64_t record_footprint_bytes, uint64_t bucket_footprint_bytes,
+                                                double bucket_share, int threads_per_block, int blocks_per_sm,
+                                                int steps, double *records_per_s, void *stream)
+{
+    using namespace mcmi;
+    if (!records_per_s || record_footprint_bytes < 4096 || bucket_footprint_bytes < 4096 ||
+        !(bucket_share >= 0.0 && bucket_share <= 1.0) || threads_per_block < 32 || threads_per_block > 1024 ||
+        blocks_per_sm < 1 || steps < 1) {
+        set_error_message("mcmi_gather_roofline_mix: bad argument");
+        return MCMI_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t nrec = record_footprint_bytes / 64, nbkt = bucket_footprint_bytes / 16;
+    const uint32_t ool = bucket_share >= 1.0 ? 0xFFFFFFFFu : (uint32_t)(bucket_share * 4294967296.0);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    uint4 *rec = nullptr, *bkt = nullptr;
+    unsigned long long *sink = nullptr;
+    cudaError_t e = cudaMallocAsync(&rec, nrec * 64, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&bkt, nbkt * 16, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&sink, 8, s);
+    if (e != cudaSuccess) {
+        if (rec) cudaFreeAsync(rec, s);
+        if (bkt) cudaFreeAsync(bkt, s);
+        set_error_message("mcmi_gather_roofline_mix: allocation failed");
+        return MCMI_ERR_OOM;
+    }
+    k_fill_records<<<sms * 8, 256, 0, s>>>(rec, nrec * 4, 0x1234567u);
+    k_fill_records<<<sms * 8, 256, 0, s>>>(bkt, nbkt, 0x7654321u);
+    const int grid = sms * blocks_per_sm;
+    k_gather_probe_mix<<<grid, threads_per_block, 0, s>>>(rec, nrec, bkt, nbkt, ool, 8, 1u, sink);   // warm-up
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    k_gather_probe_mix<<<grid, threads_per_block, 0, s>>>(rec, nrec, bkt, nbkt, ool, steps, 2u, sink);
+    cudaEventRecord(b, s);
+    e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFreeAsync(rec, s);
+    cudaFreeAsync(bkt, s);
+    cudaFreeAsync(sink, s);
+    if (e != cudaSuccess) {
+        set_error_message("mcmi_gather_roofline_mix: kernel failed");
         return MCMI_ERR_CUDA;
     }
     *records_per_s = (double)grid * threads_per_block * 2.0 * steps / (ms * 1e-3);

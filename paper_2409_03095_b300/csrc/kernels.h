@@ -19,6 +19,8 @@ void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const doubl
                    float *invd32, cudaStream_t s);
 
 size_t walk_smem_bytes(int precision, int log2H, bool dump);
+// 32-bit cells per block of the walk-time magnitude sketch (a.cells)
+size_t walk_sketch_cells();
 // depth: loads per thread in flight after the walks (4 or 8)
 cudaError_t walk_occupancy(int precision, int table, int acc, bool dump, int cpt, int depth, int threads, int log2H,
                            int *blocks_per_sm);

@@ -97,12 +97,14 @@ struct WalkArgs {
     // visits that find the on-chip table full go to a per-block log (column,
     // addend); after the walks the log is reduced on chip, in hash-range
     // passes, into a per-block list of the row's distinct entries
-    uint2 *log_key;               // {column, FP32 bits of its 1/d_j}
+    uint2 *log_key;               // {column, FP32 bits of its 1/d_j}; sketch kernels: {column, FP32 bits of W}
     unsigned long long *log_val;
     uint32_t log_cap;             // log entries per block (>= the visits of one row)
     uint32_t *ent_col;
     unsigned long long *ent_val;  // finished values M_ij (FP64 bits, or FP32 bits in the low word)
     uint32_t *ent_cnt;            // parity dump: visit counts
+    uint32_t *cells;              // walk-time magnitude sketch: walk_sketch_cells() words per block, zero
+                                  // at launch (each block clears its cells after a row that used them)
     uint32_t ent_cap;             // entries per block (>= log_cap + on-chip slots)
     // filter
     double tau;

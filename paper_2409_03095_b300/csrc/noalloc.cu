@@ -59,7 +59,10 @@ extern "C" mcmi_status mcmi_exclusive_scan_noalloc(const int32_t *counts, int64_
     int64_t *scratch = nullptr;
     {
         // one-time set-up per device, with that device current: look up the
-        // device address of the fixed array (a query, not an allocation)
+        // device address of the fixed array (a query, not an allocation).
+        // The address stays valid while the device's primary context lives;
+        // a cudaDeviceReset in this process would leave it stale (the header
+        // tells callers not to use this entry point after one).
         std::lock_guard<std::mutex> lk(g_mu);
         if (!g_scratch_ptr[dev]) {
             void *ptr = nullptr;

@@ -40,7 +40,23 @@ namespace {
 constexpr int kProbeOnChip = 32;   // on-chip probe window before overflowing
 constexpr uint32_t kPartMul = 0x85EBCA77u;   // odd: col -> col * kPartMul permutes the 32-bit keys
 constexpr uint32_t kSketchMul = 0xC2B2AE35u;  // odd: cell of a column in the log's magnitude sketch
-constexpr uint32_t kSketchOne = 65536u;       // sketch units per lowthr
+// Walk-time sketch (the load-depth-8 FP32 fixed-point kernel): while a row
+// is walked, every visit that goes to the overflow log also adds its
+// magnitude |W| |1/d_j| to one of kCells cells (hash of the column; a
+// per-block array in global memory, updated by L2 atomics, so that the
+// shared memory left to the L1 cache is unchanged), in
+// units of |1/d_i| 2^-kCellUnitLog2 of the row i; a visit of 2^31 / (log
+// capacity) units or more sets the cell's top bit instead (the cell is then
+// always kept), so that the sums of a row's visits stay below 2^31.
+// A presence map of kPresBits bits (hash of the column) holds a superset of
+// the columns on chip; once the table is at its cap, a visit whose bit is
+// clear goes straight to the log without probing the table.
+constexpr int kCellsLog2 = 10;
+constexpr int kCells = 1 << kCellsLog2;
+constexpr int kCellUnitLog2 = 14;
+constexpr uint32_t kCellFlag = 0x80000000u;
+constexpr int kPresLog2 = 14;                 // 16384 bits in 512 words
+constexpr uint32_t kPresMul = 0xCC9E2D51u;    // odd: bit of a column in the presence map
 
 __device__ __forceinline__ uint32_t hash_home(uint32_t key, int log2)
 {
@@ -236,9 +252,14 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     __shared__ unsigned long long s_pass_lo, s_pass_hi;
     __shared__ float s_redf[32];
     __shared__ unsigned long long s_redu[32];
-    __shared__ uint32_t s_hist[256];
-    __shared__ uint32_t s_bstart[257];
+    // s_hist (256 words) and s_bstart (257) are used after the walks only;
+    // during the walks the first 512 words hold the presence map
+    __shared__ uint32_t s_hb[256 + 257];
+    uint32_t *const s_hist = s_hb;
+    uint32_t *const s_bstart = s_hb + 256;
+    uint32_t *const s_pres = s_hb;
     __shared__ uint32_t s_digit, s_rank;
+    __shared__ float s_cscale;   // walk-time sketch: units per |W| |1/d_j| for the current row
 
     const int tid = threadIdx.x, B = blockDim.x;
     // on-chip table kept <= 87.5% full during the walks with the compact table
@@ -258,12 +279,18 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     const int F = a.fix_shift;
     const float scaleF = __uint_as_float((uint32_t)(F + 127) << 23);   // 2^F (F <= 62)
     const bool use_tau = a.tau > 0.0;
+    uint32_t *const g_cells = SKETCH ? a.cells + (size_t)blockIdx.x * kCells : nullptr;   // zero between rows
+    // walk-time sketch: largest units one visit adds (a row logs at most log_cap visits)
+    const float cell_cap = (float)(kCellFlag / (a.log_cap > 0u ? a.log_cap : 1u) - 1u);
 
     for (int h = tid; h < H; h += B) {
         s_keys[h] = kEmpty;
         s_lo[h] = 0u;
         s_hi[h] = 0u;
         if (DUMP) s_aux[h] = 0u;
+    }
+    if (SKETCH) {
+        for (int c = tid; c < (1 << (kPresLog2 - 5)); c += B) s_pres[c] = 0u;
     }
     if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; }
 
@@ -274,7 +301,12 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     // -1: the column is absent and cannot be inserted (table at its fill cap,
     // or no free slot within the probe window), or the table is at its cap
     // and the column was not in the buckets searched.
-    auto onchip_slot = [&](uint32_t col) -> int {
+    // With the walk-time sketch (walk == true in the walk loop): a column
+    // sets its presence bit before it is inserted, so once the table is at
+    // its cap, a column whose bit is clear was never inserted and goes to
+    // the log without reading the table; the merge after the walks looks up
+    // only the logged columns whose bit is set.
+    auto onchip_slot = [&](uint32_t col, bool walk) -> int {
         uint32_t bkt = hash_home(col, a.log2H - 2);
         const uint32_t nb = (uint32_t)(H >> 2);
         // the cap is read once, alongside the first bucket: lanes probing at
@@ -282,6 +314,10 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // by up to a block's threads (a small table may fill up; a probe then
         // gives up after its bucket limit and the visit is logged)
         const bool capped = *(volatile uint32_t *)&s_fill >= fill_cap;
+        const bool pres = SKETCH && walk;
+        const uint32_t pb = (col * kPresMul) >> (32 - kPresLog2);
+        if (pres && capped && !((*(volatile uint32_t *)&s_pres[pb >> 5] >> (pb & 31)) & 1u)) return -1;
+        bool marked = false;
 #pragma unroll 1
         for (int p = 0; p < kProbeOnChip / 4; ++p) {
             uint4 kv;
@@ -293,6 +329,10 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             const int e = kv.x == kEmpty ? 0 : kv.y == kEmpty ? 1 : kv.z == kEmpty ? 2 : kv.w == kEmpty ? 3 : -1;
             if (e >= 0) {
                 if (capped) return -1;
+                if (pres && !marked) {
+                    atomicOr(&s_pres[pb >> 5], 1u << (pb & 31));
+                    marked = true;
+                }
                 const uint32_t old = atomicCAS(&s_keys[4 * bkt + e], kEmpty, col);
                 if (old == kEmpty) atomicAdd(&s_fill, 1u);
                 if (old == kEmpty || old == col) return (int)(4 * bkt) + e;
@@ -312,7 +352,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     // was not added.  The atomics come after the probe loop, where the lanes
     // of a warp have re-converged, so that one instruction serves them all.
     auto onchip_add = [&](uint32_t col, unsigned long long add) -> bool {
-        const int h = onchip_slot(col);
+        const int h = onchip_slot(col, false);
         if (h < 0) return false;
         val_add((uint32_t)h, add);
         if (DUMP) atomicAdd(&s_aux[h], 1u);
@@ -358,6 +398,13 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 const uint32_t h = 4 * hash_home(r, a.log2H - 2);   // first slot of its bucket
                 s_keys[h] = r;
                 s_fill = 1;
+                if (SKETCH) {
+                    const uint32_t pb = (r * kPresMul) >> (32 - kPresLog2);
+                    s_pres[pb >> 5] |= 1u << (pb & 31);
+                    // sketch units of this row: |1/d_i| 2^-kCellUnitLog2
+                    const float invd_r = CMP ? __ldg(a.invd32 + r) : __uint_as_float(__ldg(&a.slots[4 * (size_t)r].z));
+                    s_cscale = __fdiv_rn((float)(1u << kCellUnitLog2), fabsf(invd_r));
+                }
                 if (FIX) {
                     set_vword(h, (unsigned long long)((long long)a.N << F));
                 } else {
@@ -437,7 +484,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     if (FIX && a.lbkt && !(fabsf(w[j]) <= a.w_limit)) report(a.st, s_row, MCMI_ERR_CAPACITY);
                     if (FIX) add = (unsigned long long)(PREC == 64 ? fix_f64(w64[j], F) : fix_f32s(w[j], scaleF));
                     else add = (unsigned long long)__float_as_uint(__fmul_rn(w[j], __uint_as_float(s[j][2])));
-                    h = onchip_slot(st[j]);
+                    h = onchip_slot(st[j], true);
                 }
                 __syncwarp();
                 if (acc && h >= 0) {
@@ -456,8 +503,19 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     if (to_log) {
                         const uint32_t pos = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
                         if (pos < a.log_cap) {
-                            lc[pos] = make_uint2(st[j], CMP ? 0u : s[j][2]);   // compact: 1/d_j looked up later
-                            lv[pos] = add;
+                            if (SKETCH) {
+                                // one 8-byte entry {column, FP32 bits of W}: the
+                                // addend fix_f32s(W) is recomputed when read
+                                lc[pos] = make_uint2(st[j], __float_as_uint(w[j]));
+                                const float invd_j = CMP ? __ldg(a.invd32 + st[j]) : __uint_as_float(s[j][2]);
+                                const float q = __fmul_ru(__fmul_ru(fabsf(w[j]), fabsf(invd_j)), s_cscale);
+                                uint32_t *cell = &g_cells[(st[j] * kSketchMul) >> (32 - kCellsLog2)];
+                                if (q < cell_cap) atomicAdd(cell, (uint32_t)ceilf(q));
+                                else atomicOr(cell, kCellFlag);   // large, infinite or NaN
+                            } else {
+                                lc[pos] = make_uint2(st[j], CMP ? 0u : s[j][2]);   // compact: 1/d_j looked up later
+                                lv[pos] = add;
+                            }
                         } else {
                             report(a.st, s_row, MCMI_ERR_CAPACITY);   // cannot happen: a row makes at most N Lb visits
                         }
@@ -491,7 +549,9 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         __syncthreads();
 
         // ---- row statistics ----
-        for (int b = tid; b < 256; b += B) s_hist[b] = 0;
+        if (!SKETCH) {   // the sketch kernels still need the presence map (cleared after the merge)
+            for (int b = tid; b < 256; b += B) s_hist[b] = 0;
+        }
         const unsigned long long row_steps = block_sum(my_steps, s_redu);
         if (tid == 0) {
             if (a.count_steps) atomicAdd(&a.st->steps, row_steps);
@@ -595,8 +655,45 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         };
 
         // ---- the overflow log ----
+        // the addend of log entry e: stored, or recomputed from the FP32
+        // weight of an 8-byte entry (the same conversion as during the walk)
+        auto log_add = [&](uint2 key, const unsigned long long *vals, uint32_t e) -> unsigned long long {
+            if (SKETCH) return (unsigned long long)fix_f32s(__uint_as_float(key.y), scaleF);
+            return vals[e];
+        };
+        // 1/d_j of a log entry's column: carried in the entry, or looked up
+        auto log_invd = [&](uint2 key) -> VT {
+            if (SKETCH || PREC == 64 || CMP) return load_invd(key.x);
+            return (VT)__uint_as_float(key.y);
+        };
         uint32_t nrem = 0;
-        if (nlog) {   // block-uniform
+        if (SKETCH && nlog) {   // block-uniform
+            // entries whose column may be on chip (presence bit set) are
+            // looked up and added there; the others cannot be on chip
+            for (uint32_t e0 = tid; e0 < nlog; e0 += UF * B) {
+                uint2 key[UF];
+#pragma unroll
+                for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
+#pragma unroll
+                for (int u = 0; u < UF; ++u) {
+                    if (key[u].x == kEmpty) continue;
+                    const uint32_t pb = (key[u].x * kPresMul) >> (32 - kPresLog2);
+                    if ((s_pres[pb >> 5] >> (pb & 31)) & 1u) {
+                        const int h = onchip_find(key[u].x);
+                        if (h >= 0) {
+                            val_add((uint32_t)h, log_add(key[u], lv, 0u));
+                            lc[e0 + u * B].x = kEmpty;
+                            continue;
+                        }
+                    }
+                    ++nrem;
+                }
+            }
+            nrem = (uint32_t)block_sum(nrem, s_redu);
+            // the presence map's words become the histogram again
+            for (int b = tid; b < 256; b += B) s_hist[b] = 0;
+            __syncthreads();
+        } else if (nlog) {   // block-uniform
             // entries whose column is on chip are added there; the others are
             // counted per hash-range bucket (top 8 bits of col * kPartMul)
             for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
@@ -662,49 +759,40 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 if (kb > (float)lowthr) lowthr = (VT)kb;
                 __syncthreads();
             }
-            // Magnitude sketch (FP32 fixed-point builds with tau or top-k): the 2H value
-            // words of the emptied table become cells holding, per hash of the
-            // column, the sum of the log entries' magnitudes rounded up, in
-            // units of lowthr / 65536.  A column's finished |M_ij| is at most
-            // the sum of its entries' magnitudes (times 1 + 2^-22 for the
-            // finish's roundings), so a column whose cell stays below 65535
-            // units is under lowthr and can never be kept: its entries are
-            // neither bucketed nor reduced.
-            const bool sketch = SKETCH && lowthr > (VT)0;   // block-uniform
-            uint32_t *cells = s_lo;                         // s_lo, s_hi: 2H words
-            const int cell_shift = 32 - (a.log2H + 1);
-            if (sketch) {
-                for (int b = tid; b < 256; b += B) s_hist[b] = 0u;
-                const float qs = __fdiv_ru((float)kSketchOne, (float)lowthr);
-                for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
-                    uint2 key[UL];
-                    unsigned long long val[UL];
-#pragma unroll
-                    for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
-#pragma unroll
-                    for (int u = 0; u < UL; ++u) val[u] = key[u].x != kEmpty ? lv[e0 + u * B] : 0ull;
-#pragma unroll
-                    for (int u = 0; u < UL; ++u) {
-                        if (key[u].x == kEmpty) continue;
-                        uint32_t *cell = &cells[(key[u].x * kSketchMul) >> cell_shift];
-                        if (*(volatile uint32_t *)cell >= kSketchOne - 1u) continue;   // already kept
-                        const long long x = (long long)val[u];
-                        const float m = __ull2float_ru((unsigned long long)(x < 0 ? -x : x));
-                        const float id = CMP ? (float)load_invd(key[u].x) : __uint_as_float(key[u].y);
-                        const float v = __fmul_ru(__fmul_ru(m, a.fin_scale), fabsf(id));
-                        const float q = ceilf(__fmul_ru(v, qs));
-                        atomicAdd(cell, q < (float)kSketchOne ? (uint32_t)q : kSketchOne);   // NaN: kept
-                    }
-                }
+            // Walk-time magnitude sketch (SKETCH kernels): cell c holds at least
+            // s_cscale times the sum of |W| |1/d_j| over the logged visits of
+            // the columns that hash to it, or has its top bit set.  A column
+            // that is not on chip finishes at |M_ij| <= (cell / (s_cscale N))
+            // (1 + 2^-21) (the conversion and the finish's two products round
+            // to nearest), so a column whose cell stays below
+            // Tc = lowthr s_cscale N (1 - 2^-20), rounded down, is under lowthr
+            // and can never be kept: its entries are neither bucketed nor
+            // reduced.  (lowthr = 0: every cell is kept.)
+            uint32_t Tc = 0u;
+            if (SKETCH && lowthr > (VT)0) {
+                const float tf = __fmul_rd(__fmul_rd(__fmul_rd((float)lowthr, s_cscale), (float)a.N), 1.0f - 0x1p-20f);
+                Tc = !(tf >= 0.0f) ? 0u : (tf >= 2147483648.0f ? kCellFlag : (uint32_t)tf);
+            }
+            auto hot = [&](uint32_t col) -> bool {
+                const uint32_t c = __ldcg(&g_cells[(col * kSketchMul) >> (32 - kCellsLog2)]);
+                return (c & kCellFlag) || c >= Tc;
+            };
+            // SKETCH: one pass keeps the entries of hot cells, appended in
+            // arrival order to lc2 and counted per hash-range bucket; they are
+            // then bucketed into lc (free once this pass is over)
+            if (SKETCH) {
+                if (tid == 0) s_nsub = 0u;
                 __syncthreads();
-                for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
-                    uint32_t key[UL];
+                for (uint32_t e0 = tid; e0 < nlog; e0 += UF * B) {
+                    uint2 key[UF];
 #pragma unroll
-                    for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B].x : kEmpty;
+                    for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
 #pragma unroll
-                    for (int u = 0; u < UL; ++u)
-                        if (key[u] != kEmpty && cells[(key[u] * kSketchMul) >> cell_shift] >= kSketchOne - 1u)
-                            atomicAdd(&s_hist[(key[u] * kPartMul) >> 24], 1u);
+                    for (int u = 0; u < UF; ++u)
+                        if (key[u].x != kEmpty && hot(key[u].x)) {
+                            atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
+                            lc2[atomicAdd(&s_nsub, 1u)] = key[u];
+                        }
                 }
                 __syncthreads();
             }
@@ -731,28 +819,30 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 if (tid == 31) s_bstart[256] = run;
             }
             __syncthreads();
-            for (uint32_t e0 = tid; e0 < nlog; e0 += UL * B) {
+            // bucketed copy: SKETCH kernels scatter their compact list of hot
+            // entries from lc2 into lc, the others the whole log from lc into lc2
+            const uint2 *src = SKETCH ? lc2 : lc;
+            uint2 *const lb = SKETCH ? lc : lc2;
+            const uint32_t nsrc = SKETCH ? s_nsub : nlog;
+            for (uint32_t e0 = tid; e0 < nsrc; e0 += UL * B) {
                 uint2 key[UL];
                 unsigned long long val[UL];
 #pragma unroll
-                for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
+                for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nsrc ? src[e0 + u * B] : make_uint2(kEmpty, 0u);
+                if (!SKETCH) {
 #pragma unroll
-                for (int u = 0; u < UL; ++u) val[u] = key[u].x != kEmpty ? lv[e0 + u * B] : 0ull;
+                    for (int u = 0; u < UL; ++u) val[u] = key[u].x != kEmpty ? lv[e0 + u * B] : 0ull;
+                }
 #pragma unroll
                 for (int u = 0; u < UL; ++u) {
                     if (key[u].x == kEmpty) continue;
-                    if (sketch && cells[(key[u].x * kSketchMul) >> cell_shift] < kSketchOne - 1u) continue;
                     const uint32_t p = atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
-                    lc2[p] = key[u];
-                    lv2[p] = val[u];
+                    lb[p] = key[u];
+                    if (!SKETCH) lv2[p] = val[u];
                 }
             }
             if (tid == 0) s_fill = 0;
             __syncthreads();
-            if (sketch) {   // the table's value words back to zero
-                for (int h = tid; h < 2 * H; h += B) cells[h] = 0u;
-                __syncthreads();
-            }
             // Buckets of at most 32 entries: one warp each.  Lanes holding the
             // same column find each other with __match_any_sync; the group's
             // lowest lane sums it in a per-warp scratch row of 64-bit words
@@ -773,8 +863,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         const uint32_t s0 = bk < 256 ? s_bstart[bk] : 0u;
                         cnt[u] = bk < 256 ? s_bstart[bk + 1] - s0 : 0u;
                         const bool act = cnt[u] <= 32u && lane < cnt[u];
-                        key[u] = act ? lc2[s0 + lane] : make_uint2(kEmpty, 0u);
-                        val[u] = act ? lv2[s0 + lane] : 0ull;
+                        key[u] = act ? lb[s0 + lane] : make_uint2(kEmpty, 0u);
+                        val[u] = act ? log_add(key[u], lv2, s0 + lane) : 0ull;
                     }
 #pragma unroll
                     for (int u = 0; u < UB; ++u) {
@@ -798,7 +888,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         VT v = (VT)0;
                         bool keep = false;
                         if (lead) {
-                            const VT invd = (PREC == 64 || CMP) ? load_invd(key[u].x) : (VT)__uint_as_float(key[u].y);
+                            const VT invd = log_invd(key[u]);
                             v = finish(single ? val[u] : scratch[lane], invd);
                             const VT av = v < (VT)0 ? -v : v;
                             lmax = av > lmax ? av : lmax;
@@ -861,9 +951,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     uint32_t key[UL];
                     unsigned long long val[UL];
 #pragma unroll
-                    for (int u = 0; u < UL; ++u) key[u] = eb + u * B < e1 ? lc2[eb + u * B].x : kEmpty;
-#pragma unroll
-                    for (int u = 0; u < UL; ++u) val[u] = key[u] != kEmpty ? lv2[eb + u * B] : 0ull;
+                    for (int u = 0; u < UL; ++u) {
+                        const uint2 kk = eb + u * B < e1 ? lb[eb + u * B] : make_uint2(kEmpty, 0u);
+                        key[u] = kk.x;
+                        val[u] = kk.x != kEmpty ? log_add(kk, lv2, eb + u * B) : 0ull;
+                    }
 #pragma unroll
                     for (int u = 0; u < UL; ++u) {
                         if (key[u] == kEmpty) continue;
@@ -1145,6 +1237,12 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         __syncthreads();
         // ---- reset the accumulator for the next row ----
         clear_table();
+        if (SKETCH) {
+            if (nlog) {   // block-uniform: only a row that logged visits touched its cells
+                for (int c = tid; c < kCells / 4; c += B) reinterpret_cast<uint4 *>(g_cells)[c] = make_uint4(0, 0, 0, 0);
+            }
+            for (int c = tid; c < (1 << (kPresLog2 - 5)); c += B) s_pres[c] = 0u;
+        }
         if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; }
     }
 }
@@ -1154,6 +1252,8 @@ size_t walk_smem_bytes(int precision, int log2H, bool dump)
 {
     return ((size_t)1 << log2H) * ((dump || precision == 64) ? 16 : 12);
 }
+
+size_t walk_sketch_cells() { return (size_t)kCells; }
 
 namespace {
 using WalkFn = void (*)(WalkArgs);

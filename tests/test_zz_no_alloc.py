@@ -58,6 +58,12 @@ def test_noalloc_scan_large_and_limit():
     ref[1:] = torch.cumsum(counts.to(torch.int64), 0)
     assert torch.equal(_noalloc(counts), ref)
     assert torch.equal(_noalloc(counts[:12345].contiguous()), ref[:12346])
+    # exactly the limit: every tile of the fixed array, the last scratch word included
+    full = torch.randint(0, 64, (33_554_432,), device="cuda", dtype=torch.int32, generator=g)
+    ref_full = torch.zeros(full.numel() + 1, dtype=torch.int64, device="cuda")
+    ref_full[1:] = torch.cumsum(full.to(torch.int64), 0)
+    assert torch.equal(_noalloc(full), ref_full)
+    del full, ref_full
     empty = torch.zeros(0, dtype=torch.int32, device="cuda")
     assert _noalloc(empty).tolist() == [0]
     lib = mc.load()
