@@ -81,6 +81,10 @@ def _args():
     ap.add_argument("--reduce", action="store_true",
                     help="matrix reduction sweep judged by BiCGstab/GMRES on --workload (one JSON line)")
     ap.add_argument("--train-steps", type=int, default=100)
+    ap.add_argument("--theta-out", default="", help="--learned: save the trained network's parameters (.npy)")
+    ap.add_argument("--theta-in", default="", help="--learned: evaluate these parameters instead of training")
+    ap.add_argument("--learned-rows", type=int, default=256,
+                    help="--learned: sample rows for the estimator error (exact rows by FP64 solves)")
     ap.add_argument("--shard", action="store_true",
                     help="one matrix, its rows split over the ranks (Sec. IV-A), CSR pieces gathered over NCCL "
                          "(strong scaling); default: one independent build per rank (weak scaling)")
@@ -580,15 +584,18 @@ def _exact_rows(mc, m, alpha, rows):
     return exact
 
 
-def _estimator_error(mc, B, m, p, rows, exact):
+def _estimator_error(mc, B, m, p, rows, exact, per_row=False):
     """eps_hat: mean over sample rows of ||X_i - x_i*||_2 / ||x_i*||_2 for the
-    unfiltered estimate X_i (the parity dump of the same walks)."""
+    unfiltered estimate X_i (the parity dump of the same walks).  per_row:
+    also the rows' errors and transition counts."""
     dump = mc.mcmi_walk_dump(B, p, rows, min(400000, m.n))
     errs = []
     for g, xe in zip(dump, exact):
         est = np.zeros(m.n)
         est[g["col"]] = g["val"]
         errs.append(np.linalg.norm(est - xe) / np.linalg.norm(xe))
+    if per_row:
+        return np.array(errs), np.array([g["steps"] for g in dump], dtype=np.float64)
     return float(np.mean(errs)), sum(g["steps"] for g in dump)
 
 
@@ -617,33 +624,53 @@ def run_learned(a):
     out = {"metric": METRIC, "unit": "steps/s", "workload": "aniso2d_9pt 1024^2 (n=1048576), 32x32-block rotated "
            "anisotropy 1e-3; learned BF16 MLP proposal vs |c| proposal", "data": "synthetic"}
     t0 = time.perf_counter()
-    train = [synth.aniso2d_9pt(int(nx), seed=2001 + k)
-             for k, nx in enumerate(np.random.default_rng(2000).integers(32, 129, a.train_count))]
-    Bt = [mc.DeviceCsr.from_host(m) for m in train]
-    P = mc.Proposal()
-    tp = mc.mcmi_train_params(steps=a.train_steps, lr=3e-3, chains=64, max_len=256, delta=1e-3, alpha=0.3, seed=7,
-                              round_bf16=1)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    hist = mc.mcmi_proposal_train(Bt, tp, P)
-    torch.cuda.synchronize()
-    out["training"] = {"matrices": len(train), "rows": int(sum(m.n for m in train)),
-                       "edges": int(sum(m.nnz for m in train)), "steps": a.train_steps,
-                       "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
-                       "seconds": time.perf_counter() - t1, "generation_s": t1 - t0}
-    del Bt
+
+    def note(msg):
+        sys.stderr.write(f"[learned {time.perf_counter() - t0:7.1f} s] {msg}\n")
+        sys.stderr.flush()
+    if a.theta_in:
+        # parameters of an earlier training run (same family, same settings)
+        P = mc.Proposal(np.load(a.theta_in))
+        out["training"] = {"from": os.path.basename(a.theta_in)}
+        note("loaded trained parameters")
+    else:
+        train = [synth.aniso2d_9pt(int(nx), seed=2001 + k)
+                 for k, nx in enumerate(np.random.default_rng(2000).integers(32, 129, a.train_count))]
+        Bt = [mc.DeviceCsr.from_host(m) for m in train]
+        note(f"generated {len(train)} training matrices")
+        P = mc.Proposal()
+        tp = mc.mcmi_train_params(steps=a.train_steps, lr=3e-3, chains=64, max_len=256, delta=1e-3, alpha=0.3,
+                                  seed=7, round_bf16=1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        hist = mc.mcmi_proposal_train(Bt, tp, P)
+        torch.cuda.synchronize()
+        out["training"] = {"matrices": len(train), "rows": int(sum(m.n for m in train)),
+                           "edges": int(sum(m.nnz for m in train)), "steps": a.train_steps,
+                           "loss_first": float(hist[0]), "loss_last": float(hist[-1]),
+                           "seconds": time.perf_counter() - t1, "generation_s": t1 - t0}
+        note(f"trained: loss {hist[0]:.4f} -> {hist[-1]:.4f}")
+        if a.theta_out:
+            np.save(a.theta_out, P.get())
+        del Bt
     m = synth.aniso2d_9pt(1024, seed=1005)
     B = mc.DeviceCsr.from_host(m)
     alpha = _pick_alpha(mc, B)
     out["alpha"] = alpha
     N, L, delta, tau = 128, 256, 1e-3, 1e-2
-    rows = np.random.default_rng(1).choice(m.n, 32, replace=False)
+    nrows, nrhs, seeds = a.learned_rows, 8, (11, 12, 13)
+    rows = np.random.default_rng(1).choice(m.n, nrows, replace=False)
+    t2 = time.perf_counter()
     exact = _exact_rows(mc, m, alpha, rows)
-    res = {}
+    out["exact_rows"] = {"rows": nrows, "seconds": time.perf_counter() - t2}
+    note(f"{nrows} exact rows")
+    rhs = [torch.from_numpy(np.random.default_rng(100 + r).standard_normal(m.n)).cuda() for r in range(nrhs)]
+    res, per = {}, {}
     for name, prop in (("plain", None), ("learned", P)):
-        p = mc.params(chains=N, max_len=L, delta=delta, seed=11, alpha=alpha, filter_tau=tau,
+        p = mc.params(chains=N, max_len=L, delta=delta, seed=seeds[0], alpha=alpha, filter_tau=tau,
                       table=mc.TABLE_ALIAS, proposal=prop)
-        eps_hat, steps_sample = _estimator_error(mc, B, m, p, rows, exact)
+        errs, stp = _estimator_error(mc, B, m, p, rows, exact, per_row=True)
+        per[name] = (errs, stp)
         # timed builds of the whole matrix
         for _ in range(2):
             M = mc.mcmi_build_ex(B, p)
@@ -652,28 +679,46 @@ def run_learned(a):
             M = mc.mcmi_build_ex(B, p)
             ts.append(M.stats.ms_prepare + M.stats.ms_walk + M.stats.ms_assemble)
         st = M.stats
-        bvec = torch.from_numpy(np.random.default_rng(2).standard_normal(m.n)).cuda()
-        x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
-        its, relres = mc.mcmi_solve(B, M, bvec, x, mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
-        # GMRES(50): monotone residuals, a steadier comparison than BiCGstab's
-        xg = torch.zeros(m.n, dtype=torch.float64, device="cuda")
-        its_g, relres_g = mc.mcmi_solve(B, M, bvec, xg, mc.SOLVE_GMRES, rtol=1e-8, maxit=20000, restart=50)
-        res[name] = {"eps_hat": eps_hat, "steps_per_row": steps_sample / len(rows),
-                     "build_ms": float(np.median(ts)), "steps": int(st.steps),
+        # Krylov judge: each seed's M, each right-hand side
+        its_b, its_g = [], []
+        for sd in seeds:
+            q = type(p).from_buffer_copy(p)
+            q.seed = sd
+            Ms = mc.mcmi_build_ex(B, q)
+            for bvec in rhs:
+                x = torch.zeros(m.n, dtype=torch.float64, device="cuda")
+                its_b.append(mc.mcmi_solve(B, Ms, bvec, x, mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)[0])
+                x.zero_()
+                # GMRES(50): monotone residuals, a steadier comparison than BiCGstab's
+                its_g.append(mc.mcmi_solve(B, Ms, bvec, x, mc.SOLVE_GMRES, rtol=1e-8, maxit=20000, restart=50)[0])
+            Ms.close()
+        note(f"{name}: Krylov solves done")
+        res[name] = {"eps_hat": float(errs.mean()), "eps_hat_sd_of_mean": float(errs.std(ddof=1) / np.sqrt(nrows)),
+                     "steps_per_row": float(stp.mean()), "build_ms": float(np.median(ts)), "steps": int(st.steps),
                      "steps_per_s": st.steps / (np.median(ts) / 1e3), "nnz_M": int(st.nnz),
-                     "bicgstab_iters": int(its), "relres": float(relres),
-                     "gmres50_iters": int(its_g), "gmres50_relres": float(relres_g)}
-    its0, _ = mc.mcmi_solve(B, None, bvec, torch.zeros_like(bvec), mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)
-    its0_g, _ = mc.mcmi_solve(B, None, bvec, torch.zeros_like(bvec), mc.SOLVE_GMRES, rtol=1e-8, maxit=20000,
-                              restart=50)
+                     "bicgstab_iters_mean": float(np.mean(its_b)), "bicgstab_iters_sd": float(np.std(its_b, ddof=1)),
+                     "gmres50_iters_mean": float(np.mean(its_g)), "gmres50_iters_sd": float(np.std(its_g, ddof=1)),
+                     "bicgstab_iters": [int(v) for v in its_b], "gmres50_iters": [int(v) for v in its_g]}
+    its0 = [mc.mcmi_solve(B, None, bv, torch.zeros_like(bv), mc.SOLVE_BICGSTAB, rtol=1e-8, maxit=20000)[0]
+            for bv in rhs[:2]]
+    its0_g = [mc.mcmi_solve(B, None, bv, torch.zeros_like(bv), mc.SOLVE_GMRES, rtol=1e-8, maxit=20000, restart=50)[0]
+              for bv in rhs[:2]]
     pl, le = res["plain"], res["learned"]
-    # steps needed for the plain proposal's error (error ~ N^-1/2 at fixed walk lengths)
-    eq = (le["eps_hat"] / pl["eps_hat"]) ** 2
-    out.update({"plain": pl, "learned": le, "bicgstab_iters_unpreconditioned": int(its0),
-                "gmres50_iters_unpreconditioned": int(its0_g),
-                "learned_steps_at_equal_error_over_plain": eq * le["steps_per_row"] / pl["steps_per_row"],
-                "learned_iters_over_plain": le["bicgstab_iters"] / max(1, pl["bicgstab_iters"]),
-                "learned_gmres_iters_over_plain": le["gmres50_iters"] / max(1, pl["gmres50_iters"]),
+
+    # steps needed for the plain proposal's error (error ~ N^-1/2 at fixed
+    # walk lengths), with a bootstrap over the sample rows (same rows for both)
+    def ratio(ix):
+        ep, sp = per["plain"][0][ix].mean(), per["plain"][1][ix].mean()
+        el, sl = per["learned"][0][ix].mean(), per["learned"][1][ix].mean()
+        return (el / ep) ** 2 * sl / sp
+    boot = np.array([ratio(np.random.default_rng(7 + b).integers(0, nrows, nrows)) for b in range(2000)])
+    out.update({"plain": pl, "learned": le, "bicgstab_iters_unpreconditioned": [int(v) for v in its0],
+                "gmres50_iters_unpreconditioned": [int(v) for v in its0_g],
+                "learned_steps_at_equal_error_over_plain": ratio(np.arange(nrows)),
+                "learned_steps_at_equal_error_ci95": [float(np.percentile(boot, 2.5)), float(np.percentile(boot, 97.5))],
+                "learned_bicgstab_iters_over_plain": le["bicgstab_iters_mean"] / pl["bicgstab_iters_mean"],
+                "learned_gmres_iters_over_plain": le["gmres50_iters_mean"] / pl["gmres50_iters_mean"],
+                "krylov": f"{nrhs} right-hand sides x seeds {list(seeds)}, rtol 1e-8, FP64 residual",
                 "chains": N, "max_len": L, "delta": delta, "tau": tau})
     print(json.dumps(out), flush=True)
     return 0

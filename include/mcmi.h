@@ -109,10 +109,8 @@ typedef struct {
     int32_t load_depth;  /* global loads each walk thread keeps in flight in the loops after the
                           * walks: 4 (FP32: 64 registers, eight 128-thread blocks per SM) or 8
                           * (72 registers, seven blocks; fewer L2 round trips through the overflow
-                          * log, and FP32 tau builds drop the log's columns that a magnitude
-                          * sketch proves below the threshold before reducing it); 0 = auto: 8
-                          * for FP32 walks on matrices of more than six off-diagonals per row on
-                          * average, else 4 */
+                          * log); 0 = auto: 8 for FP32 walks on matrices of more than six
+                          * off-diagonals per row on average, else 4 */
     const struct mcmi_proposal_s *proposal; /* learned proposal (mcmi_proposal_*), NULL = p_ij = |c_ij|/s_i */
 } mcmi_params;
 
@@ -127,8 +125,9 @@ typedef struct {
     int32_t table;          /* table type used */
     int32_t hash_log2;      /* accumulator slots used (log2) */
     int64_t spilled;        /* distinct columns reduced from the overflow log (visits that did not fit on
-                             * chip); with tau, FP32 builds at load depth 8 first drop the log's columns
-                             * whose magnitude bound is below the threshold, and those are not counted */
+                             * chip); with tau or top-k, FP32 fixed-point builds first drop the log's
+                             * columns whose magnitude bound is below the threshold, and those are not
+                             * counted */
     int64_t deferred_rows;  /* rows re-run because the first output buffer was full */
     float ms_prepare;       /* split + tables (CUDA events on the build stream) */
     float ms_walk;          /* walk stage incl. overflow-log set-up and deferred rows */
@@ -191,7 +190,9 @@ mcmi_status mcmi_autotune(const mcmi_csr *B, mcmi_params *p, void *stream, mcmi_
 /* Batched build of `count` independent matrices (each n >= 1) with the same
  * parameters: the matrices are gathered into one block-diagonal CSR so that
  * one persistent walk launch drains the rows of all of them from a single
- * device queue; the walk and the row-offset scan run as one CUDA graph.  A
+ * device queue; the walk and the row-offset scan run as one CUDA graph,
+ * whose executable form is kept per host thread and device and updated in
+ * place for the next batched build when the topology matches.  A
  * row's random numbers are keyed by its index inside its own matrix, so
  * Ms[b] equals what mcmi_build_ex gives for Bs[b] alone with the same
  * parameters and table type.  If p->threads, p->chains_per_thread and

@@ -968,7 +968,23 @@ static mcmi_status batched_impl(const mcmi_csr *Bs, int32_t count, const mcmi_pa
     int64_t *tmp = S.get<int64_t>(scan_tmp_elems(tn));
     if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation (batch staging)");
 
-    // walk + scan as one CUDA graph on a private stream ordered after `s`
+    // walk + scan as one CUDA graph on a private stream ordered after `s`.
+    // The executable graph of the previous batched build on this host
+    // thread and device is updated in place (cudaGraphExecUpdate) when the
+    // new capture has the same topology, so repeated builds pay the capture
+    // but not the instantiation.
+    struct GraphCache {
+        cudaGraphExec_t exec = nullptr;
+        int device = -1;
+        ~GraphCache() { if (exec) cudaGraphExecDestroy(exec); }
+    };
+    static thread_local GraphCache gcache;
+    int cur_dev = 0;
+    cudaGetDevice(&cur_dev);
+    if (gcache.exec && gcache.device != cur_dev) {
+        cudaGraphExecDestroy(gcache.exec);
+        gcache.exec = nullptr;
+    }
     cudaStream_t cs = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -987,11 +1003,26 @@ static mcmi_status batched_impl(const mcmi_csr *Bs, int32_t count, const mcmi_pa
         e = cudaStreamEndCapture(cs, &graph);
         if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&gexec, graph, 0);
+    if (e == cudaSuccess && gcache.exec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(gcache.exec, graph, &info) == cudaSuccess) {
+            gexec = gcache.exec;
+        } else {
+            cudaGetLastError();   // an update that does not apply is not an error of this build
+            cudaGraphExecDestroy(gcache.exec);
+            gcache.exec = nullptr;
+        }
+    }
+    if (e == cudaSuccess && !gexec) {
+        e = cudaGraphInstantiate(&gexec, graph, 0);
+        if (e == cudaSuccess) {
+            gcache.exec = gexec;
+            gcache.device = cur_dev;
+        }
+    }
     if (e == cudaSuccess) e = cudaGraphLaunch(gexec, cs);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], cs);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[3], 0);
-    if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
     if (cs) {
         cudaStreamSynchronize(cs);

@@ -185,9 +185,65 @@ __device__ __forceinline__ void bitonic_warp_batched(unsigned long long *a, int 
     }
 }
 
+// Stable LSD radix sort of n <= kAsmWarpMax 32-bit keys in a[] by their bits
+// [lo, lo + bits), 8 bits per pass, by one warp (b[]: scratch of n keys,
+// cnt[]: 256 counters).  Each pass counts the digits, scans the counts, and
+// scatters the keys 32 at a time in their input order: lanes holding the
+// same digit find each other with __match_any_sync and take consecutive
+// places, so every pass is stable.  Returns the buffer holding the result.
+__device__ __forceinline__ uint32_t *radix_warp(uint32_t *a, uint32_t *b, uint32_t *cnt, int n, int lo, int bits,
+                                                int lane)
+{
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int sh = lo; sh < lo + bits; sh += 8) {
+        for (int d = lane; d < 256; d += 32) cnt[d] = 0u;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) atomicAdd(&cnt[(a[i] >> sh) & 255u], 1u);
+        __syncwarp();
+        // exclusive scan: lane l holds counters 8l .. 8l + 7
+        uint32_t c8[8], tot = 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            c8[u] = cnt[8 * lane + u];
+            tot += c8[u];
+        }
+        uint32_t incl = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += nb;
+        }
+        uint32_t run = incl - tot;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            cnt[8 * lane + u] = run;
+            run += c8[u];
+        }
+        __syncwarp();
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + lane;
+            const bool v = i < n;
+            const uint32_t k = v ? a[i] : 0u;
+            const uint32_t d = (k >> sh) & 255u;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, v ? d : 256u + (uint32_t)lane);
+            const uint32_t pos = cnt[d] + (uint32_t)__popc(peers & lt);
+            __syncwarp();
+            if (v && 31 - __clz(peers) == lane) cnt[d] += (uint32_t)__popc(peers);   // the group's last lane
+            __syncwarp();
+            if (v) b[pos] = k;
+        }
+        __syncwarp();
+        uint32_t *t = a;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
 // rows of at most wmax entries (32, or kAsmWarpMax with kAsmWarpMax keys of
 // dynamic shared memory per warp), one warp per row; longer rows are left to
-// k_assemble_long
+// k_assemble_long.  A row whose columns span less than 2^22 is sorted by a
+// radix sort of 32-bit keys (column - row minimum) << 10 | staging index;
+// wider rows take the bitonic network on (column, value) keys.
 __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(
     int64_t rows, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ st_off,
     const int32_t *__restrict__ st_cnt, const uint32_t *__restrict__ st_col, const float *__restrict__ st_val,
@@ -196,6 +252,7 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(
     extern __shared__ unsigned long long sk[];
     const int lane = threadIdx.x & 31;
     unsigned long long *key = sk + (threadIdx.x >> 5) * kAsmWarpMax;
+    uint32_t *rcnt = reinterpret_cast<uint32_t *>(sk + kAsmWarps * kAsmWarpMax) + (threadIdx.x >> 5) * 256;
     const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = warp; r < rows; r += nwarps) {
@@ -215,6 +272,32 @@ __global__ void __launch_bounds__(32 * kAsmWarps) k_assemble(
                 out_val[dst + rank] = v;
             }
         } else if (cnt <= wmax) {
+            // the row's column range decides the sort
+            uint32_t cmin = 0xFFFFFFFFu, cmax = 0u;
+            for (int i = lane; i < cnt; i += 32) {
+                const uint32_t c = st_col[off + i];
+                cmin = min(cmin, c);
+                cmax = max(cmax, c);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                cmin = min(cmin, __shfl_xor_sync(0xFFFFFFFFu, cmin, o));
+                cmax = max(cmax, __shfl_xor_sync(0xFFFFFFFFu, cmax, o));
+            }
+            const uint32_t range = cmax - cmin;
+            if (range < (1u << 22)) {
+                uint32_t *ka = reinterpret_cast<uint32_t *>(key), *kb = ka + kAsmWarpMax;
+                for (int i = lane; i < cnt; i += 32) ka[i] = ((st_col[off + i] - cmin) << 10) | (uint32_t)i;
+                __syncwarp();
+                const int bits = range ? 32 - __clz(range) : 1;
+                const uint32_t *sorted = radix_warp(ka, kb, rcnt, cnt, 10, bits, lane);
+                for (int i = lane; i < cnt; i += 32) {
+                    const uint32_t k = sorted[i];
+                    out_col[dst + i] = (int32_t)(cmin + (k >> 10));
+                    out_val[dst + i] = st_val[off + (k & 1023u)];
+                }
+                __syncwarp();
+                continue;
+            }
             int P = 64;
             while (P < cnt) P <<= 1;
             for (int i = lane; i < P; i += 32) key[i] = i < cnt ? pack_entry(st_col[off + i], st_val[off + i]) : kKeyInf;
@@ -249,16 +332,98 @@ __device__ __forceinline__ void cmp_swap_global(int32_t *col, float *val, int64_
     }
 }
 
-// rows longer than wmax, one block per row: tiles of kAsmTile entries
-// are sorted in shared memory and written out; merges of larger blocks run
-// their steps of distance >= kAsmTile on the output arrays in global memory
-// and the shorter half-cleaners tile by tile in shared memory
+// Stable LSD radix sort of n <= kAsmTile 32-bit keys by their bits
+// [lo, lo + bits), 8 bits per pass, by the whole block (kAsmLongThreads
+// threads): warp w owns a contiguous segment of the keys, counts its digits
+// in its own 256 counters, and after a block-wide scan over (digit, warp)
+// scatters its segment 32 keys at a time in input order (lanes with the same
+// digit take consecutive places, found with __match_any_sync), so every
+// pass is stable.  Returns the buffer holding the result.
+__device__ __forceinline__ uint32_t *radix_block(uint32_t *a, uint32_t *b, uint32_t *cnt, uint32_t *dsum, int n,
+                                                 int lo, int bits)
+{
+    constexpr int NW = kAsmLongThreads / 32;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int seg = (((n + NW - 1) / NW) + 31) & ~31;
+    const int s0 = w * seg, s1 = min(n, s0 + seg);
+    uint32_t *my = cnt + 256 * w;
+    for (int sh = lo; sh < lo + bits; sh += 8) {
+        for (int d = lane; d < 256; d += 32) my[d] = 0u;
+        __syncwarp();
+        for (int i = s0 + lane; i < s1; i += 32) atomicAdd(&my[(a[i] >> sh) & 255u], 1u);
+        __syncthreads();
+        // digit totals, their exclusive scan, then each warp's cursor per digit
+        if (t < 256) {
+            uint32_t tot = 0u;
+            for (int v = 0; v < NW; ++v) tot += cnt[256 * v + t];
+            dsum[t] = tot;
+        }
+        __syncthreads();
+        if (t < 32) {
+            uint32_t c8[8], tot = 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                c8[u] = dsum[8 * t + u];
+                tot += c8[u];
+            }
+            uint32_t incl = tot;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (t >= o) incl += nb;
+            }
+            uint32_t run = incl - tot;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                dsum[8 * t + u] = run;
+                run += c8[u];
+            }
+        }
+        __syncthreads();
+        if (t < 256) {
+            uint32_t run = dsum[t];
+            for (int v = 0; v < NW; ++v) {
+                const uint32_t c = cnt[256 * v + t];
+                cnt[256 * v + t] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        for (int base = s0; base < s1; base += 32) {
+            const int i = base + lane;
+            const bool v = i < s1;
+            const uint32_t k = v ? a[i] : 0u;
+            const uint32_t d = (k >> sh) & 255u;
+            const uint32_t peers = __match_any_sync(0xFFFFFFFFu, v ? d : 256u + (uint32_t)lane);
+            const uint32_t pos = my[d] + (uint32_t)__popc(peers & lt);
+            __syncwarp();
+            if (v && 31 - __clz(peers) == lane) my[d] += (uint32_t)__popc(peers);   // the group's last lane
+            __syncwarp();
+            if (v) b[pos] = k;
+        }
+        __syncthreads();
+        uint32_t *tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return a;
+}
+
+// rows longer than wmax, one block per row.  A row of at most kAsmTile
+// entries whose columns span less than 2^20 is sorted by a block radix sort
+// of 32-bit keys (column - row minimum) << 12 | staging index.  Other rows:
+// tiles of kAsmTile entries are sorted in shared memory and written out;
+// merges of larger blocks run their steps of distance >= kAsmTile on the
+// output arrays in global memory and the shorter half-cleaners tile by tile
+// in shared memory
 __global__ void __launch_bounds__(kAsmLongThreads) k_assemble_long(
     int64_t rows, const int64_t *__restrict__ row_ptr, const int64_t *__restrict__ st_off,
     const int32_t *__restrict__ st_cnt, const uint32_t *__restrict__ st_col, const float *__restrict__ st_val,
     int32_t *out_col, float *out_val, int wmax)
 {
     __shared__ unsigned long long tile[kAsmTile];
+    __shared__ uint32_t rcnt[256 * (kAsmLongThreads / 32)], rsum[256];
+    __shared__ uint32_t rmin[kAsmLongThreads / 32], rmax[kAsmLongThreads / 32];
     __shared__ int64_t list[kAsmLongThreads];
     __shared__ int nlist;
     const int t = threadIdx.x;
@@ -274,6 +439,44 @@ __global__ void __launch_bounds__(kAsmLongThreads) k_assemble_long(
             const int64_t cnt = st_cnt[r], off = st_off[r];
             int32_t *oc = out_col + row_ptr[r];
             float *ov = out_val + row_ptr[r];
+            if (cnt <= kAsmTile) {
+                uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+                for (int64_t i = t; i < cnt; i += kAsmLongThreads) {
+                    const uint32_t c = st_col[off + i];
+                    lo = min(lo, c);
+                    hi = max(hi, c);
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    lo = min(lo, __shfl_xor_sync(0xFFFFFFFFu, lo, o));
+                    hi = max(hi, __shfl_xor_sync(0xFFFFFFFFu, hi, o));
+                }
+                if ((t & 31) == 0) {
+                    rmin[t >> 5] = lo;
+                    rmax[t >> 5] = hi;
+                }
+                __syncthreads();
+                uint32_t cmin = rmin[0], cmax = rmax[0];
+                for (int v = 1; v < kAsmLongThreads / 32; ++v) {
+                    cmin = min(cmin, rmin[v]);
+                    cmax = max(cmax, rmax[v]);
+                }
+                const uint32_t range = cmax - cmin;
+                if (range < (1u << 20)) {   // block-uniform
+                    uint32_t *ka = reinterpret_cast<uint32_t *>(tile), *kb = ka + kAsmTile;
+                    for (int i = t; i < (int)cnt; i += kAsmLongThreads)
+                        ka[i] = ((st_col[off + i] - cmin) << 12) | (uint32_t)i;
+                    __syncthreads();
+                    const int bits = range ? 32 - __clz(range) : 1;
+                    const uint32_t *sorted = radix_block(ka, kb, rcnt, rsum, (int)cnt, 12, bits);
+                    for (int i = t; i < (int)cnt; i += kAsmLongThreads) {
+                        const uint32_t k = sorted[i];
+                        oc[i] = (int32_t)(cmin + (k >> 12));
+                        ov[i] = st_val[off + (k & 4095u)];
+                    }
+                    __syncthreads();
+                    continue;
+                }
+            }
             int64_t P = 1;
             while (P < cnt) P <<= 1;
             const int tp = P < kAsmTile ? (int)P : kAsmTile;
@@ -346,7 +549,8 @@ cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t 
     // rows known to fit a warp's shuffles need no shared memory (more blocks per SM)
     const bool small = max_cnt > 0 && max_cnt <= 32;
     const int wmax = small ? 32 : kAsmWarpMax;
-    const size_t smem = small ? 0 : (size_t)kAsmWarps * kAsmWarpMax * sizeof(unsigned long long);
+    // per warp: kAsmWarpMax 64-bit keys (or two buffers of 32-bit radix keys) and 256 radix counters
+    const size_t smem = small ? 0 : (size_t)kAsmWarps * (kAsmWarpMax * sizeof(unsigned long long) + 256 * sizeof(uint32_t));
     int64_t g = (rows * 32 + bs - 1) / bs;
     if (g > (int64_t)sms * 32) g = (int64_t)sms * 32;
     k_assemble<<<(unsigned)g, bs, smem, s>>>(rows, row_ptr, st_off, st_cnt, st_col, st_val, out_col, out_val, wmax);

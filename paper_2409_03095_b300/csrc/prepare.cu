@@ -174,14 +174,21 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
         uint32_t w[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) w[k] = 0u;
-        // pass 1: degree and total mass
+        // pass 1: the degree; for alias rows also each weight and sign, kept
+        // in wscratch (q | neg << 32) so that the FP64 divisions run once
         uint32_t deg = 0;
+        for (int64_t k = a; k < b; ++k) deg += col[k] != i;
+        const bool cum_row = table == MCMI_TABLE_CUMULATIVE || (table == MCMI_TABLE_HYBRID && deg <= (uint32_t)kInlineCum);
         unsigned long long Q = 0;
-        for (int64_t k = a; k < b; ++k) {
-            if (col[k] == i) continue;
-            bool ng;
-            Q += entry_weight(val[k], di, si, &ng);
-            ++deg;
+        if (!cum_row) {
+            uint32_t m = 0;
+            for (int64_t k = a; k < b; ++k) {
+                if (col[k] == i) continue;
+                bool ng;
+                const uint32_t q = entry_weight(val[k], di, si, &ng);
+                Q += q;
+                wscratch[(uint32_t)a + m++] = (unsigned long long)q | (ng ? (1ull << 32) : 0ull);
+            }
         }
         w[0] = (uint32_t)Q;
         w[1] = __float_as_uint(__double2float_rn(si));
@@ -190,7 +197,6 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
         const uint32_t begin = (uint32_t)a;
         // the hybrid table takes the cumulative layout for rows of at most
         // kInlineCum transitions (always inline) and the alias layout otherwise
-        const bool cum_row = table == MCMI_TABLE_CUMULATIVE || (table == MCMI_TABLE_HYBRID && deg <= (uint32_t)kInlineCum);
         if (cum_row) {
             const bool inl = deg <= (uint32_t)kInlineCum;
             w[3] = deg | (inl ? 0u : kOolFlag) | (table == MCMI_TABLE_HYBRID ? kCumFlag : 0u);
@@ -217,6 +223,7 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
                 }
                 ++m;
             }
+            w[0] = T;   // Q
         } else {
             const bool inl = deg <= (uint32_t)kInlineAlias;
             w[3] = deg | (inl ? 0u : kOolFlag);
@@ -225,8 +232,9 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
             uint32_t ns = 0, nl = 0, m = 0;
             for (int64_t k = a; k < b; ++k) {
                 if (col[k] == i) continue;
-                bool ng;
-                const unsigned long long wj = (unsigned long long)entry_weight(val[k], di, si, &ng) * deg;
+                const unsigned long long qn = wscratch[begin + m];
+                const bool ng = (qn >> 32) != 0ull;
+                const unsigned long long wj = (qn & 0xFFFFFFFFull) * deg;
                 wscratch[begin + m] = wj;
                 ool_b[begin + m] = (uint32_t)col[k] | (ng ? kNegBit : 0u);  // own col|sign (CSR order)
                 if (wj < Q) small_stk[begin + ns++] = m; else large_stk[begin + nl++] = m;

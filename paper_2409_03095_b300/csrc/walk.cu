@@ -40,7 +40,7 @@ namespace {
 constexpr int kProbeOnChip = 32;   // on-chip probe window before overflowing
 constexpr uint32_t kPartMul = 0x85EBCA77u;   // odd: col -> col * kPartMul permutes the 32-bit keys
 constexpr uint32_t kSketchMul = 0xC2B2AE35u;  // odd: cell of a column in the log's magnitude sketch
-// Walk-time sketch (the load-depth-8 FP32 fixed-point kernel): while a row
+// Walk-time sketch (the FP32 fixed-point production kernel at load depth 8): while a row
 // is walked, every visit that goes to the overflow log also adds its
 // magnitude |W| |1/d_j| to one of kCells cells (hash of the column; a
 // per-block array in global memory, updated by L2 atomics, so that the
@@ -210,7 +210,9 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
     constexpr bool CMP = TABLE == MCMI_TABLE_COMPACT;   // 32-byte records, 1/d_j from invd32
-    // log magnitude sketch (tau builds), in the variant for log-heavy rows
+    // 8-byte log entries, walk-time magnitude sketch and presence map, in the
+    // FP32 fixed-point production kernel for log-heavy rows (load depth 8;
+    // on the stencil-like rows of the depth-4 kernel they cost 12%)
     constexpr bool SKETCH = FIX && PREC == 32 && !DUMP && DEPTH == 8;
     // finished values and the filter work in the build's precision: FP32
     // builds use no FP64 instruction per entry (FP64 issues at a small
