@@ -798,191 +798,222 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 }
                 __syncthreads();
             }
-            // bucket starts: exclusive scan of the 256 counts (warp 0, 8 per lane)
-            if (tid < 32) {
-                uint32_t c8[8], tot = 0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    c8[u] = s_hist[8 * tid + u];
-                    tot += c8[u];
-                }
-                uint32_t incl = tot;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                    if (tid >= o) incl += nb;
-                }
-                uint32_t run = incl - tot;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    s_bstart[8 * tid + u] = run;
-                    s_hist[8 * tid + u] = run;   // scatter cursor
-                    run += c8[u];
-                }
-                if (tid == 31) s_bstart[256] = run;
-            }
-            __syncthreads();
-            // bucketed copy: SKETCH kernels scatter their compact list of hot
-            // entries from lc2 into lc, the others the whole log from lc into lc2
-            const uint2 *src = SKETCH ? lc2 : lc;
-            uint2 *const lb = SKETCH ? lc : lc2;
-            const uint32_t nsrc = SKETCH ? s_nsub : nlog;
-            for (uint32_t e0 = tid; e0 < nsrc; e0 += UL * B) {
-                uint2 key[UL];
-                unsigned long long val[UL];
-#pragma unroll
-                for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nsrc ? src[e0 + u * B] : make_uint2(kEmpty, 0u);
-                if (!SKETCH) {
-#pragma unroll
-                    for (int u = 0; u < UL; ++u) val[u] = key[u].x != kEmpty ? lv[e0 + u * B] : 0ull;
-                }
-#pragma unroll
-                for (int u = 0; u < UL; ++u) {
-                    if (key[u].x == kEmpty) continue;
-                    const uint32_t p = atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
-                    lb[p] = key[u];
-                    if (!SKETCH) lv2[p] = val[u];
-                }
-            }
-            if (tid == 0) s_fill = 0;
-            __syncthreads();
-            // Buckets of at most 32 entries: one warp each.  Lanes holding the
-            // same column find each other with __match_any_sync; the group's
-            // lowest lane sums it in a per-warp scratch row of 64-bit words
-            // (over the empty table's low words, which needs 2B <= H slots) and
-            // appends the finished entry.
-            const bool by_warp = 2 * B <= H;
-            if (by_warp) {
-                unsigned long long *scratch = reinterpret_cast<unsigned long long *>(s_lo) + (tid & ~31);
-                constexpr int UB = 2;   // buckets per iteration: their loads are in flight together
-                const int nw = B >> 5;
-                for (int bk0 = tid >> 5; bk0 < 256; bk0 += UB * nw) {
-                    uint2 key[UB];
-                    unsigned long long val[UB];
-                    uint32_t cnt[UB];
-#pragma unroll
-                    for (int u = 0; u < UB; ++u) {
-                        const int bk = bk0 + u * nw;
-                        const uint32_t s0 = bk < 256 ? s_bstart[bk] : 0u;
-                        cnt[u] = bk < 256 ? s_bstart[bk + 1] - s0 : 0u;
-                        const bool act = cnt[u] <= 32u && lane < cnt[u];
-                        key[u] = act ? lb[s0 + lane] : make_uint2(kEmpty, 0u);
-                        val[u] = act ? log_add(key[u], lv2, s0 + lane) : 0ull;
-                    }
-#pragma unroll
-                    for (int u = 0; u < UB; ++u) {
-                        if (cnt[u] == 0u || cnt[u] > 32u) continue;   // warp-uniform
-                        const bool act = lane < cnt[u];
-                        const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key[u].x);
-                        const uint32_t leader = (uint32_t)__ffs(grp) - 1u;
-                        // a column seen once is its own sum; groups of several
-                        // lanes add up in the warp's scratch row
-                        const bool single = (grp & (grp - 1u)) == 0u;
-                        if (!__all_sync(0xFFFFFFFFu, single || !act)) {
-                            scratch[lane] = 0ull;
-                            __syncwarp();
-                            if (act && !single) {
-                                if (FIX) fix_add_shared(&scratch[leader], (long long)val[u]);
-                                else comp_add(&scratch[leader], __uint_as_float((uint32_t)val[u]));
-                            }
-                            __syncwarp();
-                        }
-                        const bool lead = act && lane == leader;
-                        VT v = (VT)0;
-                        bool keep = false;
-                        if (lead) {
-                            const VT invd = log_invd(key[u]);
-                            v = finish(single ? val[u] : scratch[lane], invd);
-                            const VT av = v < (VT)0 ? -v : v;
-                            lmax = av > lmax ? av : lmax;
-                            keep = !(av < lowthr);
-                            ++nred;
-                        }
-                        const uint32_t lm = __ballot_sync(0xFFFFFFFFu, keep);
-                        const int first = __ffs(lm) - 1;
-                        uint32_t base = 0;
-                        if (lm && (int)lane == first) base = atomicAdd(&s_nent, (uint32_t)__popc(lm));
-                        if (lm) base = __shfl_sync(0xFFFFFFFFu, base, first);
-                        if (keep) {
-                            const uint32_t p = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
-                            ec[p] = key[u].x;
-                            ev[p] = enc(v);
-                            if (DUMP) ecn[p] = (uint32_t)__popc(grp);
-                        }
-                        __syncwarp();
-                    }
-                }
-                scratch[lane] = 0ull;
-            }
-            // larger buckets stay pending: s_hist[b] = entries of pending bucket b, else 0
-            for (int bk = tid; bk < 256; bk += B) {
-                const uint32_t cnt = s_bstart[bk + 1] - s_bstart[bk];
-                s_hist[bk] = (cnt > 32u || !by_warp) ? cnt : 0u;
-            }
-            // Pending buckets: passes over hash ranges [lo, hi) holding at most
-            // per_pass of their entries (so at most per_pass distinct columns)
-            // through the on-chip table; a pass that still does not fit is
-            // retried on the lower half of its range.
+            // SKETCH: when the kept entries fit the emptied table's pass size,
+            // one pass adds them all on chip and finishes them (a few L2
+            // round trips, instead of one warp per hash bucket); if a probe
+            // window overflows, the table is cleared and the bucketed
+            // reduction below runs instead
             const uint32_t per_pass = (uint32_t)(H - (H >> 2)) - (uint32_t)((H - (H >> 2)) >> 2);
-            unsigned long long lo = 0, retry_hi = 0;
-            for (;;) {
+            bool reduced = false;
+            if (SKETCH && s_nsub <= per_pass) {   // block-uniform
+                if (tid == 0) s_fill = 0;
                 __syncthreads();
-                if (tid == 0) {
-                    unsigned long long l = lo, h = retry_hi;
-                    if (!h) {
-                        uint32_t b0 = (uint32_t)(l >> 24);
-                        while (b0 < 256u && s_hist[b0] == 0u) ++b0;
-                        if (b0 > (uint32_t)(l >> 24)) l = (unsigned long long)b0 << 24;
-                        if (b0 < 256u) {
-                            uint32_t b1 = b0 + 1, c = s_hist[b0];
-                            while (b1 < 256u && c + s_hist[b1] <= per_pass) c += s_hist[b1++];
-                            h = (unsigned long long)b1 << 24;
-                        } else {
-                            l = h = 1ull << 32;
-                        }
-                    }
-                    s_pass_lo = l;
-                    s_pass_hi = h;
-                }
-                __syncthreads();
-                lo = s_pass_lo;
-                const unsigned long long hi = s_pass_hi;
-                if (lo >= (1ull << 32)) break;
-                const uint32_t e0 = s_bstart[lo >> 24], e1 = s_bstart[((hi - 1) >> 24) + 1];
+                const uint32_t nh = s_nsub;
                 bool ok = true;
-                for (uint32_t eb = e0 + tid; eb < e1 && ok; eb += UL * B) {
-                    uint32_t key[UL];
-                    unsigned long long val[UL];
+                for (uint32_t e0 = tid; e0 < nh; e0 += UF * B) {
+                    uint2 key[UF];
 #pragma unroll
-                    for (int u = 0; u < UL; ++u) {
-                        const uint2 kk = eb + u * B < e1 ? lb[eb + u * B] : make_uint2(kEmpty, 0u);
-                        key[u] = kk.x;
-                        val[u] = kk.x != kEmpty ? log_add(kk, lv2, eb + u * B) : 0ull;
-                    }
+                    for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nh ? lc2[e0 + u * B] : make_uint2(kEmpty, 0u);
 #pragma unroll
-                    for (int u = 0; u < UL; ++u) {
-                        if (key[u] == kEmpty) continue;
-                        const unsigned long long hv = key[u] * kPartMul;
-                        if (hv < lo || hv >= hi || s_hist[hv >> 24] == 0u) continue;
-                        if (!onchip_add(key[u], val[u])) ok = false;
-                    }
+                    for (int u = 0; u < UF; ++u)
+                        if (key[u].x != kEmpty && !onchip_add(key[u].x, log_add(key[u], lv2, 0u))) ok = false;
                 }
                 if (__syncthreads_or(!ok)) {
                     clear_table();
-                    if (hi - lo > 1) {
-                        retry_hi = lo + ((hi - lo) >> 1);
-                    } else {   // one hash value is one column, which always fits: not reached
-                        report(a.st, row, MCMI_ERR_CAPACITY);
-                        retry_hi = 0;
-                        lo = hi;
-                    }
                 } else {
                     finish_table(true, true);
-                    retry_hi = 0;
-                    lo = hi;
+                    reduced = true;
                 }
                 __syncthreads();
                 if (tid == 0) s_fill = 0;
+                __syncthreads();
             }
+            if (!reduced) {   // block-uniform
+                // bucket starts: exclusive scan of the 256 counts (warp 0, 8 per lane)
+                if (tid < 32) {
+                    uint32_t c8[8], tot = 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        c8[u] = s_hist[8 * tid + u];
+                        tot += c8[u];
+                    }
+                    uint32_t incl = tot;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t nb = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                        if (tid >= o) incl += nb;
+                    }
+                    uint32_t run = incl - tot;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        s_bstart[8 * tid + u] = run;
+                        s_hist[8 * tid + u] = run;   // scatter cursor
+                        run += c8[u];
+                    }
+                    if (tid == 31) s_bstart[256] = run;
+                }
+                __syncthreads();
+                // bucketed copy: SKETCH kernels scatter their compact list of hot
+                // entries from lc2 into lc, the others the whole log from lc into lc2
+                const uint2 *src = SKETCH ? lc2 : lc;
+                uint2 *const lb = SKETCH ? lc : lc2;
+                const uint32_t nsrc = SKETCH ? s_nsub : nlog;
+                for (uint32_t e0 = tid; e0 < nsrc; e0 += UL * B) {
+                    uint2 key[UL];
+                    unsigned long long val[UL];
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) key[u] = e0 + u * B < nsrc ? src[e0 + u * B] : make_uint2(kEmpty, 0u);
+                    if (!SKETCH) {
+#pragma unroll
+                        for (int u = 0; u < UL; ++u) val[u] = key[u].x != kEmpty ? lv[e0 + u * B] : 0ull;
+                    }
+#pragma unroll
+                    for (int u = 0; u < UL; ++u) {
+                        if (key[u].x == kEmpty) continue;
+                        const uint32_t p = atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
+                        lb[p] = key[u];
+                        if (!SKETCH) lv2[p] = val[u];
+                    }
+                }
+                if (tid == 0) s_fill = 0;
+                __syncthreads();
+                // Buckets of at most 32 entries: one warp each.  Lanes holding the
+                // same column find each other with __match_any_sync; the group's
+                // lowest lane sums it in a per-warp scratch row of 64-bit words
+                // (over the empty table's low words, which needs 2B <= H slots) and
+                // appends the finished entry.
+                const bool by_warp = 2 * B <= H;
+                if (by_warp) {
+                    unsigned long long *scratch = reinterpret_cast<unsigned long long *>(s_lo) + (tid & ~31);
+                    constexpr int UB = 2;   // buckets per iteration: their loads are in flight together
+                    const int nw = B >> 5;
+                    for (int bk0 = tid >> 5; bk0 < 256; bk0 += UB * nw) {
+                        uint2 key[UB];
+                        unsigned long long val[UB];
+                        uint32_t cnt[UB];
+#pragma unroll
+                        for (int u = 0; u < UB; ++u) {
+                            const int bk = bk0 + u * nw;
+                            const uint32_t s0 = bk < 256 ? s_bstart[bk] : 0u;
+                            cnt[u] = bk < 256 ? s_bstart[bk + 1] - s0 : 0u;
+                            const bool act = cnt[u] <= 32u && lane < cnt[u];
+                            key[u] = act ? lb[s0 + lane] : make_uint2(kEmpty, 0u);
+                            val[u] = act ? log_add(key[u], lv2, s0 + lane) : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < UB; ++u) {
+                            if (cnt[u] == 0u || cnt[u] > 32u) continue;   // warp-uniform
+                            const bool act = lane < cnt[u];
+                            const uint32_t grp = __match_any_sync(0xFFFFFFFFu, key[u].x);
+                            const uint32_t leader = (uint32_t)__ffs(grp) - 1u;
+                            // a column seen once is its own sum; groups of several
+                            // lanes add up in the warp's scratch row
+                            const bool single = (grp & (grp - 1u)) == 0u;
+                            if (!__all_sync(0xFFFFFFFFu, single || !act)) {
+                                scratch[lane] = 0ull;
+                                __syncwarp();
+                                if (act && !single) {
+                                    if (FIX) fix_add_shared(&scratch[leader], (long long)val[u]);
+                                    else comp_add(&scratch[leader], __uint_as_float((uint32_t)val[u]));
+                                }
+                                __syncwarp();
+                            }
+                            const bool lead = act && lane == leader;
+                            VT v = (VT)0;
+                            bool keep = false;
+                            if (lead) {
+                                const VT invd = log_invd(key[u]);
+                                v = finish(single ? val[u] : scratch[lane], invd);
+                                const VT av = v < (VT)0 ? -v : v;
+                                lmax = av > lmax ? av : lmax;
+                                keep = !(av < lowthr);
+                                ++nred;
+                            }
+                            const uint32_t lm = __ballot_sync(0xFFFFFFFFu, keep);
+                            const int first = __ffs(lm) - 1;
+                            uint32_t base = 0;
+                            if (lm && (int)lane == first) base = atomicAdd(&s_nent, (uint32_t)__popc(lm));
+                            if (lm) base = __shfl_sync(0xFFFFFFFFu, base, first);
+                            if (keep) {
+                                const uint32_t p = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
+                                ec[p] = key[u].x;
+                                ev[p] = enc(v);
+                                if (DUMP) ecn[p] = (uint32_t)__popc(grp);
+                            }
+                            __syncwarp();
+                        }
+                    }
+                    scratch[lane] = 0ull;
+                }
+                // larger buckets stay pending: s_hist[b] = entries of pending bucket b, else 0
+                for (int bk = tid; bk < 256; bk += B) {
+                    const uint32_t cnt = s_bstart[bk + 1] - s_bstart[bk];
+                    s_hist[bk] = (cnt > 32u || !by_warp) ? cnt : 0u;
+                }
+                // Pending buckets: passes over hash ranges [lo, hi) holding at most
+                // per_pass of their entries (so at most per_pass distinct columns)
+                // through the on-chip table; a pass that still does not fit is
+                // retried on the lower half of its range.
+                unsigned long long lo = 0, retry_hi = 0;
+                for (;;) {
+                    __syncthreads();
+                    if (tid == 0) {
+                        unsigned long long l = lo, h = retry_hi;
+                        if (!h) {
+                            uint32_t b0 = (uint32_t)(l >> 24);
+                            while (b0 < 256u && s_hist[b0] == 0u) ++b0;
+                            if (b0 > (uint32_t)(l >> 24)) l = (unsigned long long)b0 << 24;
+                            if (b0 < 256u) {
+                                uint32_t b1 = b0 + 1, c = s_hist[b0];
+                                while (b1 < 256u && c + s_hist[b1] <= per_pass) c += s_hist[b1++];
+                                h = (unsigned long long)b1 << 24;
+                            } else {
+                                l = h = 1ull << 32;
+                            }
+                        }
+                        s_pass_lo = l;
+                        s_pass_hi = h;
+                    }
+                    __syncthreads();
+                    lo = s_pass_lo;
+                    const unsigned long long hi = s_pass_hi;
+                    if (lo >= (1ull << 32)) break;
+                    const uint32_t e0 = s_bstart[lo >> 24], e1 = s_bstart[((hi - 1) >> 24) + 1];
+                    bool ok = true;
+                    for (uint32_t eb = e0 + tid; eb < e1 && ok; eb += UL * B) {
+                        uint32_t key[UL];
+                        unsigned long long val[UL];
+#pragma unroll
+                        for (int u = 0; u < UL; ++u) {
+                            const uint2 kk = eb + u * B < e1 ? lb[eb + u * B] : make_uint2(kEmpty, 0u);
+                            key[u] = kk.x;
+                            val[u] = kk.x != kEmpty ? log_add(kk, lv2, eb + u * B) : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < UL; ++u) {
+                            if (key[u] == kEmpty) continue;
+                            const unsigned long long hv = key[u] * kPartMul;
+                            if (hv < lo || hv >= hi || s_hist[hv >> 24] == 0u) continue;
+                            if (!onchip_add(key[u], val[u])) ok = false;
+                        }
+                    }
+                    if (__syncthreads_or(!ok)) {
+                        clear_table();
+                        if (hi - lo > 1) {
+                            retry_hi = lo + ((hi - lo) >> 1);
+                        } else {   // one hash value is one column, which always fits: not reached
+                            report(a.st, row, MCMI_ERR_CAPACITY);
+                            retry_hi = 0;
+                            lo = hi;
+                        }
+                    } else {
+                        finish_table(true, true);
+                        retry_hi = 0;
+                        lo = hi;
+                    }
+                    __syncthreads();
+                    if (tid == 0) s_fill = 0;
+                }
+            }   // !reduced
             __syncthreads();
             if (nred) atomicAdd(&s_nred, nred);
             __syncthreads();
