@@ -248,7 +248,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 
     __shared__ long long s_row, s_pos, s_key_row;
     __shared__ int s_next_chain;
-    __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent, s_nred, s_nsub;
+    __shared__ uint32_t s_fill, s_wpos, s_ncand, s_nlog, s_nent, s_nred, s_nsub, s_nmrg;
     __shared__ long long s_off;
     __shared__ double s_diag;
     __shared__ unsigned long long s_pass_lo, s_pass_hi;
@@ -294,7 +294,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     if (SKETCH) {
         for (int c = tid; c < (1 << (kPresLog2 - 5)); c += B) s_pres[c] = 0u;
     }
-    if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; }
+    if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; s_nmrg = 0; }
 
     // Slot of col in the on-chip table, inserting it if absent; -1 when it
     // is not added.  Linear probing over 4-slot buckets, one 16-byte read per
@@ -304,10 +304,13 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     // or no free slot within the probe window), or the table is at its cap
     // and the column was not in the buckets searched.
     // With the walk-time sketch (walk == true in the walk loop): a column
-    // sets its presence bit before it is inserted, so once the table is at
-    // its cap, a column whose bit is clear was never inserted and goes to
-    // the log without reading the table; the merge after the walks looks up
-    // only the logged columns whose bit is set.
+    // sets its presence bit, then takes a fill ticket (never given back),
+    // then claims its slot, and only a ticket below the cap may insert.  So
+    // once a visit has read a fill at the cap, a column whose bit it then
+    // finds clear can never be inserted: the visit returns -2 and goes to
+    // the main log, whose columns are never on chip.  A visit that read the
+    // table and still found no slot returns -1 and goes to the merge log,
+    // whose columns are looked up on chip after the walks.
     auto onchip_slot = [&](uint32_t col, bool walk) -> int {
         uint32_t bkt = hash_home(col, a.log2H - 2);
         const uint32_t nb = (uint32_t)(H >> 2);
@@ -315,10 +318,17 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // the same time may each still insert, so the table can pass the cap
         // by up to a block's threads (a small table may fill up; a probe then
         // gives up after its bucket limit and the visit is logged)
-        const bool capped = *(volatile uint32_t *)&s_fill >= fill_cap;
         const bool pres = SKETCH && walk;
+        uint32_t fill_now;
+        if (pres) {   // acquire: the presence bits set before the tickets read here are seen below
+            asm volatile("ld.acquire.cta.shared.u32 %0, [%1];"
+                         : "=r"(fill_now) : "r"((uint32_t)__cvta_generic_to_shared(&s_fill)) : "memory");
+        } else {
+            fill_now = *(volatile uint32_t *)&s_fill;
+        }
+        const bool capped = fill_now >= fill_cap;
         const uint32_t pb = (col * kPresMul) >> (32 - kPresLog2);
-        if (pres && capped && !((*(volatile uint32_t *)&s_pres[pb >> 5] >> (pb & 31)) & 1u)) return -1;
+        if (pres && capped && !((*(volatile uint32_t *)&s_pres[pb >> 5] >> (pb & 31)) & 1u)) return -2;
         bool marked = false;
 #pragma unroll 1
         for (int p = 0; p < kProbeOnChip / 4; ++p) {
@@ -334,9 +344,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 if (pres && !marked) {
                     atomicOr(&s_pres[pb >> 5], 1u << (pb & 31));
                     marked = true;
+                    __threadfence_block();   // the bit before the ticket
+                    if (atomicAdd(&s_fill, 1u) >= fill_cap) return -1;
                 }
                 const uint32_t old = atomicCAS(&s_keys[4 * bkt + e], kEmpty, col);
-                if (old == kEmpty) atomicAdd(&s_fill, 1u);
+                if (!pres && old == kEmpty) atomicAdd(&s_fill, 1u);
                 if (old == kEmpty || old == col) return (int)(4 * bkt) + e;
                 --p;   // another key took the slot: read the bucket again
                 continue;
@@ -495,20 +507,33 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 }
                 // visits that do not fit on chip go to the log with the FP32 bits
                 // of 1/d_col from the record just read; one atomic per warp
+                // (sketch kernels: the main log for h == -2, the merge log in
+                // the second region for h == -1)
                 const bool to_log = acc && h < 0;
-                const uint32_t lm = __ballot_sync(0xFFFFFFFFu, to_log);
-                if (lm) {
-                    const int first = __ffs(lm) - 1;
-                    uint32_t base = 0;
-                    if ((int)lane == first) base = atomicAdd(&s_nlog, (uint32_t)__popc(lm));
-                    base = __shfl_sync(0xFFFFFFFFu, base, first);
+                const uint32_t lall = __ballot_sync(0xFFFFFFFFu, to_log);
+                if (lall) {
+                    const uint32_t lmg = SKETCH ? __ballot_sync(0xFFFFFFFFu, to_log && h == -1) : 0u;
+                    const uint32_t lm = lall & ~lmg;
+                    const uint32_t lt = (1u << lane) - 1u;
+                    uint32_t base = 0, mbase = 0;
+                    if (lm) {
+                        const int first = __ffs(lm) - 1;
+                        if ((int)lane == first) base = atomicAdd(&s_nlog, (uint32_t)__popc(lm));
+                        base = __shfl_sync(0xFFFFFFFFu, base, first);
+                    }
+                    if (SKETCH && lmg) {
+                        const int first = __ffs(lmg) - 1;
+                        if ((int)lane == first) mbase = atomicAdd(&s_nmrg, (uint32_t)__popc(lmg));
+                        mbase = __shfl_sync(0xFFFFFFFFu, mbase, first);
+                    }
                     if (to_log) {
-                        const uint32_t pos = base + (uint32_t)__popc(lm & ((1u << lane) - 1u));
+                        const bool mrg = SKETCH && h == -1;
+                        const uint32_t pos = mrg ? mbase + (uint32_t)__popc(lmg & lt) : base + (uint32_t)__popc(lm & lt);
                         if (pos < a.log_cap) {
                             if (SKETCH) {
                                 // one 8-byte entry {column, FP32 bits of W}: the
                                 // addend fix_f32s(W) is recomputed when read
-                                lc[pos] = make_uint2(st[j], __float_as_uint(w[j]));
+                                (mrg ? lc2 : lc)[pos] = make_uint2(st[j], __float_as_uint(w[j]));
                                 const float invd_j = CMP ? __ldg(a.invd32 + st[j]) : __uint_as_float(s[j][2]);
                                 const float q = __fmul_ru(__fmul_ru(fabsf(w[j]), fabsf(invd_j)), s_cscale);
                                 uint32_t *cell = &g_cells[(st[j] * kSketchMul) >> (32 - kCellsLog2)];
@@ -561,7 +586,9 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             s_wpos = 0;
             s_ncand = 0;
         }
-        const uint32_t nlog = min(s_nlog, a.log_cap);
+        uint32_t nlog = min(s_nlog, a.log_cap);
+        const uint32_t nmrg = min(s_nmrg, a.log_cap);   // 0 in the kernels without the sketch
+        const bool touched = nlog != 0u || nmrg != 0u;   // the row's sketch cells were used
 
         // finished values M_ij = (1/N) X_ij / d_j of the raw accumulator
         // words; invd = 1/d_j (the record's FP32 copy, or FP64), unused by the
@@ -669,29 +696,28 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             return (VT)__uint_as_float(key.y);
         };
         uint32_t nrem = 0;
-        if (SKETCH && nlog) {   // block-uniform
-            // entries whose column may be on chip (presence bit set) are
-            // looked up and added there; the others cannot be on chip
-            for (uint32_t e0 = tid; e0 < nlog; e0 += UF * B) {
+        if (SKETCH && touched) {   // block-uniform
+            // the merge log's columns are looked up on chip and added there;
+            // those not found join the main log, whose columns are not on chip
+            for (uint32_t e0 = tid; e0 < nmrg; e0 += UF * B) {
                 uint2 key[UF];
 #pragma unroll
-                for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
+                for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nmrg ? lc2[e0 + u * B] : make_uint2(kEmpty, 0u);
 #pragma unroll
                 for (int u = 0; u < UF; ++u) {
                     if (key[u].x == kEmpty) continue;
-                    const uint32_t pb = (key[u].x * kPresMul) >> (32 - kPresLog2);
-                    if ((s_pres[pb >> 5] >> (pb & 31)) & 1u) {
-                        const int h = onchip_find(key[u].x);
-                        if (h >= 0) {
-                            val_add((uint32_t)h, log_add(key[u], lv, 0u));
-                            lc[e0 + u * B].x = kEmpty;
-                            continue;
-                        }
+                    const int h = onchip_find(key[u].x);
+                    if (h >= 0) {
+                        val_add((uint32_t)h, log_add(key[u], lv, 0u));
+                    } else {
+                        const uint32_t p = atomicAdd(&s_nlog, 1u);   // < log_cap: the two logs hold one row's visits
+                        if (p < a.log_cap) lc[p] = key[u];
                     }
-                    ++nrem;
                 }
             }
-            nrem = (uint32_t)block_sum(nrem, s_redu);
+            __syncthreads();
+            nlog = min(s_nlog, a.log_cap);
+            nrem = nlog;
             // the presence map's words become the histogram again
             for (int b = tid; b < 256; b += B) s_hist[b] = 0;
             __syncthreads();
@@ -1271,12 +1297,12 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // ---- reset the accumulator for the next row ----
         clear_table();
         if (SKETCH) {
-            if (nlog) {   // block-uniform: only a row that logged visits touched its cells
+            if (touched) {   // block-uniform: only a row that logged visits touched its cells
                 for (int c = tid; c < kCells / 4; c += B) reinterpret_cast<uint4 *>(g_cells)[c] = make_uint4(0, 0, 0, 0);
             }
             for (int c = tid; c < (1 << (kPresLog2 - 5)); c += B) s_pres[c] = 0u;
         }
-        if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; }
+        if (tid == 0) { s_fill = 0; s_nlog = 0; s_nent = 0; s_nred = 0; s_nmrg = 0; }
     }
 }
 
