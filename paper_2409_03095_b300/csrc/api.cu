@@ -1245,7 +1245,7 @@ mcmi_status mcmi_apply(mcmi_matrix M, const float *x, float *y, void *stream)
     if (!M) return fail(MCMI_ERR_ARG, "M is NULL");
     if (M->rows > 0 && (!x || !y)) return fail(MCMI_ERR_ARG, "NULL vector");
     if (M->rows == 0) return MCMI_OK;
-    cudaError_t e = launch_spmv(M->rows, M->rp, M->col, M->val, x, y, (cudaStream_t)stream);
+    cudaError_t e = launch_spmv(M->rows, M->nnz, M->rp, M->col, M->val, x, y, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "apply");
     return MCMI_OK;
 }

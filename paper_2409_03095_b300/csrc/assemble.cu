@@ -562,36 +562,41 @@ cudaError_t launch_assemble(int64_t rows, const int64_t *row_ptr, const int64_t 
     return cudaGetLastError();
 }
 
-// y = M x, eight lanes per row.
+// y = M x, LANES lanes per row (8 for short rows, a warp for long ones).
+template <int LANES>
 __global__ void k_spmv(int64_t rows, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                        const float *__restrict__ val, const float *__restrict__ x, float *__restrict__ y)
 {
-    const int sub = threadIdx.x & 7;
-    const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 3;
-    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) >> 3;
-    // the loop bound is uniform across the warp (4 row groups per warp) so
+    constexpr int G = 32 / LANES;   // rows per warp
+    const int sub = threadIdx.x & (LANES - 1);
+    const int64_t grp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LANES;
+    const int64_t ngrp = ((int64_t)gridDim.x * blockDim.x) / LANES;
+    // the loop bound is uniform across the warp (G row groups per warp) so
     // that every lane reaches the shuffles
-    for (int64_t r0 = grp & ~(int64_t)3; r0 < rows; r0 += ngrp) {
-        const int64_t r = r0 + (grp & 3);
+    for (int64_t r0 = grp - (grp % G); r0 < rows; r0 += ngrp) {
+        const int64_t r = r0 + (grp % G);
         float acc = 0.0f;
         if (r < rows)
-            for (int64_t k = rp[r] + sub; k < rp[r + 1]; k += 8)
+            for (int64_t k = rp[r] + sub; k < rp[r + 1]; k += LANES)
                 acc = fmaf(__ldg(val + k), __ldg(x + __ldg(col + k)), acc);
-        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
-        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
-        acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+#pragma unroll
+        for (int o = LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if (sub == 0 && r < rows) y[r] = acc;
     }
 }
 
-cudaError_t launch_spmv(int64_t rows, const int64_t *rp, const int32_t *col, const float *val, const float *x,
-                        float *y, cudaStream_t s)
+cudaError_t launch_spmv(int64_t rows, int64_t nnz, const int64_t *rp, const int32_t *col, const float *val,
+                        const float *x, float *y, cudaStream_t s)
 {
     const int bs = 256;
-    int64_t g = (rows * 8 + bs - 1) / bs;
+    // rows of more than 64 entries on average take a warp each
+    const bool wide = rows > 0 && nnz > 64 * rows;
+    const int lanes = wide ? 32 : 8;
+    int64_t g = (rows * lanes + bs - 1) / bs;
     if (g > 148 * 16) g = 148 * 16;
     if (g < 1) g = 1;
-    k_spmv<<<(unsigned)g, bs, 0, s>>>(rows, rp, col, val, x, y);
+    if (wide) k_spmv<32><<<(unsigned)g, bs, 0, s>>>(rows, rp, col, val, x, y);
+    else k_spmv<8><<<(unsigned)g, bs, 0, s>>>(rows, rp, col, val, x, y);
     return cudaGetLastError();
 }
 

@@ -76,8 +76,8 @@ cudaError_t launch_split(const BatchOut *out, int count, const int64_t *row_base
                          int64_t total_rows, int64_t total_nnz, const int64_t *rpM, const int32_t *colM,
                          const float *valM, cudaStream_t s);
 
-cudaError_t launch_spmv(int64_t rows, const int64_t *rp, const int32_t *col, const float *val, const float *x,
-                        float *y, cudaStream_t s);
+cudaError_t launch_spmv(int64_t rows, int64_t nnz, const int64_t *rp, const int32_t *col, const float *val,
+                        const float *x, float *y, cudaStream_t s);
 
 // recovery of B^-1 (Eq. 3) and dense copies
 cudaError_t launch_aug_diag(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
