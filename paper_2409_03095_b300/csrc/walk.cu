@@ -311,6 +311,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     // the main log, whose columns are never on chip.  A visit that read the
     // table and still found no slot returns -1 and goes to the merge log,
     // whose columns are looked up on chip after the walks.
+    bool seen_cap = false;   // this thread has read the fill at the cap during the current row's walks
     auto onchip_slot = [&](uint32_t col, bool walk) -> int {
         uint32_t bkt = hash_home(col, a.log2H - 2);
         const uint32_t nb = (uint32_t)(H >> 2);
@@ -319,14 +320,18 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // by up to a block's threads (a small table may fill up; a probe then
         // gives up after its bucket limit and the visit is logged)
         const bool pres = SKETCH && walk;
-        uint32_t fill_now;
-        if (pres) {   // acquire: the presence bits set before the tickets read here are seen below
-            asm volatile("ld.acquire.cta.shared.u32 %0, [%1];"
-                         : "=r"(fill_now) : "r"((uint32_t)__cvta_generic_to_shared(&s_fill)) : "memory");
-        } else {
-            fill_now = *(volatile uint32_t *)&s_fill;
+        bool capped = pres && seen_cap;   // the fill only grows: once seen at the cap, it stays there
+        if (!capped) {
+            uint32_t fill_now;
+            if (pres) {   // acquire: the presence bits set before the tickets read here are seen below
+                asm volatile("ld.acquire.cta.shared.u32 %0, [%1];"
+                             : "=r"(fill_now) : "r"((uint32_t)__cvta_generic_to_shared(&s_fill)) : "memory");
+            } else {
+                fill_now = *(volatile uint32_t *)&s_fill;
+            }
+            capped = fill_now >= fill_cap;
+            if (pres && capped) seen_cap = true;
         }
-        const bool capped = fill_now >= fill_cap;
         const uint32_t pb = (col * kPresMul) >> (32 - kPresLog2);
         if (pres && capped && !((*(volatile uint32_t *)&s_pres[pb >> 5] >> (pb & 31)) & 1u)) return -2;
         bool marked = false;
@@ -443,6 +448,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // CPT dependent gathers are in flight per thread; a chain that stops
         // is replaced by the row's next chain index ----
         unsigned long long my_steps = 0;
+        seen_cap = false;
         uint32_t st[CPT];
         float w[CPT];            // FP32 weight (the FP64 path keeps it as the stop shadow)
         double w64[CPT];
@@ -645,6 +651,12 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // is larger, so the entry list keeps only possible candidates (0: keep
         // everything).
         VT lowthr = (VT)0;
+        // sketch kernels with tau: tau |M_ii| (rounded down) also bounds the
+        // threshold from below, before any other entry is finished: the
+        // diagonal is exact after the walks (inserted first, in the first slot
+        // of its home bucket, where every visit of it finds it), so on-chip
+        // entries below it need not go to the entry list
+        VT lowpre = (VT)0;
         uint32_t nred = 0;   // distinct log columns this thread reduced (statistics)
         // Finishes the on-chip entries, in place, or appended to the entry
         // list with the table cleared (from_log: entries reduced from the log).
@@ -666,7 +678,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     if (key[u] == (uint32_t)row) s_diag = (double)v;
                     if (to_list) {
                         nred += from_log;
-                        if (!(from_log && av < lowthr)) {
+                        if (!(av < (from_log ? lowthr : lowpre))) {
                             const uint32_t p = atomicAdd(&s_nent, 1u);
                             ec[p] = key[u];
                             ev[p] = enc(v);
@@ -747,6 +759,17 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             nrem = (uint32_t)block_sum(nrem, s_redu);
         }
         if (nrem) {   // block-uniform
+            if (SKETCH && use_tau && PREC == 32) {
+                if (tid == 0) {
+                    const uint32_t rr = (uint32_t)row;
+                    const uint32_t h0 = 4u * hash_home(rr, a.log2H - 2);
+                    const float vd = fabsf((float)finish(vword(h0), load_invd(rr)));
+                    s_redf[0] = __fmul_rd(__double2float_rd(a.tau), vd);
+                }
+                __syncthreads();
+                lowpre = (VT)s_redf[0];
+                __syncthreads();
+            }
             finish_table(true, false);
             if (!DUMP && use_tau) {
                 // the on-chip entries (the diagonal among them) bound the row maximum from below
@@ -801,8 +824,17 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 const float tf = __fmul_rd(__fmul_rd(__fmul_rd((float)lowthr, s_cscale), (float)a.N), 1.0f - 0x1p-20f);
                 Tc = !(tf >= 0.0f) ? 0u : (tf >= 2147483648.0f ? kCellFlag : (uint32_t)tf);
             }
+            // the cells, staged in the emptied table's value words (one
+            // coalesced copy instead of a gather per log entry)
+            const bool staged = SKETCH && 2 * H >= kCells;   // block-uniform
+            if (staged) {
+                for (int c = tid; c < kCells / 4; c += B)
+                    reinterpret_cast<uint4 *>(s_lo)[c] = __ldcg(reinterpret_cast<const uint4 *>(g_cells) + c);
+                __syncthreads();
+            }
             auto hot = [&](uint32_t col) -> bool {
-                const uint32_t c = __ldcg(&g_cells[(col * kSketchMul) >> (32 - kCellsLog2)]);
+                const uint32_t ci = (col * kSketchMul) >> (32 - kCellsLog2);
+                const uint32_t c = staged ? s_lo[ci] : __ldcg(&g_cells[ci]);
                 return (c & kCellFlag) || c >= Tc;
             };
             // SKETCH: one pass keeps the entries of hot cells, appended in
@@ -823,6 +855,10 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         }
                 }
                 __syncthreads();
+                if (staged) {   // the value words back to zero
+                    for (int c = tid; c < kCells / 4; c += B) reinterpret_cast<uint4 *>(s_lo)[c] = make_uint4(0, 0, 0, 0);
+                    __syncthreads();
+                }
             }
             // SKETCH: when the kept entries fit the emptied table's pass size,
             // one pass adds them all on chip and finishes them (a few L2
@@ -907,7 +943,10 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 // lowest lane sums it in a per-warp scratch row of 64-bit words
                 // (over the empty table's low words, which needs 2B <= H slots) and
                 // appends the finished entry.
-                const bool by_warp = 2 * B <= H;
+                // (the sketch kernels reach here only when their kept entries did not
+                // fit one pass: hash-range passes through the table handle them faster
+                // than one warp per bucket)
+                const bool by_warp = !SKETCH && 2 * B <= H;
                 if (by_warp) {
                     unsigned long long *scratch = reinterpret_cast<unsigned long long *>(s_lo) + (tid & ~31);
                     constexpr int UB = 2;   // buckets per iteration: their loads are in flight together
