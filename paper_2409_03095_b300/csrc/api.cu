@@ -434,6 +434,14 @@ void fill_walk_args(WalkArgs &a, const mcmi_params *p, const Prepared &P, const 
     a.top_k = p->top_k;
     a.st = P.st;
     a.count_steps = 1;
+    // sketch kernels: the code of |1/d_j| rides in the spare top bits of the
+    // log's column words when at least 9 are free (columns below 2^23) and the
+    // table's value words can hold the cells; otherwise the walks add to the
+    // global cells
+    int nb = 0;
+    while (nb < 31 && ((int64_t)1 << nb) < P.n) ++nb;   // bits of the largest column index
+    const int cb = 32 - nb;
+    a.sk_code_bits = (cb >= 9 && 2 * ((size_t)1 << W.log2H) >= walk_sketch_cells()) ? (cb < 12 ? cb : 12) : 0;
 }
 
 // Per-block overflow log (visits in arrival order, then bucketed: two

@@ -105,6 +105,9 @@ struct WalkArgs {
     uint32_t *ent_cnt;            // parity dump: visit counts
     uint32_t *cells;              // walk-time magnitude sketch: walk_sketch_cells() words per block, zero
                                   // at launch (each block clears its cells after a row that used them)
+    int sk_code_bits;             // sketch kernels: 9..12 = the top bits of a log entry's column word hold
+                                  // a rounded-up code of |1/d_j| and the sketch is built after the walks
+                                  // in shared memory (cells unused); 0 = walk-time sketch in cells
     uint32_t ent_cap;             // entries per block (>= log_cap + on-chip slots)
     // filter
     double tau;

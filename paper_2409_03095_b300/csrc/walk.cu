@@ -63,6 +63,24 @@ __device__ __forceinline__ uint32_t hash_home(uint32_t key, int log2)
     return (key * 0x9E3779B1u) >> (32 - log2);
 }
 
+// Log entries of the sketch kernels with cb code bits (9..12): the column
+// in the low 32 - cb bits; in the top cb bits, bits 30 .. 31 - cb of the
+// FP32 pattern of |1/d_j| rounded up, at most 2^cb - 2, so that the decoded
+// value is >= |1/d_j| (infinite or NaN at the top codes) and a packed word
+// never equals the empty key 0xFFFFFFFF.
+__device__ __forceinline__ uint32_t sketch_pack(uint32_t col, float invd, int cb)
+{
+    const uint32_t sh = 31u - (uint32_t)cb;
+    const uint32_t b = __float_as_uint(invd) & 0x7FFFFFFFu;
+    const uint32_t code = min((b >> sh) + ((b & ((1u << sh) - 1u)) != 0u), (1u << cb) - 2u);
+    return col | (code << (sh + 1u));
+}
+
+__device__ __forceinline__ float sketch_decode(uint32_t word, int cb)
+{
+    return __uint_as_float((word >> (32 - cb)) << (31 - cb));
+}
+
 // w * 2^F (scale = 2^F as a float) rounded to the nearest integer, ties to
 // even, by one float-to-integer conversion: the product is exact, and for
 // FP32 walks with the |c| proposal F makes it an integer (every weight is a
@@ -284,6 +302,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     uint32_t *const g_cells = SKETCH ? a.cells + (size_t)blockIdx.x * kCells : nullptr;   // zero between rows
     // walk-time sketch: largest units one visit adds (a row logs at most log_cap visits)
     const float cell_cap = (float)(kCellFlag / (a.log_cap > 0u ? a.log_cap : 1u) - 1u);
+    // the column of a log entry's word (sketch kernels may keep a code in its top bits)
+    const uint32_t colmask = (SKETCH && a.sk_code_bits) ? (0xFFFFFFFFu >> a.sk_code_bits) : 0xFFFFFFFFu;
 
     for (int h = tid; h < H; h += B) {
         s_keys[h] = kEmpty;
@@ -538,13 +558,21 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                         if (pos < a.log_cap) {
                             if (SKETCH) {
                                 // one 8-byte entry {column, FP32 bits of W}: the
-                                // addend fix_f32s(W) is recomputed when read
-                                (mrg ? lc2 : lc)[pos] = make_uint2(st[j], __float_as_uint(w[j]));
+                                // addend fix_f32s(W) is recomputed when read; the
+                                // column word carries the code of |1/d_j| for the
+                                // sketch built after the walks, or the visit adds
+                                // its magnitude to the global cells now
                                 const float invd_j = CMP ? __ldg(a.invd32 + st[j]) : __uint_as_float(s[j][2]);
-                                const float q = __fmul_ru(__fmul_ru(fabsf(w[j]), fabsf(invd_j)), s_cscale);
-                                uint32_t *cell = &g_cells[(st[j] * kSketchMul) >> (32 - kCellsLog2)];
-                                if (q < cell_cap) atomicAdd(cell, (uint32_t)ceilf(q));
-                                else atomicOr(cell, kCellFlag);   // large, infinite or NaN
+                                if (a.sk_code_bits) {
+                                    (mrg ? lc2 : lc)[pos] =
+                                        make_uint2(sketch_pack(st[j], invd_j, a.sk_code_bits), __float_as_uint(w[j]));
+                                } else {
+                                    (mrg ? lc2 : lc)[pos] = make_uint2(st[j], __float_as_uint(w[j]));
+                                    const float q = __fmul_ru(__fmul_ru(fabsf(w[j]), fabsf(invd_j)), s_cscale);
+                                    uint32_t *cell = &g_cells[(st[j] * kSketchMul) >> (32 - kCellsLog2)];
+                                    if (q < cell_cap) atomicAdd(cell, (uint32_t)ceilf(q));
+                                    else atomicOr(cell, kCellFlag);   // large, infinite or NaN
+                                }
                             } else {
                                 lc[pos] = make_uint2(st[j], CMP ? 0u : s[j][2]);   // compact: 1/d_j looked up later
                                 lv[pos] = add;
@@ -704,7 +732,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         };
         // 1/d_j of a log entry's column: carried in the entry, or looked up
         auto log_invd = [&](uint2 key) -> VT {
-            if (SKETCH || PREC == 64 || CMP) return load_invd(key.x);
+            if (SKETCH || PREC == 64 || CMP) return load_invd(key.x & colmask);
             return (VT)__uint_as_float(key.y);
         };
         uint32_t nrem = 0;
@@ -718,7 +746,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 #pragma unroll
                 for (int u = 0; u < UF; ++u) {
                     if (key[u].x == kEmpty) continue;
-                    const int h = onchip_find(key[u].x);
+                    const int h = onchip_find(key[u].x & colmask);
                     if (h >= 0) {
                         val_add((uint32_t)h, log_add(key[u], lv, 0u));
                     } else {
@@ -824,17 +852,41 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 const float tf = __fmul_rd(__fmul_rd(__fmul_rd((float)lowthr, s_cscale), (float)a.N), 1.0f - 0x1p-20f);
                 Tc = !(tf >= 0.0f) ? 0u : (tf >= 2147483648.0f ? kCellFlag : (uint32_t)tf);
             }
-            // the cells, staged in the emptied table's value words (one
-            // coalesced copy instead of a gather per log entry)
+            // the cells, staged in the emptied table's value words: copied
+            // from the walk-time cells (one coalesced copy instead of a gather
+            // per log entry), or built here from the main log's codes of
+            // |1/d_j| (the same units, by the same rounded-up products, of a
+            // value >= |1/d_j|; only the main log's columns, which the merge
+            // has left off chip)
             const bool staged = SKETCH && 2 * H >= kCells;   // block-uniform
             if (staged) {
-                for (int c = tid; c < kCells / 4; c += B)
-                    reinterpret_cast<uint4 *>(s_lo)[c] = __ldcg(reinterpret_cast<const uint4 *>(g_cells) + c);
+                if (a.sk_code_bits) {
+                    if (Tc != 0u) {   // block-uniform (Tc = 0: every cell is hot)
+                        __syncthreads();   // the table is empty
+                        for (uint32_t e0 = tid; e0 < nlog; e0 += UF * B) {
+                            uint2 key[UF];
+#pragma unroll
+                            for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
+#pragma unroll
+                            for (int u = 0; u < UF; ++u) {
+                                if (key[u].x == kEmpty) continue;
+                                const float q = __fmul_ru(__fmul_ru(fabsf(__uint_as_float(key[u].y)),
+                                                                    sketch_decode(key[u].x, a.sk_code_bits)), s_cscale);
+                                uint32_t *cell = &s_lo[((key[u].x & colmask) * kSketchMul) >> (32 - kCellsLog2)];
+                                if (q < cell_cap) atomicAdd(cell, (uint32_t)ceilf(q));
+                                else atomicOr(cell, kCellFlag);   // large, infinite or NaN
+                            }
+                        }
+                    }
+                } else {
+                    for (int c = tid; c < kCells / 4; c += B)
+                        reinterpret_cast<uint4 *>(s_lo)[c] = __ldcg(reinterpret_cast<const uint4 *>(g_cells) + c);
+                }
                 __syncthreads();
             }
             auto hot = [&](uint32_t col) -> bool {
                 const uint32_t ci = (col * kSketchMul) >> (32 - kCellsLog2);
-                const uint32_t c = staged ? s_lo[ci] : __ldcg(&g_cells[ci]);
+                const uint32_t c = staged ? s_lo[ci] : (a.sk_code_bits ? kCellFlag : __ldcg(&g_cells[ci]));
                 return (c & kCellFlag) || c >= Tc;
             };
             // SKETCH: one pass keeps the entries of hot cells, appended in
@@ -849,8 +901,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nlog ? lc[e0 + u * B] : make_uint2(kEmpty, 0u);
 #pragma unroll
                     for (int u = 0; u < UF; ++u)
-                        if (key[u].x != kEmpty && hot(key[u].x)) {
-                            atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
+                        if (key[u].x != kEmpty && hot(key[u].x & colmask)) {
+                            atomicAdd(&s_hist[((key[u].x & colmask) * kPartMul) >> 24], 1u);
                             lc2[atomicAdd(&s_nsub, 1u)] = key[u];
                         }
                 }
@@ -878,7 +930,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                     for (int u = 0; u < UF; ++u) key[u] = e0 + u * B < nh ? lc2[e0 + u * B] : make_uint2(kEmpty, 0u);
 #pragma unroll
                     for (int u = 0; u < UF; ++u)
-                        if (key[u].x != kEmpty && !onchip_add(key[u].x, log_add(key[u], lv2, 0u))) ok = false;
+                        if (key[u].x != kEmpty && !onchip_add(key[u].x & colmask, log_add(key[u], lv2, 0u))) ok = false;
                 }
                 if (__syncthreads_or(!ok)) {
                     clear_table();
@@ -931,7 +983,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 #pragma unroll
                     for (int u = 0; u < UL; ++u) {
                         if (key[u].x == kEmpty) continue;
-                        const uint32_t p = atomicAdd(&s_hist[(key[u].x * kPartMul) >> 24], 1u);
+                        const uint32_t p = atomicAdd(&s_hist[((key[u].x & colmask) * kPartMul) >> 24], 1u);
                         lb[p] = key[u];
                         if (!SKETCH) lv2[p] = val[u];
                     }
@@ -1050,7 +1102,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 #pragma unroll
                         for (int u = 0; u < UL; ++u) {
                             const uint2 kk = eb + u * B < e1 ? lb[eb + u * B] : make_uint2(kEmpty, 0u);
-                            key[u] = kk.x;
+                            key[u] = kk.x == kEmpty ? kEmpty : (kk.x & colmask);
                             val[u] = kk.x != kEmpty ? log_add(kk, lv2, eb + u * B) : 0ull;
                         }
 #pragma unroll
@@ -1336,7 +1388,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         // ---- reset the accumulator for the next row ----
         clear_table();
         if (SKETCH) {
-            if (touched) {   // block-uniform: only a row that logged visits touched its cells
+            if (touched && !a.sk_code_bits) {   // block-uniform: only a row that logged visits touched its cells
                 for (int c = tid; c < kCells / 4; c += B) reinterpret_cast<uint4 *>(g_cells)[c] = make_uint4(0, 0, 0, 0);
             }
             for (int c = tid; c < (1 << (kPresLog2 - 5)); c += B) s_pres[c] = 0u;

@@ -41,11 +41,12 @@ def _csr_rows(M):
     return rp, col, val
 
 
-def _check(name, m, B, p, M, rows, table, tau, top_k, alpha=0.0, theta=None, row_base=0):
-    """Dump parity and filtered-row parity of sampled rows; returns the errors."""
+def _check(name, m, B, p, M, rows, table, tau, top_k, alpha=0.0, theta=None, row_base=0, threads=0):
+    """Dump parity and filtered-row parity of sampled rows; returns the errors.
+    threads: oracle threads (0: all cores; each holds dense per-column sums)."""
     orc = _orc()
     orows, d, s = orc.walk(m, rows=rows, chains=p.chains, max_len=p.max_len, delta=p.delta, seed=p.seed,
-                           table=table, alpha=alpha, theta=theta)
+                           table=table, alpha=alpha, theta=theta, threads=threads)
     cap = max(len(r["col"]) for r in orows) + 16
     grows = mc.mcmi_walk_dump(B, p, rows, cap)
     d_max, d_med, d_bnd = P.compare_dump(grows, orows, d)
