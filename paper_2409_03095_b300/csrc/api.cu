@@ -173,7 +173,7 @@ struct Prepared {
     uint32_t *a = nullptr, *b = nullptr, *c = nullptr;
     uint4 *bkt = nullptr;
     uint4 *lbkt = nullptr;       // learned proposal: 32-byte buckets
-    float *invd32 = nullptr;     // compact table: fl32(1/d_i)
+    float *invd32 = nullptr;     // fl32(1/d_i): compact table, and FP32 builds of the |c| proposal
     bool learned = false;
     double2 *rowd = nullptr;
     double smax = 0.0, smin = 0.0;
@@ -295,7 +295,10 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     P.Lb = P.learned ? p->max_len : walk_len_bound(smax, p->delta, p->max_len);
     const bool alias_kind = table == MCMI_TABLE_ALIAS || table == MCMI_TABLE_HYBRID;
     P.slots = S.get<uint4>((size_t)n * (table == MCMI_TABLE_COMPACT ? 2 : 4));
-    if (table == MCMI_TABLE_COMPACT) P.invd32 = S.get<float>(n);
+    // fl32(1/d_i) per row: the compact table's only copy; beside the other
+    // tables' records (the finish after the walks then gathers from 4 bytes
+    // per row, which stay in L2, instead of the 64-byte records)
+    if (table == MCMI_TABLE_COMPACT || (p->precision == 32 && !P.learned)) P.invd32 = S.get<float>(n);
     P.a = S.get<uint32_t>(nnz);
     P.b = S.get<uint32_t>(nnz);
     unsigned long long *wscr = nullptr;

@@ -193,6 +193,7 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
         w[0] = (uint32_t)Q;
         w[1] = __float_as_uint(__double2float_rn(si));
         w[2] = __float_as_uint(__double2float_rn(__ddiv_rn(1.0, di)));
+        if (invd32) invd32[i] = __uint_as_float(w[2]);
         if (rowd) rowd[i] = make_double2(si, __ddiv_rn(1.0, di));
         const uint32_t begin = (uint32_t)a;
         // the hybrid table takes the cumulative layout for rows of at most

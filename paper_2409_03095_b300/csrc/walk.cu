@@ -625,12 +625,13 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
         const bool touched = nlog != 0u || nmrg != 0u;   // the row's sketch cells were used
 
         // finished values M_ij = (1/N) X_ij / d_j of the raw accumulator
-        // words; invd = 1/d_j (the record's FP32 copy, or FP64), unused by the
-        // Kahan accumulator, whose sums are already scaled
+        // words; invd = 1/d_j (FP32: the 4-byte-per-row array, which stays in
+        // L2, else the record's copy; or FP64), unused by the Kahan
+        // accumulator, whose sums are already scaled
         auto load_invd = [&](uint32_t col) -> VT {
             if (!FIX) return (VT)0;
             if (PREC == 64) return (VT)__ldg(&a.rowd[col].y);
-            if (CMP) return (VT)__ldg(a.invd32 + col);
+            if (CMP || a.invd32) return (VT)__ldg(a.invd32 + col);
             return (VT)__uint_as_float(__ldg(&a.slots[4 * (size_t)col].z));
         };
         auto finish = [&](unsigned long long raw, VT invd) -> VT {
