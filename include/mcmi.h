@@ -414,7 +414,9 @@ mcmi_status mcmi_gather_roofline(uint64_t footprint_bytes, int record_bytes, int
  * buffer of bucket_footprint_bytes and takes the next record index from it:
  * the walk's steps out of rows whose alias table is stored out of line.
  * *records_per_s (host) receives the record reads per second (each with its
- * bucket read where taken).  Allocates and frees both buffers
+ * bucket read where taken), the faster of two schedules: the bucket read
+ * within the step, or in the chain's next read slot while the lanes of the
+ * other chains go on (the walk's schedule on alias tables).  Allocates and frees both buffers
  * stream-ordered; synchronises `stream`.  Errors: MCMI_ERR_ARG (a footprint
  * < 4096, bucket_share outside [0, 1], bad launch shape), MCMI_ERR_OOM,
  * MCMI_ERR_CUDA.  (Sec. I, Sec. IV-B: random memory access limits the
