@@ -11,12 +11,16 @@ namespace mcmi {
 void launch_validate(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *col, const double *val,
                      DevState *st, cudaStream_t s);
 void launch_rownorm(int64_t n, const int64_t *rp, const double *val, DevState *st, cudaStream_t s);
+// rows ordered by CSR row length, longest first (counts32: 32 words of scratch)
+cudaError_t launch_len_order(int64_t n, const int64_t *rp, unsigned long long *counts32, int32_t *order,
+                             cudaStream_t s);
+// order: rows in the order the threads take them (nullptr: 0 .. n-1)
 void launch_split(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double alpha,
-                  double *d, double *sv, DevState *st, cudaStream_t s);
+                  double *d, double *sv, DevState *st, cudaStream_t s, const int32_t *order = nullptr);
 void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
                    const double *sv, int table, uint4 *slots, uint32_t *a, uint32_t *b, uint32_t *c,
                    uint4 *bkt, unsigned long long *wscr, uint32_t *sstk, uint32_t *lstk, double2 *rowd,
-                   float *invd32, cudaStream_t s);
+                   float *invd32, cudaStream_t s, const int32_t *order = nullptr);
 
 size_t walk_smem_bytes(int precision, int log2H, bool dump);
 // 32-bit cells per block of the walk-time magnitude sketch (a.cells)

@@ -33,6 +33,57 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ r
     }
 }
 
+// Rows ordered by the length of their CSR row, longest first, in 16 classes
+// (class 15 - min(floor(log2(len)), 15)), so that the threads of a warp of
+// the one-thread-per-row kernels below get rows of similar length: on
+// power-law rows a warp otherwise waits for its longest row.  The order
+// inside a class is arbitrary; the kernels' results do not depend on it.
+constexpr int kLenClasses = 16;
+
+__device__ __forceinline__ int len_class(int64_t len)
+{
+    const int b = len > 0 ? 63 - __clzll((unsigned long long)len) : 0;
+    return kLenClasses - 1 - (b < kLenClasses - 1 ? b : kLenClasses - 1);
+}
+
+// counts[0 .. 16): rows per class
+__global__ void k_len_count(int64_t n, const int64_t *__restrict__ rp, unsigned long long *__restrict__ counts)
+{
+    __shared__ unsigned int h[kLenClasses];
+    if (threadIdx.x < kLenClasses) h[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[len_class(rp[i + 1] - rp[i])], 1u);
+    __syncthreads();
+    if (threadIdx.x < kLenClasses && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], (unsigned long long)h[threadIdx.x]);
+}
+
+// order[...]: the rows, class by class (counts from k_len_count; cursor[16]
+// zero at launch).  Each block reserves its range of every class with one
+// atomic, then places its rows inside it.
+__global__ void k_len_scatter(int64_t n, const int64_t *__restrict__ rp, const unsigned long long *__restrict__ counts,
+                              unsigned long long *__restrict__ cursor, int32_t *__restrict__ order)
+{
+    __shared__ unsigned int h[kLenClasses];
+    __shared__ unsigned long long base[kLenClasses];
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        if (threadIdx.x < kLenClasses) h[threadIdx.x] = 0u;
+        __syncthreads();
+        const int c = i < n ? len_class(rp[i + 1] - rp[i]) : 0;
+        const unsigned int pos = i < n ? atomicAdd(&h[c], 1u) : 0u;
+        __syncthreads();
+        if (threadIdx.x < kLenClasses) {
+            unsigned long long start = 0;
+            for (int k = 0; k < (int)threadIdx.x; ++k) start += counts[k];
+            base[threadIdx.x] = start + (h[threadIdx.x] ? atomicAdd(&cursor[threadIdx.x], (unsigned long long)h[threadIdx.x]) : 0ull);
+        }
+        __syncthreads();
+        if (i < n) order[base[c] + pos] = (int32_t)i;
+        __syncthreads();
+    }
+}
+
 // ||B||_inf for the Eq. 1 augmentation.
 __global__ void k_rownorm(int64_t n, const int64_t *__restrict__ rp, const double *__restrict__ val,
                           DevState *st)
@@ -49,14 +100,15 @@ __global__ void k_rownorm(int64_t n, const int64_t *__restrict__ rp, const doubl
 // s_i = sum_j |c_ij| in CSR order (explicitly rounded operations, no FMA).
 __global__ void k_split(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                         const double *__restrict__ val, double alpha, double *__restrict__ d,
-                        double *__restrict__ s, DevState *st)
+                        double *__restrict__ s, DevState *st, const int32_t *__restrict__ order)
 {
     const double bnorm = __longlong_as_double((long long)st->bnorm_bits);
     // this thread's extremes over its rows, combined per warp before the
     // device-wide atomics (s_i >= 0: the bit patterns order like the values)
     unsigned long long smax = 0, smin = ~0ull, dmax = 0, omax = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = order ? (int64_t)order[q] : q;
         const int64_t a = rp[i], b = rp[i + 1];
         double bii = 0.0;
         unsigned long long ndeg = 0;   // off-diagonals and their largest |j - i|
@@ -133,10 +185,11 @@ __global__ void k_tables(int64_t n, const int64_t *__restrict__ rp, const int32_
                          uint32_t *__restrict__ ool_c, uint4 *__restrict__ ool_bkt,
                          unsigned long long *__restrict__ wscratch,
                          uint32_t *__restrict__ small_stk, uint32_t *__restrict__ large_stk,
-                         double2 *__restrict__ rowd, float *__restrict__ invd32)
+                         double2 *__restrict__ rowd, float *__restrict__ invd32, const int32_t *__restrict__ order)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = order ? (int64_t)order[q] : q;
         const int64_t a = rp[i], b = rp[i + 1];
         const double di = d[i], si = s[i];
         if (table == MCMI_TABLE_COMPACT) {
@@ -297,23 +350,36 @@ void launch_rownorm(int64_t n, const int64_t *rp, const double *val, DevState *s
     k_rownorm<<<(unsigned)(g < 148 * 32 ? g : 148 * 32), bs, 0, s>>>(n, rp, val, st);
 }
 
+cudaError_t launch_len_order(int64_t n, const int64_t *rp, unsigned long long *counts32, int32_t *order,
+                             cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(counts32, 0, 2 * kLenClasses * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int bs = 256;
+    const int64_t g = (n + bs - 1) / bs;
+    const unsigned grid = (unsigned)(g < 148 * 8 ? (g < 1 ? 1 : g) : 148 * 8);
+    k_len_count<<<grid, bs, 0, s>>>(n, rp, counts32);
+    k_len_scatter<<<grid, bs, 0, s>>>(n, rp, counts32, counts32 + kLenClasses, order);
+    return cudaGetLastError();
+}
+
 void launch_split(int64_t n, const int64_t *rp, const int32_t *col, const double *val, double alpha,
-                  double *d, double *sv, DevState *st, cudaStream_t s)
+                  double *d, double *sv, DevState *st, cudaStream_t s, const int32_t *order)
 {
     const int bs = 256;
     const int64_t g = (n + bs - 1) / bs;
-    k_split<<<(unsigned)(g < 148 * 32 ? g : 148 * 32), bs, 0, s>>>(n, rp, col, val, alpha, d, sv, st);
+    k_split<<<(unsigned)(g < 148 * 32 ? g : 148 * 32), bs, 0, s>>>(n, rp, col, val, alpha, d, sv, st, order);
 }
 
 void launch_tables(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *d,
                    const double *sv, int table, uint4 *slots, uint32_t *a, uint32_t *b, uint32_t *c,
                    uint4 *bkt, unsigned long long *wscr, uint32_t *sstk, uint32_t *lstk, double2 *rowd,
-                   float *invd32, cudaStream_t s)
+                   float *invd32, cudaStream_t s, const int32_t *order)
 {
     const int bs = 128;
     const int64_t g = (n + bs - 1) / bs;
     k_tables<<<(unsigned)(g < 148 * 64 ? g : 148 * 64), bs, 0, s>>>(n, rp, col, val, d, sv, table, slots, a,
-                                                                     b, c, bkt, wscr, sstk, lstk, rowd, invd32);
+                                                                     b, c, bkt, wscr, sstk, lstk, rowd, invd32, order);
 }
 
 }  // namespace mcmi
