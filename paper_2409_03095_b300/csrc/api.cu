@@ -257,12 +257,17 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
     if (r != MCMI_OK) return r;
     if (p->alpha > 0.0) launch_rownorm(n, B->row_ptr, B->val, P.st, s);
     // the split and the tables take one row per thread, in an order that
-    // gives each warp rows of similar length
-    int32_t *order = S.get<int32_t>(n);
-    unsigned long long *ocnt = S.get<unsigned long long>(32);
-    if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
-    cudaError_t oe = launch_len_order(n, B->row_ptr, ocnt, order, s);
-    if (oe != cudaSuccess) return cuda_fail(oe, "row order");
+    // gives each warp rows of similar length (from 2^16 rows on: below, the
+    // two ordering launches cost more than the balance gains)
+    int32_t *order = nullptr;
+    unsigned long long *ocnt = nullptr;
+    if (n >= (1 << 16)) {
+        order = S.get<int32_t>(n);
+        ocnt = S.get<unsigned long long>(32);
+        if (S.err != cudaSuccess) return cuda_fail(S.err, "allocation");
+        cudaError_t oe = launch_len_order(n, B->row_ptr, ocnt, order, s);
+        if (oe != cudaSuccess) return cuda_fail(oe, "row order");
+    }
     launch_split(n, B->row_ptr, B->col, B->val, p->alpha, P.d, P.s, P.st, s, order);
     r = read_state(P.st, &h, s);
     if (r != MCMI_OK) return r;
@@ -339,8 +344,8 @@ mcmi_status prepare(const mcmi_csr *B, const mcmi_params *p, cudaStream_t s, Scr
         launch_tables(n, B->row_ptr, B->col, B->val, P.d, P.s, table, P.slots, P.a, P.b, P.c, P.bkt, wscr, sstk,
                       lstk, P.rowd, P.invd32, s, order);
     }
-    S.release(ocnt);
-    S.release(order);
+    if (ocnt) S.release(ocnt);
+    if (order) S.release(order);
     if (wscr) S.release(wscr);
     if (sstk) S.release(sstk);
     if (lstk) S.release(lstk);
