@@ -84,6 +84,28 @@ def test_tables_bit_exact(name, table):
             assert np.array_equal(got[:, 0], prob) and np.array_equal(got[:, 1], cs) and np.array_equal(got[:, 2], cs[al])
 
 
+@pytest.mark.parametrize("table", [0, 1, 2])
+def test_tables_independent_of_row_order(table):
+    """From 2^16 rows on, the split and table kernels take the rows in order
+    of CSR row length.  A row's split and table depend only on its own entries
+    (and its offset), so the 4096 power-law rows (checked against the oracle
+    by test_tables_bit_exact) must come out the same when they open a matrix
+    of 2^16 + 4096 rows whose other rows are diagonal only."""
+    small = _cases_small()["powerlaw_4k"]
+    n = (1 << 16) + small.n
+    extra = n - small.n
+    big = synth.Csr(n, np.concatenate([small.row_ptr, small.nnz + np.arange(1, extra + 1, dtype=np.int64)]),
+                    np.concatenate([small.col, np.arange(small.n, n, dtype=np.int32)]),
+                    np.concatenate([small.val, np.ones(extra)]))
+    gs = mc.mcmi_debug_tables(mc.DeviceCsr.from_host(small), mc.params(table=table))
+    gb = mc.mcmi_debug_tables(mc.DeviceCsr.from_host(big), mc.params(table=table))
+    k, z = small.n, small.nnz
+    assert np.array_equal(gb["d"][:k], gs["d"]) and np.array_equal(gb["s"][:k], gs["s"])
+    assert np.array_equal(gb["slot"][:k], gs["slot"])
+    for a in ("a", "b", "c"):
+        assert np.array_equal(gb[a][:z], gs[a][:z])
+
+
 @pytest.mark.parametrize("name", ["stencil2d", "stencil3d_12"])
 def test_compact_tables_bit_exact(name):
     """The compact table's 32-byte records against the oracle's weights at
