@@ -40,19 +40,26 @@ namespace {
 constexpr int kProbeOnChip = 32;   // on-chip probe window before overflowing
 constexpr uint32_t kPartMul = 0x85EBCA77u;   // odd: col -> col * kPartMul permutes the 32-bit keys
 constexpr uint32_t kSketchMul = 0xC2B2AE35u;  // odd: cell of a column in the log's magnitude sketch
-// Walk-time sketch (the FP32 fixed-point production kernel at load depth 8): while a row
-// is walked, every visit that goes to the overflow log also adds its
-// magnitude |W| |1/d_j| to one of kCells cells (hash of the column; a
-// per-block array in global memory, updated by L2 atomics, so that the
-// shared memory left to the L1 cache is unchanged), in
-// units of |1/d_i| 2^-kCellUnitLog2 of the row i; a visit of 2^31 / (log
-// capacity) units or more sets the cell's top bit instead (the cell is then
-// always kept), so that the sums of a row's visits stay below 2^31.
+// Magnitude sketch of the overflow log (the FP32 fixed-point production
+// kernel at load depth 8): every logged visit adds its magnitude
+// |W| |1/d_j| to one cell (hash of the column), in units of
+// |1/d_i| 2^-kCellUnitLog2 of the row i; a visit of 2^31 / (log capacity)
+// units or more sets the cell's top bit instead (the cell is then always
+// kept), so that the sums of a row's visits stay below 2^31.  Either after
+// the walks, from a code of |1/d_j| in the log entries' column words, into
+// 2^kCellsCodeLog2 cells in the emptied table; or (columns too wide for the
+// code) during the walks into kCells cells of a per-block array in global
+// memory, updated by L2 atomics, so that the shared memory left to the L1
+// cache is unchanged.
 // A presence map of kPresBits bits (hash of the column) holds a superset of
 // the columns on chip; once the table is at its cap, a visit whose bit is
 // clear goes straight to the log without probing the table.
 constexpr int kCellsLog2 = 10;
 constexpr int kCells = 1 << kCellsLog2;
+// cells of the sketch built after the walks (in the emptied table's value
+// words, 2H of them at most): clearing shared cells costs little, so it
+// takes more than the global cells' 1024
+constexpr int kCellsCodeLog2 = 12;
 constexpr int kCellUnitLog2 = 14;
 constexpr uint32_t kCellFlag = 0x80000000u;
 constexpr int kPresLog2 = 14;                 // 16384 bits in 512 words
@@ -304,6 +311,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     const float cell_cap = (float)(kCellFlag / (a.log_cap > 0u ? a.log_cap : 1u) - 1u);
     // the column of a log entry's word (sketch kernels may keep a code in its top bits)
     const uint32_t colmask = (SKETCH && a.sk_code_bits) ? (0xFFFFFFFFu >> a.sk_code_bits) : 0xFFFFFFFFu;
+    // cells of the sketch: built after the walks (code form), or the walk-time global cells
+    const int cell_log2 = (SKETCH && a.sk_code_bits) ? min(kCellsCodeLog2, a.log2H + 1) : kCellsLog2;
 
     for (int h = tid; h < H; h += B) {
         s_keys[h] = kEmpty;
@@ -859,7 +868,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
             // |1/d_j| (the same units, by the same rounded-up products, of a
             // value >= |1/d_j|; only the main log's columns, which the merge
             // has left off chip)
-            const bool staged = SKETCH && 2 * H >= kCells;   // block-uniform
+            const bool staged = SKETCH && 2 * H >= (1 << cell_log2);   // block-uniform
             if (staged) {
                 if (a.sk_code_bits) {
                     if (Tc != 0u) {   // block-uniform (Tc = 0: every cell is hot)
@@ -873,7 +882,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                                 if (key[u].x == kEmpty) continue;
                                 const float q = __fmul_ru(__fmul_ru(fabsf(__uint_as_float(key[u].y)),
                                                                     sketch_decode(key[u].x, a.sk_code_bits)), s_cscale);
-                                uint32_t *cell = &s_lo[((key[u].x & colmask) * kSketchMul) >> (32 - kCellsLog2)];
+                                uint32_t *cell = &s_lo[((key[u].x & colmask) * kSketchMul) >> (32 - cell_log2)];
                                 if (q < cell_cap) atomicAdd(cell, (uint32_t)ceilf(q));
                                 else atomicOr(cell, kCellFlag);   // large, infinite or NaN
                             }
@@ -886,7 +895,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 __syncthreads();
             }
             auto hot = [&](uint32_t col) -> bool {
-                const uint32_t ci = (col * kSketchMul) >> (32 - kCellsLog2);
+                const uint32_t ci = (col * kSketchMul) >> (32 - cell_log2);
                 const uint32_t c = staged ? s_lo[ci] : (a.sk_code_bits ? kCellFlag : __ldcg(&g_cells[ci]));
                 return (c & kCellFlag) || c >= Tc;
             };
@@ -909,7 +918,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 }
                 __syncthreads();
                 if (staged) {   // the value words back to zero
-                    for (int c = tid; c < kCells / 4; c += B) reinterpret_cast<uint4 *>(s_lo)[c] = make_uint4(0, 0, 0, 0);
+                    for (int c = tid; c < (1 << cell_log2) / 4; c += B) reinterpret_cast<uint4 *>(s_lo)[c] = make_uint4(0, 0, 0, 0);
                     __syncthreads();
                 }
             }
