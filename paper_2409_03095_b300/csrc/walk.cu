@@ -235,8 +235,8 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
 {
     constexpr bool FIX = ACC == MCMI_ACC_FIXED64;
     constexpr bool CMP = TABLE == MCMI_TABLE_COMPACT;   // 32-byte records, 1/d_j from invd32
-    // 8-byte log entries, walk-time magnitude sketch and presence map, in the
-    // FP32 fixed-point production kernel for log-heavy rows (load depth 8;
+    // 8-byte log entries, the log's magnitude sketch and the presence map, in
+    // the FP32 fixed-point production kernel for log-heavy rows (load depth 8;
     // on the stencil-like rows of the depth-4 kernel they cost 12%)
     constexpr bool SKETCH = FIX && PREC == 32 && !DUMP && DEPTH == 8;
     // finished values and the filter work in the build's precision: FP32
@@ -286,7 +286,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     uint32_t *const s_bstart = s_hb + 256;
     uint32_t *const s_pres = s_hb;
     __shared__ uint32_t s_digit, s_rank;
-    __shared__ float s_cscale;   // walk-time sketch: units per |W| |1/d_j| for the current row
+    __shared__ float s_cscale;   // the log's sketch: units per |W| |1/d_j| for the current row
 
     const int tid = threadIdx.x, B = blockDim.x;
     // on-chip table kept <= 87.5% full during the walks with the compact table
@@ -307,7 +307,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     const float scaleF = __uint_as_float((uint32_t)(F + 127) << 23);   // 2^F (F <= 62)
     const bool use_tau = a.tau > 0.0;
     uint32_t *const g_cells = SKETCH ? a.cells + (size_t)blockIdx.x * kCells : nullptr;   // zero between rows
-    // walk-time sketch: largest units one visit adds (a row logs at most log_cap visits)
+    // the log's sketch: largest units one entry adds (a row logs at most log_cap visits)
     const float cell_cap = (float)(kCellFlag / (a.log_cap > 0u ? a.log_cap : 1u) - 1u);
     // the column of a log entry's word (sketch kernels may keep a code in its top bits)
     const uint32_t colmask = (SKETCH && a.sk_code_bits) ? (0xFFFFFFFFu >> a.sk_code_bits) : 0xFFFFFFFFu;
@@ -332,7 +332,7 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
     // -1: the column is absent and cannot be inserted (table at its fill cap,
     // or no free slot within the probe window), or the table is at its cap
     // and the column was not in the buckets searched.
-    // With the walk-time sketch (walk == true in the walk loop): a column
+    // In the sketch kernels (walk == true in the walk loop): a column
     // sets its presence bit, then takes a fill ticket (never given back),
     // then claims its slot, and only a ticket below the cap may insert.  So
     // once a visit has read a fill at the cap, a column whose bit it then
@@ -848,9 +848,11 @@ __global__ void __maxnreg__(CPT == 2 ? 80 : ((PREC == 64 || DEPTH == 8) ? 72 : 6
                 if (kb > (float)lowthr) lowthr = (VT)kb;
                 __syncthreads();
             }
-            // Walk-time magnitude sketch (SKETCH kernels): cell c holds at least
-            // s_cscale times the sum of |W| |1/d_j| over the logged visits of
-            // the columns that hash to it, or has its top bit set.  A column
+            // Magnitude sketch of the log (SKETCH kernels): cell c holds at
+            // least s_cscale times the sum of |W| |1/d_j| over the main log's
+            // entries (cells built below) or over all logged visits (walk-time
+            // global cells) of the columns that hash to it, or has its top bit
+            // set.  A column
             // that is not on chip finishes at |M_ij| <= (cell / (s_cscale N))
             // (1 + 2^-21) (the conversion and the finish's two products round
             // to nearest), so a column whose cell stays below
