@@ -81,3 +81,22 @@ def test_reference_arm_takes_the_librarys_table_choice():
     cols = np.concatenate([np.arange(n), [20000]])
     vals = np.concatenate([np.full(n, 4.0), [1.0]])
     assert bench._auto_table(synth._from_coo(n, rows, cols, vals)) == 0
+
+
+def test_reference_arm_line_on_a_small_workload(capsys):
+    """The reference arm prints one JSON line with the oracle's rate on a
+    row sample that the warm-up step may re-size but never beyond the
+    matrix (here the whole 1024-row matrix fits the time budget)."""
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    if dist.is_initialized():
+        pytest.skip("a process group is already initialised")
+
+    class A:
+        workload, steps, warmup, gpus = "stencil2d_32x32", 1, 1, 1
+    assert bench.run_reference(A()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "steps/s"
+    assert line["config"]["rows_per_step"] == 1024
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
